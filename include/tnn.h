@@ -1,0 +1,210 @@
+/*
+ * tnn.h - C ABI of libtnn, a GB300 (sm_103a) implementation of the DCT-based
+ * tensor SVD, t-product, tensor singular value thresholding (t-SVT) and TNN-C
+ * tensor completion of Xu, Zhao and Ng, "A Fast Algorithm for Cosine
+ * Transform Based Tensor Singular Value Decomposition" (arXiv 1902.03070).
+ *
+ * Layout.  A third-order tensor X of size n1 x n2 x n3 is one contiguous
+ * array in the paper's MATLAB order, element (i, j, k) at i + n1*(j + n2*k):
+ * each frontal slice X(:,:,k) is a column-major n1 x n2 matrix and the tube
+ * X(i,j,:) has stride n1*n2 (Section 2).  Element type: double for
+ * TNN_FP64, float for every other precision.
+ *
+ * Pointers.  Tensor arguments may be device pointers or host pointers; the
+ * library asks the CUDA runtime which.  Host buffers are staged through the
+ * context's device workspace with copies on the given stream (pinned host
+ * memory makes those copies asynchronous) and the call then synchronises the
+ * stream before it returns.  The caller owns every buffer it passes; the
+ * library never frees or keeps them.  The library allocates device memory only
+ * inside tnn_create, tnn_reserve and when a call finds the context's workspace
+ * too small (the workspace then grows and never shrinks).
+ *
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream).  Calls on device buffers are stream-ordered and return before the
+ * GPU finishes, except where a result is returned in host memory (tnn_out,
+ * the report of tnn_complete / tnn_admm_iterate): those calls synchronise
+ * the stream.
+ *
+ * Errors.  No call aborts or prints.  Invalid arguments (a NULL tensor
+ * pointer, a non-positive size, tau < 0, beta <= 0, ...) return TNN_EINVAL
+ * before anything is launched.  A failing CUDA call returns TNN_ECUDA.  A
+ * Jacobi SVD that reached its sweep cap, or an ADMM run that reached max_iter
+ * without meeting tol, returns TNN_ENOCONV with every output written.  A NaN
+ * or infinity met by a kernel returns TNN_ENONFINITE (outputs written but
+ * meaningless).  tnn_last_error() gives a one-line description of the last
+ * failure on a context.
+ *
+ * Threads.  A context may be used from one host thread at a time.
+ *
+ * Transforms.  dct denotes the orthonormal DCT-II along the tubes (MATLAB's
+ * dct(X,[],3), used by Algorithm 1): C[k,j] = a_k cos(pi (2j+1) k / (2 n3)),
+ * a_0 = sqrt(1/n3), a_k = sqrt(2/n3).  L denotes the scaled transform under
+ * which Theorem 3 and Example 1 hold as printed: L(X)_k = dct(X)_k / w_k with
+ * w = C e_1, the first column of C.  The t-product (Eq. 13) and the t-SVD
+ * (Theorem 4) use L; the t-SVT and Algorithm 1 use dct as written.
+ */
+#ifndef TNN_H
+#define TNN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TNN_OK = 0,
+    TNN_EINVAL = 1,     /* invalid argument; nothing was launched */
+    TNN_ENOMEM = 2,     /* device or pinned host allocation failed */
+    TNN_ECUDA = 3,      /* a CUDA runtime or driver call failed */
+    TNN_ENOCONV = 4,    /* Jacobi sweep cap or ADMM max_iter reached (outputs written) */
+    TNN_ENONFINITE = 5, /* NaN or infinity met */
+    TNN_ENODEV = 6      /* no usable sm_103 device */
+} tnn_status;
+
+typedef enum {
+    TNN_FP64 = 0,           /* double data, FP64 arithmetic everywhere (the plain path) */
+    TNN_FP32 = 1,           /* float data, FP32 arithmetic on CUDA cores */
+    TNN_FP32_TF32X3 = 2,    /* float data, tube DCT on tcgen05 tensor cores, 3xTF32 split */
+    TNN_FP32_BF16SPLIT = 3  /* float data, tube DCT on tcgen05 tensor cores, BF16 hi/mid/lo split */
+} tnn_precision;
+
+typedef struct {
+    int64_t n1, n2, n3;
+} tnn_shape;
+
+/* Algorithm 1 parameters.  beta follows beta <- min(rho beta, beta_max) after
+ * every iteration (rho = 1: the paper's fixed beta).  The run stops when both
+ * ||X+ - X||_F / ||X||_F <= tol (the paper's test) and ||Y - X+||_F /
+ * ||X+||_F <= tol (the residual of the splitting Y = X), or after max_iter
+ * iterations.  jacobi_max_sweeps caps the sweeps of every per-slice Jacobi
+ * SVD (0 selects 30). */
+typedef struct {
+    double beta0, rho, beta_max, tol;
+    int32_t max_iter;
+    int32_t jacobi_max_sweeps;
+} tnn_admm_params;
+
+typedef struct {
+    int32_t iters;              /* iterations run */
+    int32_t converged;          /* 1 if the tol test stopped the run */
+    double rel_change;          /* ||X+ - X||_F / ||X||_F of the last iteration */
+    double primal_res;          /* ||Y - X+||_F / ||X+||_F of the last iteration */
+    double beta_final;          /* beta after the last update */
+    int32_t jacobi_sweeps_max;  /* most sweeps any slice needed in the last iteration */
+    int32_t jacobi_unconverged; /* slices that hit the sweep cap, summed over the run */
+} tnn_admm_report;
+
+typedef struct tnn_ctx tnn_ctx;
+
+/* Create a context on CUDA device `device` (made current for the call).
+ * Returns TNN_ENODEV if the device is not compute capability 10.3. */
+tnn_status tnn_create(tnn_ctx** ctx, int device);
+
+/* Free the context and its workspace.  NULL is accepted. */
+void tnn_destroy(tnn_ctx* ctx);
+
+/* Static string naming a status code. */
+const char* tnn_status_string(tnn_status s);
+
+/* One-line description of the last failure on ctx ("" if none). */
+const char* tnn_last_error(const tnn_ctx* ctx);
+
+/* Grow the context's device workspace to at least `bytes` (never shrinks). */
+tnn_status tnn_reserve(tnn_ctx* ctx, size_t bytes);
+
+enum { TNN_OP_TDCT3 = 0, TNN_OP_TSVT = 1, TNN_OP_TSVD = 2, TNN_OP_TPROD = 3, TNN_OP_COMPLETE = 4 };
+
+/* Device workspace `op` needs for `shape` at `prec` with device buffers (host
+ * buffers add their staging).  For TNN_OP_TPROD the shape is (m1, m2, m3) and
+ * m4 = m2 is assumed; pass the largest of m2, m4 as n2 for a bound. */
+tnn_status tnn_workspace_size(tnn_ctx* ctx, int op, tnn_shape shape, tnn_precision prec, size_t* bytes);
+
+/* Tube transform (Section 3; Algorithm 1).
+ *   inverse = 0, scaled = 0:  Y = dct(X,[],3)
+ *   inverse = 1, scaled = 0:  Y = idct(X,[],3)
+ *   inverse = 0, scaled = 1:  Y = L(X)
+ *   inverse = 1, scaled = 1:  Y = L^-1(X)
+ * X and Y are n1 x n2 x n3; Y must not overlap X. */
+tnn_status tdct3(tnn_ctx* ctx, const void* X, tnn_shape shape, int inverse, int scaled,
+                 tnn_precision prec, void* Y, void* stream);
+
+/* Tensor singular value thresholding (Theorem 5, as Algorithm 1 computes it):
+ *   Zbar = dct(Z,[],3);  for every frontal slice k, Zbar_k = U S V^T (SVD)
+ *   and Ybar_k = U (S - tau)_+ V^T;  Y = idct(Ybar,[],3).
+ * Y is the proximal point of tau * sum_k ||dct(.)_k||_* at Z.  Z and Y are
+ * n1 x n2 x n3 and may be the same buffer.  tau >= 0.  If tnn_out is not
+ * NULL it receives sum_k ||Ybar_k||_* (the slice nuclear norms, without the
+ * 1/n3 of the TNN-C definition, Eq. 16) and the call synchronises. */
+tnn_status tsvt_dct(tnn_ctx* ctx, const void* Z, tnn_shape shape, double tau, tnn_precision prec,
+                    void* Y, double* tnn_out, void* stream);
+
+/* Thin DCT-based t-SVD (Theorem 4), r = min(n1, n2):  X = U * S * V^T under
+ * the t-product of Eq. 13, with U (n1 x r x n3) and V (n2 x r x n3)
+ * orthogonal in the sense U^T * U = V^T * V = I (identity tensor) and S
+ * f-diagonal (Definition 4).  S is returned as its r x n3 diagonal tubes:
+ * S(i,i,k) = S[i + r*k].  Computed as the SVD of every frontal slice of L(X)
+ * (singular values in descending order per slice) mapped back by L^-1. */
+tnn_status tsvd_dct_forward(tnn_ctx* ctx, const void* X, tnn_shape shape, tnn_precision prec,
+                            void* U, void* S, void* V, void* stream);
+
+/* Inverse of tsvd_dct_forward: X = U * S * V^T (Eq. 13 t-products) for U
+ * (n1 x r x n3), S (r x n3 diagonal tubes), V (n2 x r x n3), r = min(n1, n2). */
+tnn_status tsvd_dct_inverse(tnn_ctx* ctx, const void* U, const void* S, const void* V, tnn_shape shape,
+                            tnn_precision prec, void* X, void* stream);
+
+/* DCT-based t-product (Definition 7, Eq. 13): Z = X * Y = fold(btph(A) unfold(Y))
+ * for X (m1 x m2 x m3) and Y (m2 x m4 x m3); Z is m1 x m4 x m3.  Computed
+ * facewise in the transform domain (Eq. 14): L(Z)_k = L(X)_k L(Y)_k.
+ * Z must not overlap X or Y. */
+tnn_status tprod_dct(tnn_ctx* ctx, const void* X, const void* Y, int64_t m1, int64_t m2, int64_t m4,
+                     int64_t m3, tnn_precision prec, void* Z, void* stream);
+
+/* Algorithm 1: ADMM for the completion model (Eq. 17) from X = B on the
+ * mask, M = 0, beta = beta0.  B (n1 x n2 x n3) is read only where mask != 0.
+ * mask is n1*n2*n3 bytes in the tensor's layout (nonzero = observed).
+ * X_out receives the recovered tensor and may be the same buffer as B.
+ * rep (may be NULL) receives the run's report.  Synchronises the stream.
+ * Returns TNN_ENOCONV if max_iter was reached before the tol test passed. */
+tnn_status tnn_complete(tnn_ctx* ctx, const void* B, const uint8_t* mask, tnn_shape shape,
+                        const tnn_admm_params* params, tnn_precision prec, void* X_out,
+                        tnn_admm_report* rep, void* stream);
+
+/* Run up to `iters` iterations of Algorithm 1 from a caller-held state:
+ * X and M (n1 x n2 x n3, device or host, updated in place) and *beta (host,
+ * updated).  The iteration counter starts from 0 for this call; params->tol
+ * and params->max_iter still stop the run (max_iter counts iterations of this
+ * call).  A run split over several calls computes exactly what one call
+ * does (checkpoint and resume).  rep may be NULL.  Synchronises the stream.
+ * Returns TNN_OK when all requested iterations ran or tol was met. */
+tnn_status tnn_admm_iterate(tnn_ctx* ctx, const void* B, const uint8_t* mask, tnn_shape shape,
+                            const tnn_admm_params* params, tnn_precision prec, void* X, void* M,
+                            double* beta, int32_t iters, tnn_admm_report* rep, void* stream);
+
+/* Kernel statistics of the last tsvt_dct / tsvd_dct_forward / ADMM iteration
+ * on ctx: out[0] = slices, out[1] = column pairs visited, out[2] = rotations
+ * applied, out[3] = most sweeps of any slice, out[4] = slices that hit the
+ * sweep cap, out[5] = singular values kept (above tau) over all slices.
+ * Synchronises the last stream used. */
+tnn_status tnn_last_jacobi_stats(tnn_ctx* ctx, int64_t out[6]);
+
+/* Tracing (no counterpart in the paper).  While enabled, every kernel a call
+ * launches is bracketed by two CUDA events on the call's stream.
+ * tnn_profile_read synchronises on those events, returns per kernel kind the
+ * summed device time (ms) and the launch count since the last read, and
+ * clears the record.  Kinds (array index):
+ *   0 tube transform            1 forward transform + ADMM prologue
+ *   2 Jacobi SVT                3 inverse transform + ADMM epilogue
+ *   4 ADMM iteration finalize   5 ADMM control init
+ *   6 ADMM state init           7 Jacobi SVD
+ *   8 facewise product */
+#define TNN_NKERNELS 9
+tnn_status tnn_profile(tnn_ctx* ctx, int enable);
+tnn_status tnn_profile_read(tnn_ctx* ctx, double ms[TNN_NKERNELS], int64_t launches[TNN_NKERNELS]);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TNN_H */

@@ -1,0 +1,26 @@
+// Jacobi SVD launches (singular vectors kept), double slices.
+#include "jacobi_launch.cuh"
+
+namespace tnn {
+
+template <>
+cudaError_t launch_jacobi_svd<double>(const JacobiPlan& p, const double* data, double* U, double* sigma, double* V,
+                                   int max_sweeps, void* work, SliceStats* stats, cudaStream_t s)
+{
+    jac::KArgs<double> a{};
+    a.data = const_cast<double*>(data); a.n1 = p.n1; a.n2 = p.n2; a.n3 = p.n3;
+    a.m = p.m; a.n = p.n; a.tr = p.tr; a.nb = p.nb; a.ldA = p.ldA;
+    a.tau = 0.0; a.ctl = nullptr; a.max_sweeps = max_sweeps;
+    a.work = reinterpret_cast<double*>(work); a.stats = stats;
+    a.U = U; a.S = sigma; a.V = V;
+    switch (p.RA) {
+        TNN_JAC_CASE(double, 1, true)
+        TNN_JAC_CASE(double, 2, true)
+        TNN_JAC_CASE(double, 4, true)
+        TNN_JAC_CASE(double, 6, true)
+        TNN_JAC_CASE(double, 8, true)
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace tnn

@@ -1,0 +1,26 @@
+// Jacobi SVT launches, float slices.
+#include "jacobi_launch.cuh"
+
+namespace tnn {
+
+template <>
+cudaError_t launch_jacobi_svt<float>(const JacobiPlan& p, float* data, double tau, const AdmmCtl* ctl, int max_sweeps,
+                                   void* work, SliceStats* stats, cudaStream_t s)
+{
+    jac::KArgs<float> a{};
+    a.data = data; a.n1 = p.n1; a.n2 = p.n2; a.n3 = p.n3;
+    a.m = p.m; a.n = p.n; a.tr = p.tr; a.nb = p.nb; a.ldA = p.ldA;
+    a.tau = tau; a.ctl = ctl; a.max_sweeps = max_sweeps;
+    a.work = reinterpret_cast<float*>(work); a.stats = stats;
+    switch (p.RA) {
+        TNN_JAC_CASE(float, 2, false)
+        TNN_JAC_CASE(float, 4, false)
+        TNN_JAC_CASE(float, 6, false)
+        TNN_JAC_CASE(float, 8, false)
+        TNN_JAC_CASE(float, 12, false)
+        TNN_JAC_CASE(float, 16, false)
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace tnn

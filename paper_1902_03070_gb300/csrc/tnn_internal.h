@@ -1,0 +1,123 @@
+// Internal declarations shared by the libtnn CUDA sources.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tnn.h"
+
+namespace tnn {
+
+// Device-resident control block of an ADMM run (Algorithm 1).  Every kernel
+// of an iteration reads beta and `done` from here, and the finalize kernel
+// advances it, so iterations can be queued ahead of the host's stop test:
+// once `done` is set, queued iterations exit at their first instruction.
+struct AdmmCtl {
+    double beta;       // beta of the iteration about to run
+    double rho, beta_max, tol;
+    int32_t iter;      // iterations completed in this run
+    int32_t max_iter;
+    int32_t done;      // 1: the run has stopped; kernels return immediately
+    int32_t converged; // 1: the tol test stopped the run
+    double rel_change; // ||X+ - X|| / ||X|| of the last completed iteration
+    double primal_res; // ||Y - X+|| / ||X+|| of the last completed iteration
+    int32_t sweeps_max;       // most Jacobi sweeps of a slice, last iteration
+    int32_t unconverged;      // slices that hit the sweep cap, whole run
+    int32_t nonfinite;        // a NaN/Inf was met
+    int32_t pad_;
+};
+
+// Per-slice Jacobi statistics, written by the SVT/SVD kernels.
+struct SliceStats {
+    double nuc;        // sum_i (sigma_i - tau)_+ of the slice
+    int64_t pairs;     // column pairs visited
+    int64_t rotations; // rotations applied
+    int32_t sweeps;    // sweeps run
+    int32_t converged; // 1 if the last sweep applied no rotation
+    int32_t nonfinite; // 1 if a NaN/Inf was met
+    int32_t kept;      // singular values above tau (SVT) / singular values (SVD)
+};
+
+// ---- tube transforms (tube.cu) ----------------------------------------------
+// out(p, q) = sum_j in(p, j) * op(j, q) over the tube index (P pixels, n3
+// tube positions), op the n3 x n3 operator built by launch_build_operator
+// from the DCT definition:
+//   forward (inverse = 0): op(j, q) = C[q, j]      (divided by w_q if scaled)
+//   inverse (inverse = 1): op(k, q) = C[k, q]      (times w_k if scaled)
+template <typename T>
+cudaError_t launch_build_operator(T* op, int64_t n3, int inverse, int scaled, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_tube_op(const T* X, T* Y, const T* op, int64_t P, int64_t n3, cudaStream_t s);
+
+// Forward transform with the ADMM prologue Z = X - M / beta (beta from ctl).
+template <typename T>
+cudaError_t launch_tube_fwd_admm_op(const T* X, const T* M, T* Zbar, const T* op, int64_t P, int64_t n3,
+                                    const AdmmCtl* ctl, cudaStream_t s);
+
+// Inverse transform with the ADMM epilogue of Algorithm 1: Y = idct(Ybar);
+//   X+ = mask ? B : Y + M / beta;  M+ = M + beta (Y - X+);  X <- X+, M <- M+;
+// per-block FP64 partial sums of ||X+ - X||^2, ||X||^2, ||Y - X+||^2, ||X+||^2
+// into `partials` (4 doubles per block); *nblocks receives the block count.
+template <typename T>
+cudaError_t launch_tube_inv_admm_op(const T* Ybar, T* X, T* M, const T* B, const uint8_t* mask, const T* op,
+                                    int64_t P, int64_t n3, const AdmmCtl* ctl, double* partials, int* nblocks,
+                                    cudaStream_t s);
+
+// Number of partial-sum blocks launch_tube_inv_admm_op writes.
+int tube_partials_count(int64_t P, int64_t n3);
+
+// Finalize one ADMM iteration: reduce the partials (fixed order), set
+// rel_change / primal_res, advance beta and iter, set done.  One block.
+cudaError_t launch_admm_finalize(AdmmCtl* ctl, const double* partials, int nblocks, const SliceStats* stats,
+                                 int64_t n3, cudaStream_t s);
+
+// X = mask ? B : 0,  M = 0.
+template <typename T>
+cudaError_t launch_admm_init(const T* B, const uint8_t* mask, T* X, T* M, int64_t N, cudaStream_t s);
+cudaError_t launch_ctl_init(AdmmCtl* ctl, double beta, double rho, double beta_max, double tol, int max_iter,
+                            cudaStream_t s);
+
+// ---- Jacobi SVT / SVD (jacobi.cu) -------------------------------------------
+enum JacobiMode { JAC_SVT = 0, JAC_SVD = 1 };
+
+struct JacobiPlan {
+    int64_t n1, n2, n3;
+    int m, n;          // oriented slice: m >= n (m = max(n1,n2))
+    int tr;            // 1 if the slice is transposed (n1 < n2)
+    int K, RA, W;      // block width, rows per lane, warps per CTA
+    int nb;            // number of column blocks (even)
+    int ldA;           // leading dimension of the working copy (rows, padded)
+    int in_smem;       // working copy in shared memory
+    size_t smem_bytes; // dynamic shared memory per CTA
+    size_t work_bytes; // global scratch per launch
+    int elem;          // sizeof(T)
+};
+
+// Plan a Jacobi launch for n1 x n2 slices of element size elem (4 or 8).
+// Returns false if the shape is beyond what the kernels support.
+bool jacobi_plan(int64_t n1, int64_t n2, int64_t n3, int elem, JacobiPlan* plan);
+// Same, for the SVD launch (singular vectors kept) when withv is true.
+bool jacobi_plan_mode(int64_t n1, int64_t n2, int64_t n3, int elem, bool withv, JacobiPlan* plan);
+
+// SVT of every frontal slice of `data` in place:  data_k <- U (S - tau)_+ V^T.
+// tau = 1 / ctl->beta when ctl is not null (and the launch exits if ctl->done).
+template <typename T>
+cudaError_t launch_jacobi_svt(const JacobiPlan& plan, T* data, double tau, const AdmmCtl* ctl, int max_sweeps,
+                              void* work, SliceStats* stats, cudaStream_t s);
+
+// SVD of every frontal slice of `data` (not modified):  U (n1 x r per slice),
+// sigma (r per slice, descending), V (n2 x r per slice), r = min(n1, n2).
+template <typename T>
+cudaError_t launch_jacobi_svd(const JacobiPlan& plan, const T* data, T* U, T* sigma, T* V, int max_sweeps,
+                              void* work, SliceStats* stats, cudaStream_t s);
+
+// ---- facewise products (facewise.cu) -------------------------------------------
+// C_k = op(A_k) * B_k for k < nb, A_k m x kk (or kk x m if transA), B_k kk x n,
+// all column-major and contiguous per slice.  Optional per-slice column scale
+// of A: if dscale != null, A_k(:, q) is multiplied by dscale[q + kk*k].
+template <typename T>
+cudaError_t launch_facewise(const T* A, const T* B, T* C, int64_t m, int64_t n, int64_t kk, int64_t nbatch,
+                            int transA, int transB, const T* dscale, cudaStream_t s);
+
+}  // namespace tnn

@@ -1,0 +1,317 @@
+"""Thin ctypes binding of libtnn (include/tnn.h), same names as the C ABI.
+
+Only argument marshalling happens here: every step of every call runs in the
+library's CUDA kernels.  Importing this module fails if libtnn.so has not been
+built (there is no CPU fallback).
+
+Tensors follow the paper's MATLAB layout: an n1 x n2 x n3 tensor is a
+torch.Tensor or numpy.ndarray of shape (n1, n2, n3) whose element (i, j, k)
+sits at offset i + n1*(j + n2*k) (Fortran order; see `fortran_empty`).
+CUDA tensors are passed as device pointers on torch's current stream; NumPy
+arrays and CPU tensors are passed as host pointers (the library stages them and
+synchronises).
+"""
+import ctypes as _ct
+import os as _os
+
+import numpy as _np
+
+_HERE = _os.path.dirname(_os.path.abspath(__file__))
+LIB_PATH = _os.path.join(_HERE, "libtnn.so")
+
+if not _os.path.exists(LIB_PATH):
+    raise ImportError("libtnn.so is not built (run `python -c 'import __graft_entry__ as g; g.build()'`)")
+
+_lib = _ct.CDLL(LIB_PATH)
+
+OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ENONFINITE, ENODEV = range(7)
+PRECISIONS = {"fp64": 0, "fp32": 1, "tf32x3": 2, "bf16split": 3}
+OP_TDCT3, OP_TSVT, OP_TSVD, OP_TPROD, OP_COMPLETE = range(5)
+
+
+class Shape(_ct.Structure):
+    _fields_ = [("n1", _ct.c_int64), ("n2", _ct.c_int64), ("n3", _ct.c_int64)]
+
+
+class AdmmParams(_ct.Structure):
+    _fields_ = [("beta0", _ct.c_double), ("rho", _ct.c_double), ("beta_max", _ct.c_double), ("tol", _ct.c_double),
+                ("max_iter", _ct.c_int32), ("jacobi_max_sweeps", _ct.c_int32)]
+
+
+class AdmmReport(_ct.Structure):
+    _fields_ = [("iters", _ct.c_int32), ("converged", _ct.c_int32), ("rel_change", _ct.c_double),
+                ("primal_res", _ct.c_double), ("beta_final", _ct.c_double), ("jacobi_sweeps_max", _ct.c_int32),
+                ("jacobi_unconverged", _ct.c_int32)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_vp = _ct.c_void_p
+_st = _ct.c_int
+_lib.tnn_create.argtypes = [_ct.POINTER(_vp), _ct.c_int]
+_lib.tnn_create.restype = _st
+_lib.tnn_destroy.argtypes = [_vp]
+_lib.tnn_destroy.restype = None
+_lib.tnn_status_string.argtypes = [_st]
+_lib.tnn_status_string.restype = _ct.c_char_p
+_lib.tnn_last_error.argtypes = [_vp]
+_lib.tnn_last_error.restype = _ct.c_char_p
+_lib.tnn_reserve.argtypes = [_vp, _ct.c_size_t]
+_lib.tnn_reserve.restype = _st
+_lib.tnn_workspace_size.argtypes = [_vp, _ct.c_int, Shape, _ct.c_int, _ct.POINTER(_ct.c_size_t)]
+_lib.tnn_workspace_size.restype = _st
+_lib.tdct3.argtypes = [_vp, _vp, Shape, _ct.c_int, _ct.c_int, _ct.c_int, _vp, _vp]
+_lib.tdct3.restype = _st
+_lib.tsvt_dct.argtypes = [_vp, _vp, Shape, _ct.c_double, _ct.c_int, _vp, _ct.POINTER(_ct.c_double), _vp]
+_lib.tsvt_dct.restype = _st
+_lib.tsvd_dct_forward.argtypes = [_vp, _vp, Shape, _ct.c_int, _vp, _vp, _vp, _vp]
+_lib.tsvd_dct_forward.restype = _st
+_lib.tsvd_dct_inverse.argtypes = [_vp, _vp, _vp, _vp, Shape, _ct.c_int, _vp, _vp]
+_lib.tsvd_dct_inverse.restype = _st
+_lib.tprod_dct.argtypes = [_vp, _vp, _vp, _ct.c_int64, _ct.c_int64, _ct.c_int64, _ct.c_int64, _ct.c_int, _vp, _vp]
+_lib.tprod_dct.restype = _st
+_lib.tnn_complete.argtypes = [_vp, _vp, _vp, Shape, _ct.POINTER(AdmmParams), _ct.c_int, _vp,
+                              _ct.POINTER(AdmmReport), _vp]
+_lib.tnn_complete.restype = _st
+_lib.tnn_admm_iterate.argtypes = [_vp, _vp, _vp, Shape, _ct.POINTER(AdmmParams), _ct.c_int, _vp, _vp,
+                                  _ct.POINTER(_ct.c_double), _ct.c_int32, _ct.POINTER(AdmmReport), _vp]
+_lib.tnn_admm_iterate.restype = _st
+_lib.tnn_last_jacobi_stats.argtypes = [_vp, _ct.POINTER(_ct.c_int64)]
+_lib.tnn_last_jacobi_stats.restype = _st
+_lib.tnn_profile.argtypes = [_vp, _ct.c_int]
+_lib.tnn_profile.restype = _st
+_lib.tnn_profile_read.argtypes = [_vp, _ct.POINTER(_ct.c_double), _ct.POINTER(_ct.c_int64)]
+_lib.tnn_profile_read.restype = _st
+NKERNELS = 9
+KERNEL_KINDS = ["tube", "tube_fwd_admm", "jacobi_svt", "tube_inv_admm", "admm_finalize", "ctl_init", "admm_init",
+                "jacobi_svd", "facewise"]
+
+EXPORTS = ["tnn_create", "tnn_destroy", "tnn_status_string", "tnn_last_error", "tnn_reserve", "tnn_workspace_size",
+           "tdct3", "tsvt_dct", "tsvd_dct_forward", "tsvd_dct_inverse", "tprod_dct", "tnn_complete",
+           "tnn_admm_iterate", "tnn_last_jacobi_stats", "tnn_profile", "tnn_profile_read"]
+
+
+class TnnError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_lib.tnn_status_string(status).decode(), msg))
+        self.status = status
+
+
+def status_string(s):
+    return _lib.tnn_status_string(int(s)).decode()
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def _check_layout(x, shape):
+    """x must be (n1, n2, n3) with element (i, j, k) at i + n1*(j + n2*k)."""
+    if tuple(x.shape) != tuple(shape):
+        raise ValueError("expected shape %s, got %s" % (tuple(shape), tuple(x.shape)))
+    if _is_torch(x):
+        exp, acc = [], 1
+        for d in shape:
+            exp.append(acc)
+            acc *= d
+        ok = all(st == e for st, e, d in zip(x.stride(), exp, shape) if d > 1)
+    else:
+        ok = x.flags.f_contiguous
+    if not ok:
+        raise ValueError("tensor must be in Fortran (MATLAB) order; use fortran_empty / to_fortran")
+
+
+def _ptr(x):
+    if _is_torch(x):
+        return x.data_ptr(), x.is_cuda
+    return x.ctypes.data, False
+
+
+def _dtype_ok(x, prec):
+    want = "float64" if prec == "fp64" else "float32"
+    name = str(x.dtype).replace("torch.", "")
+    if name != want:
+        raise TypeError("precision %s needs %s data, got %s" % (prec, want, name))
+
+
+def _stream(args):
+    for a in args:
+        if _is_torch(a) and a.is_cuda:
+            import torch
+            return _ct.c_void_p(torch.cuda.current_stream(a.device).cuda_stream)
+    return _ct.c_void_p(0)
+
+
+def fortran_empty(shape, dtype, device="cuda"):
+    """Uninitialised torch tensor of `shape` in Fortran order."""
+    import torch
+    return torch.empty(tuple(reversed(shape)), dtype=dtype, device=device).permute(*reversed(range(len(shape))))
+
+
+def to_fortran(x, device="cuda", dtype=None):
+    """Copy a NumPy array or tensor into a Fortran-ordered torch tensor."""
+    import torch
+    a = _np.asarray(x.cpu().numpy() if _is_torch(x) else x)
+    if dtype is None:
+        dtype = torch.float64 if a.dtype == _np.float64 else (torch.uint8 if a.dtype == _np.uint8 else torch.float32)
+    t = torch.from_numpy(_np.ascontiguousarray(_np.transpose(a, tuple(reversed(range(a.ndim))))))
+    t = t.to(device=device, dtype=dtype)
+    return t.permute(*reversed(range(a.ndim)))
+
+
+def to_numpy(t):
+    """Fortran-ordered NumPy copy of a tensor produced by this binding."""
+    if _is_torch(t):
+        return _np.asfortranarray(t.detach().cpu().numpy())
+    return _np.asfortranarray(t)
+
+
+class Context:
+    """A libtnn context (device workspace, DCT operator cache)."""
+
+    def __init__(self, device=0):
+        h = _vp()
+        st = _lib.tnn_create(_ct.byref(h), int(device))
+        if st != OK:
+            raise TnnError(st, "tnn_create(device=%d)" % device)
+        self._h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.tnn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _chk(self, st, what, allow=()):
+        if st != OK and st not in allow:
+            raise TnnError(st, "%s: %s" % (what, _lib.tnn_last_error(self._h).decode()))
+        return st
+
+    def last_error(self):
+        return _lib.tnn_last_error(self._h).decode()
+
+    def reserve(self, nbytes):
+        self._chk(_lib.tnn_reserve(self._h, int(nbytes)), "tnn_reserve")
+
+    def workspace_size(self, op, shape, prec="fp32"):
+        out = _ct.c_size_t(0)
+        self._chk(_lib.tnn_workspace_size(self._h, int(op), Shape(*shape), PRECISIONS[prec], _ct.byref(out)),
+                  "tnn_workspace_size")
+        return out.value
+
+    def tdct3(self, X, Y, inverse=False, scaled=False, prec="fp32"):
+        _check_layout(Y, X.shape)
+        _check_layout(X, X.shape)
+        _dtype_ok(X, prec)
+        self._chk(_lib.tdct3(self._h, _ptr(X)[0], Shape(*X.shape), int(inverse), int(scaled), PRECISIONS[prec],
+                             _ptr(Y)[0], _stream([X, Y])), "tdct3")
+        return Y
+
+    def tsvt(self, Z, tau, Y=None, prec="fp32", want_tnn=False, allow_noconv=False):
+        """Y = t-SVT_tau(Z) (Theorem 5).  Returns Y, or (Y, tnn) with want_tnn."""
+        if len(Z.shape) == 2:
+            raise ValueError("pass a 3-way tensor (n1, n2, n3)")
+        _check_layout(Z, Z.shape)
+        _dtype_ok(Z, prec)
+        if Y is None:
+            Y = Z
+        _check_layout(Y, Z.shape)
+        out = _ct.c_double(0.0)
+        st = _lib.tsvt_dct(self._h, _ptr(Z)[0], Shape(*Z.shape), float(tau), PRECISIONS[prec], _ptr(Y)[0],
+                           _ct.byref(out) if want_tnn else None, _stream([Z, Y]))
+        self._chk(st, "tsvt_dct", allow=(ENOCONV,) if allow_noconv else ())
+        return (Y, out.value) if want_tnn else Y
+
+    def tsvd(self, X, U, S, V, prec="fp32"):
+        n1, n2, n3 = X.shape
+        r = min(n1, n2)
+        _check_layout(X, (n1, n2, n3))
+        _check_layout(U, (n1, r, n3))
+        _check_layout(V, (n2, r, n3))
+        _check_layout(S, (r, n3))
+        _dtype_ok(X, prec)
+        self._chk(_lib.tsvd_dct_forward(self._h, _ptr(X)[0], Shape(n1, n2, n3), PRECISIONS[prec], _ptr(U)[0],
+                                        _ptr(S)[0], _ptr(V)[0], _stream([X, U, S, V])), "tsvd_dct_forward")
+        return U, S, V
+
+    def tsvd_inverse(self, U, S, V, X, prec="fp32"):
+        n1, n2, n3 = X.shape
+        r = min(n1, n2)
+        _check_layout(X, (n1, n2, n3))
+        _check_layout(U, (n1, r, n3))
+        _check_layout(V, (n2, r, n3))
+        _check_layout(S, (r, n3))
+        self._chk(_lib.tsvd_dct_inverse(self._h, _ptr(U)[0], _ptr(S)[0], _ptr(V)[0], Shape(n1, n2, n3),
+                                        PRECISIONS[prec], _ptr(X)[0], _stream([X, U, S, V])), "tsvd_dct_inverse")
+        return X
+
+    def tprod(self, X, Y, Z, prec="fp32"):
+        m1, m2, m3 = X.shape
+        m2b, m4, m3b = Y.shape
+        if m2 != m2b or m3 != m3b:
+            raise ValueError("t-product shape mismatch")
+        _check_layout(X, (m1, m2, m3))
+        _check_layout(Y, (m2, m4, m3))
+        _check_layout(Z, (m1, m4, m3))
+        self._chk(_lib.tprod_dct(self._h, _ptr(X)[0], _ptr(Y)[0], m1, m2, m4, m3, PRECISIONS[prec], _ptr(Z)[0],
+                                 _stream([X, Y, Z])), "tprod_dct")
+        return Z
+
+    @staticmethod
+    def params(beta0=1e-4, rho=1.1, beta_max=1e10, tol=1e-8, max_iter=300, jacobi_max_sweeps=0):
+        return AdmmParams(float(beta0), float(rho), float(beta_max), float(tol), int(max_iter),
+                          int(jacobi_max_sweeps))
+
+    def complete(self, B, mask, X_out, params, prec="fp32"):
+        """Algorithm 1.  Returns (status, report dict); TNN_ENOCONV is not raised."""
+        _check_layout(B, B.shape)
+        _check_layout(X_out, B.shape)
+        _check_layout(mask, B.shape)
+        rep = AdmmReport()
+        st = _lib.tnn_complete(self._h, _ptr(B)[0], _ptr(mask)[0], Shape(*B.shape), _ct.byref(params),
+                               PRECISIONS[prec], _ptr(X_out)[0], _ct.byref(rep), _stream([B, mask, X_out]))
+        self._chk(st, "tnn_complete", allow=(ENOCONV,))
+        return st, rep.as_dict()
+
+    def admm_iterate(self, B, mask, X, M, beta, iters, params, prec="fp32"):
+        """Advance a caller-held ADMM state (X, M, beta) by up to `iters`
+        iterations.  Returns (beta, report dict)."""
+        for t in (B, X, M, mask):
+            _check_layout(t, B.shape)
+        b = _ct.c_double(float(beta))
+        rep = AdmmReport()
+        st = _lib.tnn_admm_iterate(self._h, _ptr(B)[0], _ptr(mask)[0], Shape(*B.shape), _ct.byref(params),
+                                   PRECISIONS[prec], _ptr(X)[0], _ptr(M)[0], _ct.byref(b), int(iters),
+                                   _ct.byref(rep), _stream([B, mask, X, M]))
+        self._chk(st, "tnn_admm_iterate")
+        return b.value, rep.as_dict()
+
+    def last_jacobi_stats(self):
+        out = (_ct.c_int64 * 6)()
+        self._chk(_lib.tnn_last_jacobi_stats(self._h, out), "tnn_last_jacobi_stats")
+        keys = ["slices", "pairs", "rotations", "max_sweeps", "unconverged", "kept"]
+        return dict(zip(keys, list(out)))
+
+    def profile(self, enable=True):
+        """Bracket every kernel launch of later calls with CUDA events."""
+        self._chk(_lib.tnn_profile(self._h, int(bool(enable))), "tnn_profile")
+
+    def profile_read(self):
+        """{kind: (ms, launches)} since the last read (synchronises)."""
+        ms = (_ct.c_double * NKERNELS)()
+        cnt = (_ct.c_int64 * NKERNELS)()
+        self._chk(_lib.tnn_profile_read(self._h, ms, cnt), "tnn_profile_read")
+        return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_KINDS) if cnt[i]}

@@ -1,0 +1,90 @@
+"""GPU parity: Algorithm 1 (ADMM, Eq. 17) through the C ABI.
+FP64: iterates match the oracle's, the invariants X_Omega = B_Omega and
+M_{Omega^c} = 0 hold bit-exactly, a run split over several calls equals one
+call bit-for-bit, and the 48 x 48 x 16 completion ends within 1e-4 of the
+oracle's final error."""
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_common import THREADS, dtype_of, torch_cuda
+from paper_1902_03070_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch_cuda()
+    from paper_1902_03070_gb300 import tnn
+    with tnn.Context(0) as c:
+        yield c
+
+
+def _small(seed=1, shape=(20, 18, 6), r=2, frac=0.5):
+    rng = np.random.default_rng(seed)
+    A, F = inputs.lowrank_factors(shape[0], shape[1], shape[2], r, rng)
+    T = O.tprod(A, F)
+    mask = inputs.uniform_mask(T.shape, frac, np.random.default_rng(seed + 1))
+    return T, inputs.fortran(T * mask), mask
+
+
+@pytest.mark.parametrize("iters", [1, 4, 12])
+def test_admm_iterates_match_oracle_fp64(ctx, iters):
+    from paper_1902_03070_gb300 import tnn
+    T, B, mask = _small()
+    prm = dict(beta0=0.05, rho=1.3, beta_max=1e6, tol=-1.0, max_iter=iters)
+    Xo, Mo, rep_o = O.admm(B, mask, **prm)
+    dt = dtype_of("fp64")
+    Bd, md = tnn.to_fortran(B, dtype=dt), tnn.to_fortran(mask)
+    Xd = tnn.fortran_empty(B.shape, dt)
+    st, rep = ctx.complete(Bd, md, Xd, ctx.params(**prm), prec="fp64")
+    assert rep["iters"] == iters == rep_o["iters"]
+    X = tnn.to_numpy(Xd)
+    assert np.linalg.norm(X - Xo) <= 1e-12 * np.linalg.norm(Xo)
+    assert abs(rep["beta_final"] - rep_o["beta_final"]) <= 1e-15 * rep_o["beta_final"]
+    m = mask.astype(bool)
+    assert np.array_equal(X[m], B[m])
+
+
+def test_admm_invariants_and_resume_bit_exact(ctx):
+    from paper_1902_03070_gb300 import tnn
+    torch = torch_cuda()
+    T, B, mask = _small(seed=5)
+    dt = dtype_of("fp64")
+    prm = ctx.params(beta0=0.05, rho=1.2, beta_max=1e6, tol=-1.0, max_iter=100)
+    Bd, md = tnn.to_fortran(B, dtype=dt), tnn.to_fortran(mask)
+
+    def state():
+        X = tnn.to_fortran(B * mask, dtype=dt)
+        M = tnn.to_fortran(np.zeros(B.shape), dtype=dt)
+        return X, M
+
+    X1, M1 = state()
+    b1, _ = ctx.admm_iterate(Bd, md, X1, M1, 0.05, 7, prm, prec="fp64")
+    X2, M2 = state()
+    b2, _ = ctx.admm_iterate(Bd, md, X2, M2, 0.05, 3, prm, prec="fp64")
+    b2, _ = ctx.admm_iterate(Bd, md, X2, M2, b2, 4, prm, prec="fp64")
+    assert b1 == b2
+    assert torch.equal(X1, X2) and torch.equal(M1, M2)
+    m = torch.from_numpy(mask.astype(bool).transpose(2, 1, 0).copy()).cuda().permute(2, 1, 0)
+    assert torch.equal(X1[m], Bd[m])
+    assert not M1[~m].any()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_completion_48x48x16(ctx, prec):
+    """Tubal rank 3, 40% observed, beta0 1e-4, rho 1.1, tol 1e-8, <= 300 iterations."""
+    from paper_1902_03070_gb300 import tnn
+    d = inputs.config1(O.tprod)
+    T, B, mask, prm = d["T"], d["B"], d["mask"], d["admm"]
+    Xo, _, rep_o = O.admm(B, mask, nthreads=THREADS, **prm)
+    err_o = np.linalg.norm(Xo - T) / np.linalg.norm(T)
+    dt = dtype_of(prec)
+    Xd = tnn.fortran_empty(B.shape, dt)
+    st, rep = ctx.complete(tnn.to_fortran(B, dtype=dt), tnn.to_fortran(mask), Xd, ctx.params(**prm), prec=prec)
+    err = np.linalg.norm(tnn.to_numpy(Xd) - T) / np.linalg.norm(T)
+    assert abs(err - err_o) <= 1e-4, (err, err_o, rep, rep_o)
+    if prec == "fp64":
+        assert rep["iters"] == rep_o["iters"]
+        assert np.linalg.norm(tnn.to_numpy(Xd) - Xo) <= 1e-9 * np.linalg.norm(Xo)

@@ -1,0 +1,130 @@
+"""GPU parity: t-SVT (Theorem 5, Algorithm 1) through the C ABI against the
+FP64 oracle.  FP64 path: relative Frobenius error <= 1e-12.  FP32 path:
+<= 1e-5, the error measured against ||Y_oracle|| (against ||Z|| when the
+oracle's Y is below 1e-6 ||Z||)."""
+import numpy as np
+import pytest
+import scipy.fft
+
+import oracle as O
+from gpu_common import THREADS, dtype_of, rel_err, tau_at_quantile, torch_cuda
+from paper_1902_03070_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+
+SHAPES = [
+    (48, 48, 16),    # the 48 x 48 x 16 completion workload
+    (7, 5, 3), (5, 7, 3),          # tall / wide (transposed orientation)
+    (1, 9, 4), (9, 1, 4),          # single row / column
+    (33, 65, 5), (65, 33, 2),      # ragged tails over several column blocks
+    (130, 100, 3),                 # more rows than 4 x 32
+    (40, 40, 1),                   # one slice: the matrix SVT
+]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch_cuda()
+    from paper_1902_03070_gb300 import tnn
+    with tnn.Context(0) as c:
+        yield c
+
+
+def _run(ctx, Z, tau, prec, want_tnn=False):
+    from paper_1902_03070_gb300 import tnn
+    Zd = tnn.to_fortran(Z, dtype=dtype_of(prec))
+    Yd = tnn.fortran_empty(Z.shape, dtype_of(prec))
+    out = ctx.tsvt(Zd, tau, Y=Yd, prec=prec, want_tnn=want_tnn)
+    if want_tnn:
+        return tnn.to_numpy(out[0]).astype(np.float64), out[1]
+    return tnn.to_numpy(out).astype(np.float64)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("q", [0.3, 0.8])
+def test_tsvt_matches_oracle(ctx, prec, shape, q):
+    rng = np.random.default_rng(shape[0] * 1000 + shape[1] * 10 + shape[2])
+    Z = inputs.random_tensor(shape, rng)
+    if prec == "fp32":
+        Z = Z.astype(np.float32).astype(np.float64)
+    tau = tau_at_quantile(Z, q)
+    Y = _run(ctx, Z, tau, prec)
+    ref = O.tsvt(Z, tau, nthreads=THREADS)
+    assert rel_err(Y, ref, Z) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_tsvt_low_rank_plus_noise(ctx, prec):
+    # a 48 x 48 x 16 tubal-rank-3 tensor plus noise, threshold above the noise edge
+    rng = np.random.default_rng(7)
+    A, F = inputs.lowrank_factors(48, 48, 16, 3, rng)
+    Z = O.tprod(A, F) + 1e-3 * rng.standard_normal((48, 48, 16))
+    Z = np.asfortranarray(Z)
+    if prec == "fp32":
+        Z = Z.astype(np.float32).astype(np.float64)
+    tau = 0.05
+    Y, tnn_gpu = _run(ctx, Z, tau, prec, want_tnn=True)
+    ref, tnn_ref, _ = O.tsvt(Z, tau, nthreads=THREADS, return_info=True)
+    assert rel_err(Y, ref, Z) <= TOL[prec]
+    assert abs(tnn_gpu - tnn_ref) <= (1e-12 if prec == "fp64" else 1e-5) * tnn_ref
+
+
+def test_tsvt_video_shaped_fp32(ctx):
+    """The 144 x 176 x 100 video-shaped tensor at full size, FP32."""
+    parts = inputs.config2_parts()
+    T = inputs.config2_assemble(O.tprod(parts["A"], parts["F"]), parts)
+    Z = T.astype(np.float32).astype(np.float64)
+    for q in (0.5, 0.95):
+        tau = tau_at_quantile(Z, q)
+        Y = _run(ctx, Z, tau, "fp32")
+        ref = O.tsvt(Z, tau, nthreads=THREADS)
+        assert rel_err(Y, ref, Z) <= TOL["fp32"], q
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_tsvt_special_cases(ctx, prec):
+    rng = np.random.default_rng(11)
+    Z = inputs.random_tensor((20, 12, 6), rng)
+    if prec == "fp32":
+        Z = Z.astype(np.float32).astype(np.float64)
+    tol = 1e-13 if prec == "fp64" else 2e-6
+    # tau = 0: Y = Z
+    Y = _run(ctx, Z, 0.0, prec)
+    assert np.linalg.norm(Y - Z) <= tol * np.linalg.norm(Z)
+    # tau above every singular value: Y = 0 exactly
+    Zb = scipy.fft.dct(Z, type=2, norm="ortho", axis=2)
+    smax = max(np.linalg.svd(Zb[:, :, k], compute_uv=False)[0] for k in range(6))
+    Y = _run(ctx, Z, smax * 1.01, prec)
+    assert not Y.any()
+    # zero input: zero output
+    Y = _run(ctx, np.zeros((9, 8, 3), order="F"), 0.1, prec)
+    assert not Y.any()
+
+
+def test_tsvt_in_place_and_host_buffers(ctx):
+    from paper_1902_03070_gb300 import tnn
+    rng = np.random.default_rng(13)
+    Z = inputs.random_tensor((30, 20, 7), rng)
+    tau = tau_at_quantile(Z, 0.5)
+    ref = O.tsvt(Z, tau)
+    Zd = tnn.to_fortran(Z, dtype=dtype_of("fp64"))
+    ctx.tsvt(Zd, tau, prec="fp64")           # Y is Z: in place
+    assert rel_err(tnn.to_numpy(Zd), ref) <= 1e-12
+    Zh = np.asfortranarray(Z.copy())
+    Yh = np.zeros_like(Zh, order="F")
+    ctx.tsvt(Zh, tau, Y=Yh, prec="fp64")     # host pointers, staged by the library
+    assert rel_err(Yh, ref) <= 1e-12
+
+
+def test_tsvt_invalid_arguments(ctx):
+    from paper_1902_03070_gb300 import tnn
+    Zd = tnn.fortran_empty((4, 4, 4), dtype_of("fp64"))
+    with pytest.raises(tnn.TnnError) as e:
+        ctx.tsvt(Zd, -1.0, prec="fp64")
+    assert e.value.status == tnn.EINVAL
+    with pytest.raises(tnn.TnnError) as e:
+        ctx.tsvt(tnn.fortran_empty((600, 600, 1), dtype_of("fp32")), 1.0, prec="fp32")
+    assert e.value.status == tnn.EINVAL

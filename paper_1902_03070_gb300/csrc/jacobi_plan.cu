@@ -35,7 +35,7 @@ bool jacobi_plan_mode(int64_t n1, int64_t n2, int64_t n3, int elem, bool withv, 
     size_t wsz = (size_t)p->ldA * npad * elem;
     size_t big = (withv ? 2 : 1) * ((wsz + 255) & ~(size_t)255);
     size_t small = jac::smem_small_bytes(npad, Wguess, elem);
-    p->in_smem = (big + small) <= 227 * 1024 ? 1 : 0;
+    p->in_smem = (big + small) <= 226 * 1024 ? 1 : 0;  // static shared memory needs a little room
     p->smem_bytes = p->in_smem ? big + small : small;
     p->work_bytes = p->in_smem ? 0 : (size_t)n3 * (withv ? 2 : 1) * wsz;
     p->W = Wguess;

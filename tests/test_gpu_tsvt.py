@@ -1,7 +1,16 @@
 """GPU parity: t-SVT (Theorem 5, Algorithm 1) through the C ABI against the
-FP64 oracle.  FP64 path: relative Frobenius error <= 1e-12.  FP32 path:
-<= 1e-5, the error measured against ||Y_oracle|| (against ||Z|| when the
-oracle's Y is below 1e-6 ||Z||)."""
+FP64 oracle.
+
+FP64 path: ||Y - Y_oracle||_F <= 1e-12 ||Y_oracle||_F (||Z||_F when the
+oracle's Y is below 1e-6 ||Z||_F).
+
+FP32 path: ||Y - Y_oracle||_F <= 1e-5 ||Z||_F on every case.  The t-SVT is
+1-Lipschitz in Z, so FP32 rounding of size u ||Z|| (u = 2^-24) bounds what an
+FP32 computation can reach; relative to ||Y|| the same error grows by
+||Z|| / ||Y||.  The error relative to ||Y_oracle|| is also held to 1e-5 on the
+completion-shaped tensors and where the threshold keeps most of the energy
+(Gaussian slices, tau at the 30th-percentile singular value); with tau at the
+80th percentile (||Y|| about 0.13 ||Z||) it is held to 1e-4."""
 import numpy as np
 import pytest
 import scipy.fft
@@ -53,7 +62,13 @@ def test_tsvt_matches_oracle(ctx, prec, shape, q):
     tau = tau_at_quantile(Z, q)
     Y = _run(ctx, Z, tau, prec)
     ref = O.tsvt(Z, tau, nthreads=THREADS)
-    assert rel_err(Y, ref, Z) <= TOL[prec]
+    err_y = rel_err(Y, ref, Z)
+    if prec == "fp64":
+        assert err_y <= TOL["fp64"]
+    else:
+        err_z = np.linalg.norm(Y - ref) / np.linalg.norm(Z)
+        assert err_z <= TOL["fp32"], (err_z, err_y)
+        assert err_y <= (TOL["fp32"] if q <= 0.5 else 1e-4), (err_z, err_y)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])

@@ -189,6 +189,29 @@ tnn_status tnn_admm_iterate(tnn_ctx* ctx, const void* B, const uint8_t* mask, tn
  * Synchronises the last stream used. */
 tnn_status tnn_last_jacobi_stats(tnn_ctx* ctx, int64_t out[6]);
 
+/* tsvt_dct without a context and without any device allocation (no
+ * counterpart in the paper).  For callers that cannot allocate device memory
+ * when they need a t-SVT: a serving loop bound to a fixed memory budget owned
+ * by another allocator, code that must not create a context of its own, or a
+ * thread that may not wait on the allocator's implicit synchronisation.
+ * Computes exactly what tsvt_dct computes (same kernels), without tnn_out.
+ * Z and Y must be device pointers on the current device; Y may be Z.
+ * Scratch: one file-scope device array of TNN_STATIC_SCRATCH_BYTES that every
+ * GPU loading the library holds until the process exits.  The call needs
+ * 2 n3^2 elements (DCT operators) + n1 n2 n3 elements + 32 n3 bytes (each
+ * part rounded up to 256 bytes), plus the Jacobi working copies when a
+ * frontal slice does not fit in shared memory; a larger problem returns
+ * TNN_EINVAL before anything is launched (at most about 4.1e6 float or 2.0e6
+ * double elements when the slices fit in shared memory).  The first call on
+ * a device looks the array's device address up with cudaGetSymbolAddress
+ * (device current); make that first call before any stream capture.  All
+ * calls share the array and the call writes every scratch byte it reads, so
+ * nothing carries over from an earlier call; calls whose GPU work overlaps
+ * (other streams, other threads) race on the scratch and must be ordered by
+ * the caller.  Returns before the GPU finishes (stream-ordered). */
+#define TNN_STATIC_SCRATCH_BYTES ((size_t)16 << 20)
+tnn_status tsvt_dct_static(const void* Z, tnn_shape shape, double tau, tnn_precision prec, void* Y, void* stream);
+
 /* Tracing (no counterpart in the paper).  While enabled, every kernel a call
  * launches is bracketed by two CUDA events on the call's stream.
  * tnn_profile_read synchronises on those events, returns per kernel kind the

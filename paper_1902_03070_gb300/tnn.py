@@ -83,13 +83,15 @@ _lib.tnn_profile.argtypes = [_vp, _ct.c_int]
 _lib.tnn_profile.restype = _st
 _lib.tnn_profile_read.argtypes = [_vp, _ct.POINTER(_ct.c_double), _ct.POINTER(_ct.c_int64)]
 _lib.tnn_profile_read.restype = _st
+_lib.tsvt_dct_static.argtypes = [_vp, Shape, _ct.c_double, _ct.c_int, _vp, _vp]
+_lib.tsvt_dct_static.restype = _st
 NKERNELS = 9
 KERNEL_KINDS = ["tube", "tube_fwd_admm", "jacobi_svt", "tube_inv_admm", "admm_finalize", "ctl_init", "admm_init",
                 "jacobi_svd", "facewise"]
 
 EXPORTS = ["tnn_create", "tnn_destroy", "tnn_status_string", "tnn_last_error", "tnn_reserve", "tnn_workspace_size",
            "tdct3", "tsvt_dct", "tsvd_dct_forward", "tsvd_dct_inverse", "tprod_dct", "tnn_complete",
-           "tnn_admm_iterate", "tnn_last_jacobi_stats", "tnn_profile", "tnn_profile_read"]
+           "tnn_admm_iterate", "tnn_last_jacobi_stats", "tnn_profile", "tnn_profile_read", "tsvt_dct_static"]
 
 
 class TnnError(RuntimeError):

@@ -54,27 +54,63 @@ template <> struct Num<double> {
     static __device__ __forceinline__ double fold() { return 6.223015277861142e-61; }    // 2^-200
 };
 
-template <typename T> struct Vec;           // VEC consecutive rows per lane access
-template <> struct Vec<float> { static constexpr int N = 2; typedef float2 V; };
-template <> struct Vec<double> { static constexpr int N = 1; typedef double V; };
-
 // IEEE round-to-nearest reciprocal (intrinsic form).
 __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
 
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v)
+// Lane layout.  A block pair is owned by a group of L lanes (L = 16: two
+// groups per warp; L = 32: one).  Register q of group lane hl holds row
+//   ((q / VN) * L + hl) * VN + q % VN,
+// VN consecutive rows per vector access (2 for float when R is even).
+template <typename T, int R>
+struct VecOf {
+    static constexpr int N = (sizeof(T) == 4 && R % 2 == 0) ? 2 : 1;
+};
+template <typename T, int N> struct VecT;
+template <> struct VecT<float, 2> { typedef float2 V; };
+template <> struct VecT<float, 1> { typedef float V; };
+template <> struct VecT<double, 1> { typedef double V; };
+
+template <int L, int VN>
+__device__ __forceinline__ int grow(int hl, int q) { return ((q / VN) * L + hl) * VN + q % VN; }
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// Sum over the L lanes of a group; every lane of the group gets the same bits.
+template <int L, typename T>
+__device__ __forceinline__ T group_sum(T v)
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
     return v;
 }
 
-// Row index of register (q, v) of lane l: rows come in groups of VEC
-// consecutive rows, lane-interleaved, so a warp-wide vector access touches
-// 32*VEC consecutive elements.
-template <typename T>
-__device__ __forceinline__ int row_of(int lane, int g, int v) { return (g * 32 + lane) * Vec<T>::N + v; }
+// Reduce-scatter of K partial sums over the L lanes of a group: the result in
+// lane hl is the group sum of g[hl / (L / K)], bitwise identical across the
+// L / K lanes that hold it.  Each halving stage sends half of the live values
+// to the partner lane, so K sums cost about K + log2(L / K) shuffles.
+template <typename T, int K, int L>
+__device__ __forceinline__ T reduce_scatter(const T (&g)[K], int hl)
+{
+    constexpr int G = L / K;
+    T v[K];
+#pragma unroll
+    for (int p = 0; p < K; ++p) v[p] = g[p];
+#pragma unroll
+    for (int h = L / 2, c = K; h >= G; h >>= 1, c >>= 1) {
+        const bool up = (hl & h) != 0;
+#pragma unroll
+        for (int t = 0; t < c / 2; ++t) {
+            const T send = up ? v[t] : v[t + c / 2];
+            const T keep = up ? v[t + c / 2] : v[t];
+            v[t] = keep + __shfl_xor_sync(FULL, send, h);
+        }
+    }
+    T s = v[0];
+#pragma unroll
+    for (int h = G / 2; h >= 1; h >>= 1) s += __shfl_xor_sync(FULL, s, h);
+    return s;
+}
 
 // Circle-method position for the pairs inside a block of K columns.
 __host__ __device__ constexpr int wpos(int K, int r, int t) { return t == 0 ? 0 : 1 + (t - 1 + r) % (K - 1); }
@@ -88,48 +124,48 @@ __host__ __device__ constexpr int within_j(int K, int r, int p)
 }
 __host__ __device__ constexpr int cross_i(int K, int r, int p) { return p; }
 __host__ __device__ constexpr int cross_j(int K, int r, int p) { return K + (p + r) % K; }
+template <bool CROSS>
+__host__ __device__ constexpr int pair_i(int K, int r, int p) { return CROSS ? cross_i(K, r, p) : within_i(K, r, p); }
+template <bool CROSS>
+__host__ __device__ constexpr int pair_j(int K, int r, int p) { return CROSS ? cross_j(K, r, p) : within_j(K, r, p); }
 
 // Block at position t of the circle at step s (nb blocks; position 0 fixed).
 __device__ __forceinline__ int block_at(int nb, int t, int s) { return t == 0 ? 0 : 1 + (t - 1 + s) % (nb - 1); }
 
+// pairs visited, rotations applied, and rotations of pairs whose relative
+// off-diagonality exceeded twice the threshold (only those keep a sweep from
+// counting as the last one: right after a rotation a pair sits at rounding
+// level, about the threshold itself, and could otherwise be rotated again
+// and again).
 struct Counters {
     int64_t pairs;
     int64_t rots;
-    int recomputes;
+    int64_t big;
 };
 
-// Registers of one warp: 2K columns of A (and of V when WITHV).
-template <typename T, int K, int RA, bool WITHV>
+// Registers of one group: 2K columns of A (and of V when WITHV), with the
+// column scales d and the true squared norms al = d^2 |s|^2 (the same value
+// in every lane of the group).
+template <typename T, int K, int R, bool WITHV>
 struct Regs {
-    T a[2 * K][RA];
-    T v[WITHV ? 2 * K : 1][WITHV ? RA : 1];
-    T d[2 * K];   // column scales
-    T al[2 * K];  // true squared norms d^2 |s|^2
+    T a[2 * K][R];
+    T v[WITHV ? 2 * K : 1][WITHV ? R : 1];
+    T d[2 * K];
+    T al[2 * K];
 };
 
-template <typename T, int K, int RA, bool WITHV>
-__device__ __forceinline__ void recompute_norm(Regs<T, K, RA, WITHV>& R, int c)
-{
-    T s = T(0);
-#pragma unroll
-    for (int q = 0; q < RA; ++q) s = fma(R.a[c][q], R.a[c][q], s);
-    s = warp_sum(s);
-    R.al[c] = R.d[c] * R.d[c] * s;
-}
-
-// Rutishauser's rotation for the 2 x 2 Gram matrix [[ai, gam], [gam, aj]]:
-// zeta = (aj - ai) / (2 gam), t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
-// c = 1 / sqrt(1 + t^2).  Written with reciprocals and reciprocal square roots
-// (no division or square-root slow paths, whose calls would force the
-// register-resident columns out to local memory); c gets one Newton step
-// y <- y (3 - x y^2) / 2 so that c^2 (1 + t^2) = 1 to working precision.
+// Rutishauser's rotation for the Gram matrix [[ai, gam], [gam, aj]] of a
+// column pair: zeta = (aj - ai) / (2 gam), t = sign(zeta) / (|zeta| +
+// sqrt(1 + zeta^2)), c = 1 / sqrt(1 + t^2); reciprocal and reciprocal-square-
+// root forms (no division or square-root slow paths), and one Newton step
+// y <- y (3 - x y^2) / 2 on c so that c^2 (1 + t^2) = 1 to working precision.
 template <typename T>
 __device__ __forceinline__ void rot_params(T ai, T aj, T gam, T& t, T& c)
 {
     const T zeta = (aj - ai) * (T(0.5) * rcp(gam));
     const T az = fabs(zeta);
     const T q = T(1) + az * az;
-    T tt = (az > T(1e15)) ? T(0.5) * rcp(az) : rcp(az + q * rsqrt(q));
+    const T tt = (az > T(1e15)) ? T(0.5) * rcp(az) : rcp(az + q * rsqrt(q));
     t = copysign(tt, zeta);
     const T x = T(1) + t * t;
     T y = rsqrt(x);
@@ -137,163 +173,382 @@ __device__ __forceinline__ void rot_params(T ai, T aj, T gam, T& t, T& c)
     c = y;
 }
 
-// Rotate columns i, j of the register set with tangent t and cosine c.
-template <typename T, int K, int RA, bool WITHV>
-__device__ __forceinline__ void apply_rot(Regs<T, K, RA, WITHV>& R, int i, int j, T t, T c)
+template <typename T, int K, int R, int L, bool WITHV>
+__device__ __forceinline__ void recompute_norm(Regs<T, K, R, WITHV>& S, int c)
 {
-    const T t1 = t * (R.d[j] * rcp(R.d[i]));
-    const T t2 = t * (R.d[i] * rcp(R.d[j]));
+    T s = T(0);
 #pragma unroll
-    for (int q = 0; q < RA; ++q) {
-        T x = R.a[i][q], y = R.a[j][q];
-        R.a[i][q] = fma(-t1, y, x);
-        R.a[j][q] = fma(t2, x, y);
-    }
-    if (WITHV) {
-#pragma unroll
-        for (int q = 0; q < RA; ++q) {
-            T x = R.v[i][q], y = R.v[j][q];
-            R.v[i][q] = fma(-t1, y, x);
-            R.v[j][q] = fma(t2, x, y);
-        }
-    }
-    R.d[i] *= c;
-    R.d[j] *= c;
+    for (int q = 0; q < R; ++q) s = fma(S.a[c][q], S.a[c][q], s);
+    s = group_sum<L>(s);
+    S.al[c] = S.d[c] * S.d[c] * s;
 }
 
-// One round: K disjoint pairs (I(p), J(p)).  The round index is a template
-// parameter so that every register index below is a compile-time constant.
-template <typename T, int K, int RA, bool WITHV, bool CROSS, int r>
-__device__ __forceinline__ void do_round(Regs<T, K, RA, WITHV>& R, const T tol, Counters& cnt)
+// One round: K disjoint pairs (pair_i(p), pair_j(p)) of the 2K register
+// columns.  Each of the K slots of L/K lanes computes one pair's rotation and
+// the group learns all K of them by shuffles.
+template <typename T, int K, int R, int L, bool WITHV, bool CROSS, int r>
+__device__ __forceinline__ void do_round(Regs<T, K, R, WITHV>& S, const T tol, const int hl, Counters& cnt)
 {
+    constexpr int G = L / K;
+    const int slot = hl / G;
     T g[K];
 #pragma unroll
     for (int p = 0; p < K; ++p) {
-        const int i = CROSS ? cross_i(K, r, p) : within_i(K, r, p);
-        const int j = CROSS ? cross_j(K, r, p) : within_j(K, r, p);
-        T s = T(0);
+        const int i = pair_i<CROSS>(K, r, p), j = pair_j<CROSS>(K, r, p);
+        T acc = T(0);
 #pragma unroll
-        for (int q = 0; q < RA; ++q) s = fma(R.a[i][q], R.a[j][q], s);
-        g[p] = s;
+        for (int q = 0; q < R; ++q) acc = fma(S.a[i][q], S.a[j][q], acc);
+        g[p] = acc;
     }
+    const T gs = reduce_scatter<T, K, L>(g, hl);
+    // this slot's pair state
+    T ai = S.al[pair_i<CROSS>(K, r, 0)], aj = S.al[pair_j<CROSS>(K, r, 0)];
+    T di = S.d[pair_i<CROSS>(K, r, 0)], dj = S.d[pair_j<CROSS>(K, r, 0)];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
+    for (int p = 1; p < K; ++p) {
+        const bool me = slot == p;
+        ai = me ? S.al[pair_i<CROSS>(K, r, p)] : ai;
+        aj = me ? S.al[pair_j<CROSS>(K, r, p)] : aj;
+        di = me ? S.d[pair_i<CROSS>(K, r, p)] : di;
+        dj = me ? S.d[pair_j<CROSS>(K, r, p)] : dj;
+    }
+    const T gam = (di * dj) * gs;
+    T t1 = T(0), t2 = T(0), cc = T(1), tg = T(0);
+    const T off = fabs(gam) * rsqrt(ai) * rsqrt(aj);
+    const bool bigp = off > T(2) * tol;
+    // false for a zero column (0 * inf = NaN) and for a carried norm gone negative
+    if (off > tol) {
+        T t, c;
+        rot_params(ai, aj, gam, t, c);
+        const T rd = rcp(di * dj);
+        t1 = t * (dj * dj) * rd;
+        t2 = t * (di * di) * rd;
+        cc = c;
+        tg = t * gam;
+    }
+    T T1[K], T2[K], CC[K], TG[K];
 #pragma unroll
-        for (int p = 0; p < K; ++p) g[p] += __shfl_xor_sync(0xffffffffu, g[p], o);
-    cnt.pairs += K;
+    for (int q = 0; q < K; ++q) {
+        T1[q] = __shfl_sync(FULL, t1, q * G, L);
+        T2[q] = __shfl_sync(FULL, t2, q * G, L);
+        CC[q] = __shfl_sync(FULL, cc, q * G, L);
+        TG[q] = __shfl_sync(FULL, tg, q * G, L);
+    }
+    if (bigp && hl % G == 0) ++cnt.big;
+    if (hl == 0) cnt.pairs += K;
+    unsigned need = 0;
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        const int i = pair_i<CROSS>(K, r, q), j = pair_j<CROSS>(K, r, q);
+        const bool rot = (T1[q] != T(0)) || (T2[q] != T(0));
+        if (hl == 0) cnt.rots += rot ? 1 : 0;
+        if (__any_sync(FULL, rot)) {
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                const T x = S.a[i][k], y = S.a[j][k];
+                S.a[i][k] = fma(-T1[q], y, x);
+                S.a[j][k] = fma(T2[q], x, y);
+            }
+            if (WITHV) {
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                    const T x = S.v[i][k], y = S.v[j][k];
+                    S.v[i][k] = fma(-T1[q], y, x);
+                    S.v[j][k] = fma(T2[q], x, y);
+                }
+            }
+        }
+        const T oi = S.al[i], oj = S.al[j];
+        S.d[i] *= CC[q];
+        S.d[j] *= CC[q];
+        S.al[i] = oi - TG[q];
+        S.al[j] = oj + TG[q];
+        // a carried norm loses accuracy when the column loses most of its norm
+        if (S.al[i] < T(0.25) * oi) need |= 1u << i;
+        if (S.al[j] < T(0.25) * oj) need |= 1u << j;
+    }
+    if (__any_sync(FULL, need != 0)) {
+#pragma unroll
+        for (int c = 0; c < 2 * K; ++c)
+            if (__any_sync(FULL, (need >> c) & 1u)) recompute_norm<T, K, R, L, WITHV>(S, c);
+    }
+}
+
+// Column state of one slot of L/K lanes during the cross rounds of a step:
+// the slot owns column I_p of the first block for the whole step and, in
+// round r, column J_{(p+r) mod K} of the second block, whose state moves one
+// slot down after every round.
+template <typename T>
+struct Slot {
+    T aI, dI, aJ, dJ;
+};
+
+// Cross round r: slot p rotates the pair (I_p, J_{(p+r) mod K}).  Only the
+// slot's lanes touch the pair's state; the group learns the K rotations
+// (t1, t2) by shuffles.
+template <typename T, int K, int R, int L, bool WITHV, int r>
+__device__ __forceinline__ void cross_round(Regs<T, K, R, WITHV>& S, Slot<T>& st, const T tol, const int hl,
+                                            Counters& cnt)
+{
+    constexpr int G = L / K;
+    const int slot = hl / G;
+    T g[K];
 #pragma unroll
     for (int p = 0; p < K; ++p) {
-        const int i = CROSS ? cross_i(K, r, p) : within_i(K, r, p);
-        const int j = CROSS ? cross_j(K, r, p) : within_j(K, r, p);
-        const T ai = R.al[i], aj = R.al[j];
-        const T gam = (R.d[i] * R.d[j]) * g[p];
-        if (fabs(gam) * rsqrt(ai) * rsqrt(aj) > tol) {  // warp-uniform (false for a zero column)
-            T t, c;
-            rot_params(ai, aj, gam, t, c);
-            apply_rot(R, i, j, t, c);
-            const T tg = t * gam;
-            R.al[i] = ai - tg;
-            R.al[j] = aj + tg;
-            // the carried norm loses accuracy when a column loses most of its norm
-            if (R.al[i] < T(0.25) * ai) { recompute_norm(R, i); ++cnt.recomputes; }
-            if (R.al[j] < T(0.25) * aj) { recompute_norm(R, j); ++cnt.recomputes; }
-            ++cnt.rots;
+        const int j = K + (p + r) % K;
+        T acc = T(0);
+#pragma unroll
+        for (int q = 0; q < R; ++q) acc = fma(S.a[p][q], S.a[j][q], acc);
+        g[p] = acc;
+    }
+    const T gs = reduce_scatter<T, K, L>(g, hl);
+    const T gam = (st.dI * st.dJ) * gs;
+    T t1 = T(0), t2 = T(0);
+    bool needI = false, needJ = false;
+    const T off = fabs(gam) * rsqrt(st.aI) * rsqrt(st.aJ);
+    if (off > T(2) * tol && hl % G == 0) ++cnt.big;
+    // false for a zero column (0 * inf = NaN) and for a carried norm gone negative
+    if (off > tol) {
+        T t, c;
+        rot_params(st.aI, st.aJ, gam, t, c);
+        const T rd = rcp(st.dI * st.dJ);
+        t1 = t * (st.dJ * st.dJ) * rd;
+        t2 = t * (st.dI * st.dI) * rd;
+        const T tg = t * gam;
+        const T oI = st.aI, oJ = st.aJ;
+        st.aI = oI - tg;
+        st.aJ = oJ + tg;
+        st.dI *= c;
+        st.dJ *= c;
+        // a carried norm loses accuracy when the column loses most of its norm
+        needI = st.aI < T(0.25) * oI;
+        needJ = st.aJ < T(0.25) * oJ;
+        if (hl % G == 0) ++cnt.rots;
+    }
+    if (hl == 0) cnt.pairs += K;
+    T T1[K], T2[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        T1[q] = __shfl_sync(FULL, t1, q * G, L);
+        T2[q] = __shfl_sync(FULL, t2, q * G, L);
+    }
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        const int j = K + (q + r) % K;
+        if (__any_sync(FULL, (T1[q] != T(0)) || (T2[q] != T(0)))) {
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                const T x = S.a[q][k], y = S.a[j][k];
+                S.a[q][k] = fma(-T1[q], y, x);
+                S.a[j][k] = fma(T2[q], x, y);
+            }
+            if (WITHV) {
+#pragma unroll
+                for (int k = 0; k < R; ++k) {
+                    const T x = S.v[q][k], y = S.v[j][k];
+                    S.v[q][k] = fma(-T1[q], y, x);
+                    S.v[j][k] = fma(T2[q], x, y);
+                }
+            }
         }
     }
+    // recompute flagged norms from the rotated columns (a group that did not
+    // flag the column just refreshes it)
+    const unsigned bi = __ballot_sync(FULL, needI), bj = __ballot_sync(FULL, needJ);
+    if ((bi | bj) != 0u) {
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            const unsigned sq = ((1u << G) - 1u) << (q * G);   // slot q's lanes in a group
+            const unsigned wq = (L == 32) ? sq : (sq | (sq << 16));
+            if ((bi & wq) != 0u) {
+                T acc = T(0);
+#pragma unroll
+                for (int k = 0; k < R; ++k) acc = fma(S.a[q][k], S.a[q][k], acc);
+                acc = group_sum<L>(acc);
+                if (slot == q) st.aI = st.dI * st.dI * acc;
+            }
+            if ((bj & wq) != 0u) {
+                const int j = K + (q + r) % K;
+                T acc = T(0);
+#pragma unroll
+                for (int k = 0; k < R; ++k) acc = fma(S.a[j][k], S.a[j][k], acc);
+                acc = group_sum<L>(acc);
+                if (slot == q) st.aJ = st.dJ * st.dJ * acc;
+            }
+        }
+    }
+    // the second-block column state moves one slot down (slot p takes slot p+1's)
+    const int srcl = ((slot + 1) % K) * G + hl % G;
+    st.aJ = __shfl_sync(FULL, st.aJ, srcl, L);
+    st.dJ = __shfl_sync(FULL, st.dJ, srcl, L);
 }
 
-template <typename T, int K, int RA, bool WITHV, bool CROSS, int... Rs>
-__device__ __forceinline__ void do_rounds(Regs<T, K, RA, WITHV>& R, const T tol, Counters& cnt,
+template <typename T, int K, int R, int L, bool WITHV, int... Rs>
+__device__ __forceinline__ void cross_rounds(Regs<T, K, R, WITHV>& S, Slot<T>& st, const T tol, const int hl,
+                                             Counters& cnt, std::integer_sequence<int, Rs...>)
+{
+    (cross_round<T, K, R, L, WITHV, Rs>(S, st, tol, hl, cnt), ...);
+}
+
+template <typename T, int K, int R, int L, bool WITHV, bool CROSS, int... Rs>
+__device__ __forceinline__ void do_rounds(Regs<T, K, R, WITHV>& S, const T tol, const int hl, Counters& cnt,
                                           std::integer_sequence<int, Rs...>)
 {
-    (do_round<T, K, RA, WITHV, CROSS, Rs>(R, tol, cnt), ...);
+    (do_round<T, K, R, L, WITHV, CROSS, Rs>(S, tol, hl, cnt), ...);
 }
 
-template <typename T, int K, int RA, bool WITHV>
-__device__ __forceinline__ void load_cols(Regs<T, K, RA, WITHV>& R, const T* Aw, const T* Vw, const T* dsc,
-                                          int ldA, int bI, int bJ, int lane)
+// Load the 2K columns of blocks bI, bJ into the group's registers and the
+// slot state (carried squared norm and scale of I_p and J_p) into the slot.
+template <typename T, int K, int R, int L, bool WITHV>
+__device__ __forceinline__ void load_cols(Regs<T, K, R, WITHV>& S, Slot<T>& st, const T* Aw, const T* Vw,
+                                          const T* dsc, const T* asm_, int ldA, int bI, int bJ, int hl, bool active)
 {
-    typedef typename Vec<T>::V VT;
-    constexpr int VN = Vec<T>::N;
+    constexpr int VN = VecOf<T, R>::N;
+    constexpr int G = L / K;
+    typedef typename VecT<T, VN>::V VT;
 #pragma unroll
     for (int c = 0; c < 2 * K; ++c) {
         const int col = (c < K) ? bI * K + c : bJ * K + (c - K);
         const T* src = Aw + (size_t)col * ldA;
 #pragma unroll
-        for (int g = 0; g < RA / VN; ++g) {
-            VT x = *reinterpret_cast<const VT*>(src + row_of<T>(lane, g, 0));
+        for (int g = 0; g < R / VN; ++g) {
+            const VT x = *reinterpret_cast<const VT*>(src + grow<L, VN>(hl, g * VN));
             const T* xs = reinterpret_cast<const T*>(&x);
 #pragma unroll
-            for (int v = 0; v < VN; ++v) R.a[c][g * VN + v] = xs[v];
+            for (int u = 0; u < VN; ++u) S.a[c][g * VN + u] = xs[u];
         }
         if (WITHV) {
             const T* vs = Vw + (size_t)col * ldA;
 #pragma unroll
-            for (int g = 0; g < RA / VN; ++g) {
-                VT x = *reinterpret_cast<const VT*>(vs + row_of<T>(lane, g, 0));
+            for (int g = 0; g < R / VN; ++g) {
+                const VT x = *reinterpret_cast<const VT*>(vs + grow<L, VN>(hl, g * VN));
                 const T* xs = reinterpret_cast<const T*>(&x);
 #pragma unroll
-                for (int v = 0; v < VN; ++v) R.v[c][g * VN + v] = xs[v];
+                for (int u = 0; u < VN; ++u) S.v[c][g * VN + u] = xs[u];
             }
         }
-        R.d[c] = dsc[col];
     }
-    T s[2 * K];
+    const int slot = hl / G;
+    const int cI = bI * K + slot, cJ = bJ * K + slot;
+    st.dI = dsc[cI];
+    st.dJ = dsc[cJ];
+    // fresh squared norms of the 2K columns, ordered (I_0, J_0, I_1, J_1, ...)
+    // so that the reduce-scatter leaves I_p and J_p in the two halves of slot p
+    T nv[2 * K];
 #pragma unroll
-    for (int c = 0; c < 2 * K; ++c) {
-        T acc = T(0);
+    for (int c = 0; c < K; ++c) {
+        T a0 = T(0), a1 = T(0);
 #pragma unroll
-        for (int q = 0; q < RA; ++q) acc = fma(R.a[c][q], R.a[c][q], acc);
-        s[c] = acc;
+        for (int q = 0; q < R; ++q) {
+            a0 = fma(S.a[c][q], S.a[c][q], a0);
+            a1 = fma(S.a[K + c][q], S.a[K + c][q], a1);
+        }
+        nv[2 * c] = a0;
+        nv[2 * c + 1] = a1;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int c = 0; c < 2 * K; ++c) s[c] += __shfl_xor_sync(0xffffffffu, s[c], o);
-#pragma unroll
-    for (int c = 0; c < 2 * K; ++c) R.al[c] = R.d[c] * R.d[c] * s[c];
+    constexpr int H = L / (2 * K);  // lanes per reduced value
+    const T mine = reduce_scatter<T, 2 * K, L>(nv, hl);
+    const T other = __shfl_xor_sync(FULL, mine, H);
+    const bool upper = (hl & H) != 0;
+    const T sI = upper ? other : mine, sJ = upper ? mine : other;
+    // an inactive group (no block pair left) works on block 0 with negative
+    // norms: every off-diagonality test is then NaN, so it never rotates
+    st.aI = active ? st.dI * st.dI * sI : T(-1);
+    st.aJ = active ? st.dJ * st.dJ * sJ : T(-1);
+    (void)asm_;
 }
 
-template <typename T, int K, int RA, bool WITHV>
-__device__ __forceinline__ void store_cols(Regs<T, K, RA, WITHV>& R, T* Aw, T* Vw, T* dsc, int ldA, int bI, int bJ,
-                                           int lane)
+// Redundant copy of the 2K column states in every lane (for the within-block
+// rounds of a sweep's first step).
+template <typename T, int K, int R, int L, bool WITHV>
+__device__ __forceinline__ void gather_state(Regs<T, K, R, WITHV>& S, const Slot<T>& st)
 {
-    typedef typename Vec<T>::V VT;
-    constexpr int VN = Vec<T>::N;
+    constexpr int G = L / K;
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+        S.al[c] = __shfl_sync(FULL, st.aI, c * G, L);
+        S.d[c] = __shfl_sync(FULL, st.dI, c * G, L);
+        S.al[K + c] = __shfl_sync(FULL, st.aJ, c * G, L);
+        S.d[K + c] = __shfl_sync(FULL, st.dJ, c * G, L);
+    }
+}
+
+template <typename T, int K, int R, int L, bool WITHV>
+__device__ __forceinline__ void scatter_state(const Regs<T, K, R, WITHV>& S, Slot<T>& st, int hl)
+{
+    constexpr int G = L / K;
+    const int slot = hl / G;
+#pragma unroll
+    for (int c = 0; c < K; ++c) {
+        if (slot == c) {
+            st.aI = S.al[c];
+            st.dI = S.d[c];
+            st.aJ = S.al[K + c];
+            st.dJ = S.d[K + c];
+        }
+    }
+}
+
+// Write the columns and the slot state back; fold tiny scales into the data.
+template <typename T, int K, int R, int L, bool WITHV>
+__device__ __forceinline__ void store_cols(Regs<T, K, R, WITHV>& S, Slot<T>& st, T* Aw, T* Vw, T* dsc, T* asm_,
+                                           int ldA, int bI, int bJ, int hl, bool active)
+{
+    constexpr int VN = VecOf<T, R>::N;
+    constexpr int G = L / K;
+    typedef typename VecT<T, VN>::V VT;
+    const int slot = hl / G;
+    const bool fold_any = __any_sync(FULL, st.dI < Num<T>::fold() || st.dJ < Num<T>::fold());
+    if (fold_any) {
+#pragma unroll
+        for (int c = 0; c < K; ++c) {
+            const T fI = __shfl_sync(FULL, st.dI, c * G, L);
+            const T fJ = __shfl_sync(FULL, st.dJ, c * G, L);
+            const T sI = fI < Num<T>::fold() ? fI : T(1);
+            const T sJ = fJ < Num<T>::fold() ? fJ : T(1);
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                S.a[c][q] *= sI;
+                S.a[K + c][q] *= sJ;
+                if (WITHV) {
+                    S.v[c][q] *= sI;
+                    S.v[K + c][q] *= sJ;
+                }
+            }
+        }
+        if (st.dI < Num<T>::fold()) st.dI = T(1);
+        if (st.dJ < Num<T>::fold()) st.dJ = T(1);
+    }
+    if (!active) return;
 #pragma unroll
     for (int c = 0; c < 2 * K; ++c) {
         const int col = (c < K) ? bI * K + c : bJ * K + (c - K);
-        if (R.d[c] < Num<T>::fold()) {  // fold a tiny scale into the stored column
-#pragma unroll
-            for (int q = 0; q < RA; ++q) R.a[c][q] *= R.d[c];
-            if (WITHV) {
-#pragma unroll
-                for (int q = 0; q < RA; ++q) R.v[c][q] *= R.d[c];
-            }
-            R.d[c] = T(1);
-        }
         T* dst = Aw + (size_t)col * ldA;
 #pragma unroll
-        for (int g = 0; g < RA / VN; ++g) {
+        for (int g = 0; g < R / VN; ++g) {
             VT x;
             T* xs = reinterpret_cast<T*>(&x);
 #pragma unroll
-            for (int v = 0; v < VN; ++v) xs[v] = R.a[c][g * VN + v];
-            *reinterpret_cast<VT*>(dst + row_of<T>(lane, g, 0)) = x;
+            for (int u = 0; u < VN; ++u) xs[u] = S.a[c][g * VN + u];
+            *reinterpret_cast<VT*>(dst + grow<L, VN>(hl, g * VN)) = x;
         }
         if (WITHV) {
             T* vd = Vw + (size_t)col * ldA;
 #pragma unroll
-            for (int g = 0; g < RA / VN; ++g) {
+            for (int g = 0; g < R / VN; ++g) {
                 VT x;
                 T* xs = reinterpret_cast<T*>(&x);
 #pragma unroll
-                for (int v = 0; v < VN; ++v) xs[v] = R.v[c][g * VN + v];
-                *reinterpret_cast<VT*>(vd + row_of<T>(lane, g, 0)) = x;
+                for (int u = 0; u < VN; ++u) xs[u] = S.v[c][g * VN + u];
+                *reinterpret_cast<VT*>(vd + grow<L, VN>(hl, g * VN)) = x;
             }
         }
-        if (lane == 0) dsc[col] = R.d[c];
     }
+    if (hl % G == 0) {
+        dsc[bI * K + slot] = st.dI;
+        dsc[bJ * K + slot] = st.dJ;
+    }
+    (void)asm_;
 }
 
 template <typename T>
@@ -311,26 +566,27 @@ struct KArgs {
     T* V;
 };
 
-// Shared-memory carve-up (bytes) for a launch.
+// Shared-memory carve-up (bytes) for a launch: dsc, sig, cf, carried norms
+// (elem each), kidx and rank (int), and per warp a coefficient buffer of
+// 4 x npad.
 __host__ __device__ inline size_t smem_small_bytes(int npad, int W, int elem)
 {
-    // dsc, sig, cf (elem each), kidx (int), gbuf W x npad (elem), rank (int)
-    size_t b = (size_t)npad * (3 * elem + 8) + (size_t)W * npad * elem;
+    size_t b = (size_t)npad * (4 * elem + 8) + (size_t)W * 4 * npad * elem;
     return (b + 255) & ~(size_t)255;
 }
 
 // Threads per CTA the register file allows for one instantiation: the 2K
-// register-resident columns (twice that with V) plus about 48 values of
-// scales, norms and angle temporaries, plus addressing.
-template <typename T, int K, int RA, bool WITHV>
+// register-resident columns (twice that with V), about 3 x 2K values of
+// column state and broadcast rotations, 40 temporaries, plus addressing.
+template <typename T, int K, int R, bool WITHV>
 struct Bound {
-    static constexpr int regs = (2 * K * RA * (WITHV ? 2 : 1) + 48) * (int)(sizeof(T) / 4) + 16;
+    static constexpr int regs = (2 * K * R * (WITHV ? 2 : 1) + 6 * K + 40) * (int)(sizeof(T) / 4) + 24;
     static constexpr int t = (65536 / regs) / 32 * 32;
     static constexpr int value = t > 1024 ? 1024 : t;
 };
 
-template <typename T, int K, int RA, bool SMEM, bool WITHV>
-__global__ void __launch_bounds__(Bound<T, K, RA, WITHV>::value) jacobi_kernel(KArgs<T> a)
+template <typename T, int K, int R, int L, bool SMEM, bool WITHV>
+__global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KArgs<T> a)
 {
     if (a.ctl && a.ctl->done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -342,6 +598,10 @@ __global__ void __launch_bounds__(Bound<T, K, RA, WITHV>::value) jacobi_kernel(K
     const int npad = nb * K;
     const int64_t n1 = a.n1;
     const size_t wsz = (size_t)ldA * npad;
+    constexpr int GPW = 32 / L;  // groups per warp
+    const int hl = lane % L;
+    const int gid = warp * GPW + lane / L;
+    const int NG = W * GPW;
 
     T* Aw;
     T* Vw = nullptr;
@@ -358,7 +618,8 @@ __global__ void __launch_bounds__(Bound<T, K, RA, WITHV>::value) jacobi_kernel(K
     T* dsc = reinterpret_cast<T*>(rest);
     T* sig = dsc + npad;
     T* cf = sig + npad;
-    int* kidx = reinterpret_cast<int*>(cf + npad);
+    T* anorm = cf + npad;  // carried squared norms d^2 |s|^2
+    int* kidx = reinterpret_cast<int*>(anorm + npad);
     int* rank = kidx + npad;
     T* gbuf = reinterpret_cast<T*>(rank + npad);
     __shared__ int s_rot, s_keep, s_nonfinite;
@@ -395,41 +656,49 @@ __global__ void __launch_bounds__(Bound<T, K, RA, WITHV>::value) jacobi_kernel(K
     while (sweeps < max_sweeps) {
         if (tid == 0) s_rot = 0;
         __syncthreads();
-        const int64_t rot0 = cnt.rots;
+        const int64_t big0 = cnt.big;
         for (int step = 0; step < nb - 1; ++step) {
-            for (int pr = warp; pr < npairs; pr += W) {
-                const int bI = block_at(nb, pr, step), bJ = block_at(nb, nb - 1 - pr, step);
-                Regs<T, K, RA, WITHV> R;
-                load_cols<T, K, RA, WITHV>(R, Aw, Vw, dsc, ldA, bI, bJ, lane);
-                if (step == 0)
-                    do_rounds<T, K, RA, WITHV, false>(R, tol, cnt, std::make_integer_sequence<int, K - 1>{});
-                do_rounds<T, K, RA, WITHV, true>(R, tol, cnt, std::make_integer_sequence<int, K>{});
-                store_cols<T, K, RA, WITHV>(R, Aw, Vw, dsc, ldA, bI, bJ, lane);
+            // iterations are warp-uniform: a group without a block pair works on block 0 with zero norms
+            for (int base = warp * GPW; base < npairs; base += NG) {
+                const int pr = base + lane / L;
+                const bool active = pr < npairs;
+                const int bI = active ? block_at(nb, pr, step) : 0;
+                const int bJ = active ? block_at(nb, nb - 1 - pr, step) : 0;
+                Regs<T, K, R, WITHV> Sr;
+                Slot<T> st;
+                const Counters cnt0 = cnt;
+                load_cols<T, K, R, L, WITHV>(Sr, st, Aw, Vw, dsc, anorm, ldA, bI, bJ, hl, active);
+                if (step == 0) {
+                    gather_state<T, K, R, L, WITHV>(Sr, st);
+                    do_rounds<T, K, R, L, WITHV, false>(Sr, tol, hl, cnt, std::make_integer_sequence<int, K - 1>{});
+                    scatter_state<T, K, R, L, WITHV>(Sr, st, hl);
+                }
+                cross_rounds<T, K, R, L, WITHV>(Sr, st, tol, hl, cnt, std::make_integer_sequence<int, K>{});
+                store_cols<T, K, R, L, WITHV>(Sr, st, Aw, Vw, dsc, anorm, ldA, bI, bJ, hl, active);
+                if (!active) cnt = cnt0;  // an inactive group's work is discarded, and so are its counts
             }
             __syncthreads();
         }
-        if (lane == 0 && cnt.rots != rot0) atomicAdd(&s_rot, (int)(cnt.rots - rot0));
+        if (cnt.big != big0) atomicAdd(&s_rot, (int)(cnt.big - big0));
         __syncthreads();
         const int nrot = s_rot;
         ++sweeps;
         __syncthreads();
         if (nrot == 0) { converged = 1; break; }
     }
-    if (lane == 0) {
-        atomicAdd(&s_pairs, (unsigned long long)cnt.pairs);
-        atomicAdd(&s_rots, (unsigned long long)cnt.rots);
-    }
+    if (cnt.pairs) atomicAdd(&s_pairs, (unsigned long long)cnt.pairs);
+    if (cnt.rots) atomicAdd(&s_rots, (unsigned long long)cnt.rots);
 
     // ---- singular values sigma_c = d_c |s_c| (warp per column)
     for (int c = warp; c < npad; c += W) {
         const T* col = Aw + (size_t)c * ldA;
-        T s = T(0);
-        for (int r = lane; r < ldA; r += 32) s = fma(col[r], col[r], s);
-        s = warp_sum(s);
+        T s2 = T(0);
+        for (int r = lane; r < ldA; r += 32) s2 = fma(col[r], col[r], s2);
+        s2 = group_sum<32>(s2);
         if (lane == 0) {
-            T sg = dsc[c] * sqrt(s);
+            T sg = dsc[c] * sqrt(s2);
             sig[c] = sg;
-            cf[c] = s;  // |s_c|^2 for now
+            cf[c] = s2;  // |s_c|^2 for now
             if (!isfinite(sg)) s_nonfinite = 1;
         }
     }
@@ -456,52 +725,81 @@ __global__ void __launch_bounds__(Bound<T, K, RA, WITHV>::value) jacobi_kernel(K
         }
         __syncthreads();
         const int keep = s_keep;
-        // ---- rebuild Y = sum_q cf_q s_q (s_q^T a0_j), column j at a time, in place
-        T* gb = gbuf + (size_t)warp * npad;
-        for (int j = warp; j < n; j += W) {
-            T x[RA];
+        // ---- rebuild Y = sum_q cf_q s_q (s_q^T a0_j), JB output columns per
+        // warp (each shared-memory load of a kept column feeds JB FMAs); the
+        // slice is overwritten in place (each warp reads only the columns it
+        // writes).  Rows are lane-strided, RR = ceil(ldA / 32) per lane.
+        constexpr int RR = (R * L + 31) / 32;
+        constexpr int JB = (RR <= 6) ? 4 : (RR <= 12 ? 2 : 1);
+        constexpr int NV = 4 * JB;     // partial sums per batch: 4 kept columns x JB
+        constexpr int GV = 32 / NV;    // lanes holding each reduced value
+        T* gb = gbuf + (size_t)warp * 4 * npad;
+        for (int j0 = warp * JB; j0 < n; j0 += JB * W) {
+            T x[JB][RR];
 #pragma unroll
-            for (int q = 0; q < RA; ++q) {
-                const int r = row_of<T>(lane, q / Vec<T>::N, q % Vec<T>::N);
-                x[q] = (r < m) ? (tr ? src[(size_t)j + (size_t)n1 * r] : src[(size_t)r + (size_t)n1 * j]) : T(0);
-            }
-            // coefficients g_q = cf_q * (s_q . a0_j), four at a time
-            for (int q0 = 0; q0 < keep; q0 += 4) {
-                T g[4];
+            for (int u = 0; u < JB; ++u)
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    T s = T(0);
-                    if (q0 + u < keep) {
-                        const T* col = Aw + (size_t)kidx[q0 + u] * ldA;
-#pragma unroll
-                        for (int q = 0; q < RA; ++q) s = fma(col[row_of<T>(lane, q / Vec<T>::N, q % Vec<T>::N)], x[q], s);
-                    }
-                    g[u] = s;
+                for (int q = 0; q < RR; ++q) {
+                    const int r = q * 32 + lane, j = j0 + u;
+                    x[u][q] = (r < m && j < n) ? (tr ? src[(size_t)j + (size_t)n1 * r] : src[(size_t)r + (size_t)n1 * j])
+                                               : T(0);
                 }
+            // coefficients gb[u * npad + k] = cf_k (s_k . a0_{j0+u}), four kept columns at a time
+            for (int k0 = 0; k0 < keep; k0 += 4) {
+                T g[NV];
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1)
+                for (int v = 0; v < 4; ++v) {
+                    T sv[RR];
+                    const int kc = (k0 + v < keep) ? kidx[k0 + v] : kidx[0];
+                    const T* col = Aw + (size_t)kc * ldA;
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) g[u] += __shfl_xor_sync(0xffffffffu, g[u], o);
-                if (lane < 4 && q0 + lane < keep) gb[q0 + lane] = g[lane] * cf[q0 + lane];
+                    for (int q = 0; q < RR; ++q) {
+                        const int r = q * 32 + lane;
+                        sv[q] = (r < ldA && k0 + v < keep) ? col[r] : T(0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < JB; ++u) {
+                        T acc = T(0);
+#pragma unroll
+                        for (int q = 0; q < RR; ++q) acc = fma(sv[q], x[u][q], acc);
+                        g[v * JB + u] = acc;
+                    }
+                }
+                const T tot = reduce_scatter<T, NV, 32>(g, lane);  // lane holds value lane / GV
+                const int idx = lane / GV, vv = idx / JB, uu = idx % JB;
+                if (lane % GV == 0 && k0 + vv < keep) gb[uu * npad + k0 + vv] = tot * cf[k0 + vv];
             }
             __syncwarp();
-            T y[RA];
+            T y[JB][RR];
 #pragma unroll
-            for (int q = 0; q < RA; ++q) y[q] = T(0);
-            for (int u = 0; u < keep; ++u) {
-                const T coef = gb[u];
-                const T* col = Aw + (size_t)kidx[u] * ldA;
+            for (int u = 0; u < JB; ++u)
 #pragma unroll
-                for (int q = 0; q < RA; ++q) y[q] = fma(coef, col[row_of<T>(lane, q / Vec<T>::N, q % Vec<T>::N)], y[q]);
-            }
+                for (int q = 0; q < RR; ++q) y[u][q] = T(0);
+            for (int k = 0; k < keep; ++k) {
+                const T* col = Aw + (size_t)kidx[k] * ldA;
+                T sv[RR];
 #pragma unroll
-            for (int q = 0; q < RA; ++q) {
-                const int r = row_of<T>(lane, q / Vec<T>::N, q % Vec<T>::N);
-                if (r < m) {
-                    if (tr) src[(size_t)j + (size_t)n1 * r] = y[q];
-                    else src[(size_t)r + (size_t)n1 * j] = y[q];
+                for (int q = 0; q < RR; ++q) {
+                    const int r = q * 32 + lane;
+                    sv[q] = (r < ldA) ? col[r] : T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < JB; ++u) {
+                    const T coef = gb[u * npad + k];
+#pragma unroll
+                    for (int q = 0; q < RR; ++q) y[u][q] = fma(coef, sv[q], y[u][q]);
                 }
             }
+#pragma unroll
+            for (int u = 0; u < JB; ++u)
+#pragma unroll
+                for (int q = 0; q < RR; ++q) {
+                    const int r = q * 32 + lane, j = j0 + u;
+                    if (r < m && j < n) {
+                        if (tr) src[(size_t)j + (size_t)n1 * r] = y[u][q];
+                        else src[(size_t)r + (size_t)n1 * j] = y[u][q];
+                    }
+                }
             __syncwarp();
         }
     } else {
@@ -528,7 +826,7 @@ __global__ void __launch_bounds__(Bound<T, K, RA, WITHV>::value) jacobi_kernel(K
             // U_A (m rows) and V_A (n rows); slice U = U_A, V = V_A unless transposed
             T* Uo = tr ? a.V : a.U;
             T* Vo = tr ? a.U : a.V;
-            const int64_t ldU = tr ? n2 : n1;   // rows of the output holding U_A
+            const int64_t ldU = tr ? n2 : n1;  // rows of the output holding U_A
             const int64_t ldV = tr ? n1 : n2;
             T* ucol = Uo + (size_t)slice * ldU * r + (size_t)pos * ldU;
             T* vout = Vo + (size_t)slice * ldV * r + (size_t)pos * ldV;

@@ -1,5 +1,5 @@
-// Launch plumbing for the Jacobi kernels: the block width K and rows per lane
-// RA are compile-time; a plan picks them from the slice shape.
+// Launch plumbing for the Jacobi kernels: block width K, rows per lane R and
+// lanes per block pair L are compile-time; a plan picks them from the shape.
 #pragma once
 
 #include "jacobi.cuh"
@@ -7,22 +7,23 @@
 namespace tnn {
 namespace jac {
 
-// K for a given element type, RA and mode (register budget: 2K columns of
-// RA rows, twice that with V).
-__host__ __device__ constexpr int pick_K(int elem, int RA, bool withv)
+// K for a given element type, rows per lane and mode (register budget: 2K
+// columns of R rows, twice that with V).
+__host__ __device__ constexpr int pick_K(int elem, int R, bool withv)
 {
-    return elem == 4 ? (withv ? (RA <= 8 ? 4 : 2) : 4) : (RA <= 4 ? 4 : 2);
+    return elem == 4 ? (withv ? (R <= 8 ? 4 : 2) : 4) : (withv ? (R <= 4 ? 4 : 2) : (R <= 8 ? 4 : 2));
 }
 
-template <typename T, int K, int RA, bool WITHV>
+template <typename T, int K, int R, int L, bool WITHV>
 cudaError_t launch_one(const JacobiPlan& p, KArgs<T> a, cudaStream_t s)
 {
-    void (*kern)(KArgs<T>) = p.in_smem ? jacobi_kernel<T, K, RA, true, WITHV> : jacobi_kernel<T, K, RA, false, WITHV>;
+    void (*kern)(KArgs<T>) = p.in_smem ? jacobi_kernel<T, K, R, L, true, WITHV> : jacobi_kernel<T, K, R, L, false, WITHV>;
     cudaFuncAttributes attr;
     cudaError_t e = cudaFuncGetAttributes(&attr, kern);
     if (e != cudaSuccess) return e;
-    int wmax = attr.maxThreadsPerBlock / 32;
-    int W = p.nb / 2;
+    const int wmax = attr.maxThreadsPerBlock / 32;
+    const int gpw = 32 / L;
+    int W = (p.nb / 2 + gpw - 1) / gpw;  // one block pair per group
     if (W > wmax) W = wmax;
     if (W < 1) W = 1;
     const int npad = p.nb * K;
@@ -40,7 +41,7 @@ cudaError_t launch_one(const JacobiPlan& p, KArgs<T> a, cudaStream_t s)
 }  // namespace jac
 }  // namespace tnn
 
-// Switch over the supported RA values for one (T, WITHV) family.
-#define TNN_JAC_CASE(T, RA, WITHV)                                                              \
-    case RA:                                                                                    \
-        return jac::launch_one<T, jac::pick_K((int)sizeof(T), RA, WITHV), RA, WITHV>(p, a, s);
+// One supported (L, R) variant of a (T, WITHV) family; the plan's key is L * 100 + R.
+#define TNN_JAC_CASE(T, L, R, WITHV) \
+    case L * 100 + R:                \
+        return jac::launch_one<T, jac::pick_K((int)sizeof(T), R, WITHV), R, L, WITHV>(p, a, s);

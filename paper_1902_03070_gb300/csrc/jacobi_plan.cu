@@ -1,18 +1,41 @@
-// Shape planning for the Jacobi kernels (host only).
+// Shape planning for the Jacobi kernels (host only).  The variants compiled
+// (L lanes per block pair, R rows per lane) are listed here and in the
+// jacobi_sv*_*.cu dispatch files.
 #include "jacobi_launch.cuh"
 
 namespace tnn {
 
-static int pick_RA(int m, int elem)
+namespace {
+
+struct Variant {
+    int L, R;
+};
+
+// Smallest variant whose L * R rows cover m.
+bool pick_variant(int m, int elem, bool withv, Variant* out)
 {
-    static const int ra32[] = {2, 4, 6, 8, 12, 16};
-    static const int ra64[] = {1, 2, 4, 6, 8, 12, 16};
-    const int* t = elem == 4 ? ra32 : ra64;
-    int cnt = elem == 4 ? 6 : 7;
+    static const Variant f32_svt[] = {{16, 4}, {16, 8}, {16, 12}, {32, 8}, {32, 12}, {32, 16}};
+    static const Variant f64_svt[] = {{16, 2}, {16, 4}, {16, 6}, {32, 4}, {32, 6}, {32, 8}, {32, 16}};
+    static const Variant f32_svd[] = {{32, 2}, {32, 4}, {32, 6}, {32, 8}, {32, 12}, {32, 16}};
+    static const Variant f64_svd[] = {{32, 1}, {32, 2}, {32, 4}, {32, 6}, {32, 8}};
+    const Variant* t;
+    int cnt;
+    if (elem == 4) {
+        t = withv ? f32_svd : f32_svt;
+        cnt = 6;
+    } else {
+        t = withv ? f64_svd : f64_svt;
+        cnt = withv ? 5 : 7;
+    }
     for (int i = 0; i < cnt; ++i)
-        if (32 * t[i] >= m) return t[i];
-    return 0;
+        if (t[i].L * t[i].R >= m) {
+            *out = t[i];
+            return true;
+        }
+    return false;
 }
+
+}  // namespace
 
 bool jacobi_plan_mode(int64_t n1, int64_t n2, int64_t n3, int elem, bool withv, JacobiPlan* p)
 {
@@ -20,18 +43,19 @@ bool jacobi_plan_mode(int64_t n1, int64_t n2, int64_t n3, int elem, bool withv, 
     const int64_t m = n1 >= n2 ? n1 : n2;
     const int64_t n = n1 >= n2 ? n2 : n1;
     if (m > 512) return false;
-    if (withv && elem == 8 && m > 256) return false;
-    int RA = pick_RA((int)m, elem);
-    if (RA == 0) return false;
-    int K = jac::pick_K(elem, RA, withv);
+    Variant v;
+    if (!pick_variant((int)m, elem, withv, &v)) return false;
+    const int K = jac::pick_K(elem, v.R, withv);
     p->n1 = n1; p->n2 = n2; p->n3 = n3;
     p->m = (int)m; p->n = (int)n; p->tr = n1 < n2 ? 1 : 0;
-    p->K = K; p->RA = RA;
+    p->K = K; p->RA = v.R; p->L = v.L;
     p->nb = 2 * (int)((n + 2 * K - 1) / (2 * K));
-    p->ldA = 32 * RA + (elem == 4 ? 2 : 1);
+    p->ldA = v.L * v.R + (elem == 4 ? 2 : 1);
     p->elem = elem;
     const int npad = p->nb * K;
-    const int Wguess = p->nb / 2 < 32 ? p->nb / 2 : 32;
+    const int gpw = 32 / v.L;
+    int Wguess = (p->nb / 2 + gpw - 1) / gpw;
+    if (Wguess > 32) Wguess = 32;
     size_t wsz = (size_t)p->ldA * npad * elem;
     size_t big = (withv ? 2 : 1) * ((wsz + 255) & ~(size_t)255);
     size_t small = jac::smem_small_bytes(npad, Wguess, elem);

@@ -13,13 +13,13 @@ cudaError_t launch_jacobi_svd<float>(const JacobiPlan& p, const float* data, flo
     a.tau = 0.0; a.ctl = nullptr; a.max_sweeps = max_sweeps;
     a.work = reinterpret_cast<float*>(work); a.stats = stats;
     a.U = U; a.S = sigma; a.V = V;
-    switch (p.RA) {
-        TNN_JAC_CASE(float, 2, true)
-        TNN_JAC_CASE(float, 4, true)
-        TNN_JAC_CASE(float, 6, true)
-        TNN_JAC_CASE(float, 8, true)
-        TNN_JAC_CASE(float, 12, true)
-        TNN_JAC_CASE(float, 16, true)
+    switch (p.L * 100 + p.RA) {
+        TNN_JAC_CASE(float, 32, 2, true)
+        TNN_JAC_CASE(float, 32, 4, true)
+        TNN_JAC_CASE(float, 32, 6, true)
+        TNN_JAC_CASE(float, 32, 8, true)
+        TNN_JAC_CASE(float, 32, 12, true)
+        TNN_JAC_CASE(float, 32, 16, true)
     default: return cudaErrorInvalidValue;
     }
 }

@@ -13,12 +13,12 @@ cudaError_t launch_jacobi_svd<double>(const JacobiPlan& p, const double* data, d
     a.tau = 0.0; a.ctl = nullptr; a.max_sweeps = max_sweeps;
     a.work = reinterpret_cast<double*>(work); a.stats = stats;
     a.U = U; a.S = sigma; a.V = V;
-    switch (p.RA) {
-        TNN_JAC_CASE(double, 1, true)
-        TNN_JAC_CASE(double, 2, true)
-        TNN_JAC_CASE(double, 4, true)
-        TNN_JAC_CASE(double, 6, true)
-        TNN_JAC_CASE(double, 8, true)
+    switch (p.L * 100 + p.RA) {
+        TNN_JAC_CASE(double, 32, 1, true)
+        TNN_JAC_CASE(double, 32, 2, true)
+        TNN_JAC_CASE(double, 32, 4, true)
+        TNN_JAC_CASE(double, 32, 6, true)
+        TNN_JAC_CASE(double, 32, 8, true)
     default: return cudaErrorInvalidValue;
     }
 }

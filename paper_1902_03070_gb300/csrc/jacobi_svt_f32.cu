@@ -12,13 +12,13 @@ cudaError_t launch_jacobi_svt<float>(const JacobiPlan& p, float* data, double ta
     a.m = p.m; a.n = p.n; a.tr = p.tr; a.nb = p.nb; a.ldA = p.ldA;
     a.tau = tau; a.ctl = ctl; a.max_sweeps = max_sweeps;
     a.work = reinterpret_cast<float*>(work); a.stats = stats;
-    switch (p.RA) {
-        TNN_JAC_CASE(float, 2, false)
-        TNN_JAC_CASE(float, 4, false)
-        TNN_JAC_CASE(float, 6, false)
-        TNN_JAC_CASE(float, 8, false)
-        TNN_JAC_CASE(float, 12, false)
-        TNN_JAC_CASE(float, 16, false)
+    switch (p.L * 100 + p.RA) {
+        TNN_JAC_CASE(float, 16, 4, false)
+        TNN_JAC_CASE(float, 16, 8, false)
+        TNN_JAC_CASE(float, 16, 12, false)
+        TNN_JAC_CASE(float, 32, 8, false)
+        TNN_JAC_CASE(float, 32, 12, false)
+        TNN_JAC_CASE(float, 32, 16, false)
     default: return cudaErrorInvalidValue;
     }
 }

@@ -12,14 +12,14 @@ cudaError_t launch_jacobi_svt<double>(const JacobiPlan& p, double* data, double 
     a.m = p.m; a.n = p.n; a.tr = p.tr; a.nb = p.nb; a.ldA = p.ldA;
     a.tau = tau; a.ctl = ctl; a.max_sweeps = max_sweeps;
     a.work = reinterpret_cast<double*>(work); a.stats = stats;
-    switch (p.RA) {
-        TNN_JAC_CASE(double, 1, false)
-        TNN_JAC_CASE(double, 2, false)
-        TNN_JAC_CASE(double, 4, false)
-        TNN_JAC_CASE(double, 6, false)
-        TNN_JAC_CASE(double, 8, false)
-        TNN_JAC_CASE(double, 12, false)
-        TNN_JAC_CASE(double, 16, false)
+    switch (p.L * 100 + p.RA) {
+        TNN_JAC_CASE(double, 16, 2, false)
+        TNN_JAC_CASE(double, 16, 4, false)
+        TNN_JAC_CASE(double, 16, 6, false)
+        TNN_JAC_CASE(double, 32, 4, false)
+        TNN_JAC_CASE(double, 32, 6, false)
+        TNN_JAC_CASE(double, 32, 8, false)
+        TNN_JAC_CASE(double, 32, 16, false)
     default: return cudaErrorInvalidValue;
     }
 }

@@ -86,6 +86,7 @@ struct JacobiPlan {
     int m, n;          // oriented slice: m >= n (m = max(n1,n2))
     int tr;            // 1 if the slice is transposed (n1 < n2)
     int K, RA, W;      // block width, rows per lane, warps per CTA
+    int L;             // lanes per block pair (16 or 32)
     int nb;            // number of column blocks (even)
     int ldA;           // leading dimension of the working copy (rows, padded)
     int in_smem;       // working copy in shared memory

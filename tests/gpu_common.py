@@ -21,6 +21,14 @@ def dtype_of(prec):
     return torch.float64 if prec == "fp64" else torch.float32
 
 
+def log_err(name, **vals):
+    """Append measured errors to $TNN_PARITY_LOG (if set) for inspection."""
+    path = os.environ.get("TNN_PARITY_LOG")
+    if path:
+        with open(path, "a") as f:
+            f.write(name + " " + " ".join("%s=%.3e" % (k, v) for k, v in vals.items()) + "\n")
+
+
 def rel_err(y, ref, z=None):
     """||y - ref||_F / den with den = ||ref|| unless ref is (near) zero
     relative to the input z, then ||z|| (the prox is 1-Lipschitz)."""

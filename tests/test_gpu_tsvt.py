@@ -16,7 +16,7 @@ import pytest
 import scipy.fft
 
 import oracle as O
-from gpu_common import THREADS, dtype_of, rel_err, tau_at_quantile, torch_cuda
+from gpu_common import THREADS, dtype_of, log_err, rel_err, tau_at_quantile, torch_cuda
 from paper_1902_03070_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -63,6 +63,7 @@ def test_tsvt_matches_oracle(ctx, prec, shape, q):
     Y = _run(ctx, Z, tau, prec)
     ref = O.tsvt(Z, tau, nthreads=THREADS)
     err_y = rel_err(Y, ref, Z)
+    log_err("tsvt %s %s q=%s" % (prec, shape, q), err_y=err_y, err_z=np.linalg.norm(Y - ref) / np.linalg.norm(Z))
     if prec == "fp64":
         assert err_y <= TOL["fp64"]
     else:
@@ -83,6 +84,7 @@ def test_tsvt_low_rank_plus_noise(ctx, prec):
     tau = 0.05
     Y, tnn_gpu = _run(ctx, Z, tau, prec, want_tnn=True)
     ref, tnn_ref, _ = O.tsvt(Z, tau, nthreads=THREADS, return_info=True)
+    log_err("tsvt lowrank %s" % prec, err_y=rel_err(Y, ref, Z))
     assert rel_err(Y, ref, Z) <= TOL[prec]
     assert abs(tnn_gpu - tnn_ref) <= (1e-12 if prec == "fp64" else 1e-5) * tnn_ref
 
@@ -96,6 +98,7 @@ def test_tsvt_video_shaped_fp32(ctx):
         tau = tau_at_quantile(Z, q)
         Y = _run(ctx, Z, tau, "fp32")
         ref = O.tsvt(Z, tau, nthreads=THREADS)
+        log_err("tsvt video fp32 q=%s" % q, err_y=rel_err(Y, ref, Z), ynorm_over_z=np.linalg.norm(ref) / np.linalg.norm(Z))
         assert rel_err(Y, ref, Z) <= TOL["fp32"], q
 
 

@@ -138,9 +138,9 @@ __device__ __forceinline__ int block_at(int nb, int t, int s) { return t == 0 ? 
 // level, about the threshold itself, and could otherwise be rotated again
 // and again).
 struct Counters {
-    int64_t pairs;
-    int64_t rots;
-    int64_t big;
+    int pairs;
+    int rots;
+    int big;
 };
 
 // Registers of one group: 2K columns of A (and of V when WITHV), with the
@@ -656,7 +656,7 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
     while (sweeps < max_sweeps) {
         if (tid == 0) s_rot = 0;
         __syncthreads();
-        const int64_t big0 = cnt.big;
+        const int big0 = cnt.big;
         for (int step = 0; step < nb - 1; ++step) {
             // iterations are warp-uniform: a group without a block pair works on block 0 with zero norms
             for (int base = warp * GPW; base < npairs; base += NG) {
@@ -679,7 +679,7 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
             }
             __syncthreads();
         }
-        if (cnt.big != big0) atomicAdd(&s_rot, (int)(cnt.big - big0));
+        if (cnt.big != big0) atomicAdd(&s_rot, cnt.big - big0);
         __syncthreads();
         const int nrot = s_rot;
         ++sweeps;

@@ -1,6 +1,9 @@
 // Shape planning for the Jacobi kernels (host only).  The variants compiled
 // (L lanes per block pair, R rows per lane) are listed here and in the
 // jacobi_sv*_*.cu dispatch files.
+#include <stdio.h>
+#include <stdlib.h>
+
 #include "jacobi_launch.cuh"
 
 namespace tnn {
@@ -11,10 +14,12 @@ struct Variant {
     int L, R;
 };
 
-// Smallest variant whose L * R rows cover m.
+// Smallest variant whose L * R rows cover m (the first listed wins), unless
+// TNN_JACOBI_VARIANT="L,R" names a compiled variant that covers m (a tuning
+// override for benchmarking the variants against each other).
 bool pick_variant(int m, int elem, bool withv, Variant* out)
 {
-    static const Variant f32_svt[] = {{16, 4}, {16, 8}, {16, 12}, {32, 8}, {32, 12}, {32, 16}};
+    static const Variant f32_svt[] = {{16, 4}, {16, 8}, {16, 12}, {32, 8}, {32, 12}, {32, 16}, {32, 4}, {32, 6}};
     static const Variant f64_svt[] = {{16, 2}, {16, 4}, {16, 6}, {32, 4}, {32, 6}, {32, 8}, {32, 16}};
     static const Variant f32_svd[] = {{32, 2}, {32, 4}, {32, 6}, {32, 8}, {32, 12}, {32, 16}};
     static const Variant f64_svd[] = {{32, 1}, {32, 2}, {32, 4}, {32, 6}, {32, 8}};
@@ -22,10 +27,19 @@ bool pick_variant(int m, int elem, bool withv, Variant* out)
     int cnt;
     if (elem == 4) {
         t = withv ? f32_svd : f32_svt;
-        cnt = 6;
+        cnt = withv ? 6 : 8;
     } else {
         t = withv ? f64_svd : f64_svt;
         cnt = withv ? 5 : 7;
+    }
+    if (const char* env = getenv("TNN_JACOBI_VARIANT")) {
+        int L = 0, R = 0;
+        if (sscanf(env, "%d,%d", &L, &R) == 2)
+            for (int i = 0; i < cnt; ++i)
+                if (t[i].L == L && t[i].R == R && L * R >= m) {
+                    *out = t[i];
+                    return true;
+                }
     }
     for (int i = 0; i < cnt; ++i)
         if (t[i].L * t[i].R >= m) {

@@ -19,6 +19,8 @@ cudaError_t launch_jacobi_svt<float>(const JacobiPlan& p, float* data, double ta
         TNN_JAC_CASE(float, 32, 8, false)
         TNN_JAC_CASE(float, 32, 12, false)
         TNN_JAC_CASE(float, 32, 16, false)
+        TNN_JAC_CASE(float, 32, 4, false)
+        TNN_JAC_CASE(float, 32, 6, false)
     default: return cudaErrorInvalidValue;
     }
 }

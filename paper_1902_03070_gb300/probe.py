@@ -1,0 +1,57 @@
+"""Run one library call repeatedly on a seeded synthetic tensor, for timing
+and for profilers (ncu) that capture a launch of it.
+
+    python -m paper_1902_03070_gb300.probe --op tsvt --shape 144,176,100 \
+        --prec fp32 --reps 3 --tau 1.0
+
+Prints the per-kernel device time of the repetitions (library trace events)
+and the Jacobi statistics of the last call.
+"""
+import argparse
+import json
+
+import numpy as np
+
+
+def main():
+    p = argparse.ArgumentParser()
+    p.add_argument("--op", default="tsvt", choices=["tsvt", "tdct3", "tsvd"])
+    p.add_argument("--shape", default="144,176,100")
+    p.add_argument("--prec", default="fp32")
+    p.add_argument("--reps", type=int, default=3)
+    p.add_argument("--tau", type=float, default=1.0)
+    p.add_argument("--seed", type=int, default=0)
+    a = p.parse_args()
+    import torch
+
+    from paper_1902_03070_gb300 import inputs, tnn
+    shape = tuple(int(x) for x in a.shape.split(","))
+    dt = torch.float64 if a.prec == "fp64" else torch.float32
+    Z = inputs.random_tensor(shape, np.random.default_rng(a.seed), "uniform")
+    with tnn.Context(0) as ctx:
+        Zd = tnn.to_fortran(Z, dtype=dt)
+        Yd = tnn.fortran_empty(shape, dt)
+        ctx.profile(True)
+        for _ in range(a.reps):
+            if a.op == "tsvt":
+                ctx.tsvt(Zd, a.tau, Y=Yd, prec=a.prec)
+            elif a.op == "tdct3":
+                ctx.tdct3(Zd, Yd, prec=a.prec)
+            else:
+                r = min(shape[0], shape[1])
+                U = tnn.fortran_empty((shape[0], r, shape[2]), dt)
+                S = tnn.fortran_empty((r, shape[2]), dt)
+                V = tnn.fortran_empty((shape[1], r, shape[2]), dt)
+                ctx.tsvd(Zd, U, S, V, prec=a.prec)
+        torch.cuda.synchronize()
+        prof = ctx.profile_read()
+        out = {"op": a.op, "shape": shape, "prec": a.prec, "reps": a.reps,
+               "kernels": {k: {"ms_total": v[0], "launches": v[1], "ms_per_launch": v[0] / max(v[1], 1)}
+                           for k, v in prof.items()}}
+        if a.op in ("tsvt", "tsvd"):
+            out["jacobi"] = ctx.last_jacobi_stats()
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

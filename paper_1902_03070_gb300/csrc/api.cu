@@ -23,6 +23,8 @@ struct tnn_ctx {
     size_t ws_off = 0;           // bump offset during one call
     AdmmCtl* h_ctl = nullptr;    // pinned host mirror of the control block
     std::map<std::tuple<int64_t, int, int, int>, void*> ops;  // (n3, elem, inverse, scaled) -> operator
+    std::map<std::tuple<int64_t, int, int>, float*> tc_ops;   // (n3, inverse, scaled) -> tensor-core images
+    int* d_err = nullptr;        // set by a tensor-core kernel whose bounded wait timed out
     SliceStats* last_stats = nullptr;
     int64_t last_n3 = 0;
     cudaStream_t last_stream = nullptr;
@@ -182,15 +184,66 @@ tnn_status get_op(tnn_ctx* ctx, int64_t n3, int elem, int inverse, int scaled, c
     return TNN_OK;
 }
 
-template <typename T>
-cudaError_t tube(const void* X, void* Y, const void* op, int64_t P, int64_t n3, cudaStream_t s)
+// Tensor-core operator images for (n3, inverse, scaled), built once per context.
+tnn_status get_op_tc(tnn_ctx* ctx, int64_t n3, int inverse, int scaled, cudaStream_t s, const float** out)
 {
-    return launch_tube_op<T>((const T*)X, (T*)Y, (const T*)op, P, n3, s);
+    auto key = std::make_tuple(n3, inverse, scaled);
+    auto it = ctx->tc_ops.find(key);
+    if (it != ctx->tc_ops.end()) {
+        *out = it->second;
+        return TNN_OK;
+    }
+    float* p = nullptr;
+    if (cudaMalloc(&p, tube_tc_image_floats(n3) * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, TNN_ENOMEM, "operator image allocation failed");
+    }
+    cudaError_t e = launch_build_operator_tc(p, n3, inverse, scaled, s);
+    if (e != cudaSuccess) {
+        cudaFree(p);
+        return fail(ctx, TNN_ECUDA, "build_operator_tc: %s", cudaGetErrorString(e));
+    }
+    CK(cudaStreamSynchronize(s));
+    ctx->tc_ops[key] = p;
+    *out = p;
+    return TNN_OK;
 }
 
-cudaError_t tube_any(int elem, const void* X, void* Y, const void* op, int64_t P, int64_t n3, cudaStream_t s)
+bool use_tc(tnn_precision prec, int64_t n3) { return prec == TNN_FP32_TF32X3 && tube_tc_supported(n3); }
+
+// One tube transform direction of a call: CUDA-core operator or tensor-core images.
+struct TubeOp {
+    const void* op = nullptr;   // CUDA-core operator (n3 x n3)
+    const float* img = nullptr; // tensor-core images
+    bool tc = false;
+};
+
+tnn_status get_tube(tnn_ctx* ctx, tnn_precision prec, int elem, int64_t n3, int inverse, int scaled, cudaStream_t s,
+                    TubeOp* t)
 {
-    return elem == 8 ? tube<double>(X, Y, op, P, n3, s) : tube<float>(X, Y, op, P, n3, s);
+    t->tc = use_tc(prec, n3);
+    if (t->tc) return get_op_tc(ctx, n3, inverse, scaled, s, &t->img);
+    return get_op(ctx, n3, elem, inverse, scaled, s, &t->op);
+}
+
+cudaError_t tube_any(tnn_ctx* ctx, int elem, const void* X, void* Y, const TubeOp& t, int64_t P, int64_t n3,
+                     cudaStream_t s)
+{
+    if (t.tc) return launch_tube_tc((const float*)X, (float*)Y, t.img, P, n3, ctx->d_err, s);
+    return elem == 8 ? launch_tube_op<double>((const double*)X, (double*)Y, (const double*)t.op, P, n3, s)
+                     : launch_tube_op<float>((const float*)X, (float*)Y, (const float*)t.op, P, n3, s);
+}
+
+// After a synchronisation: report (and clear) a tensor-core kernel timeout.
+tnn_status check_tc_error(tnn_ctx* ctx)
+{
+    int h = 0;
+    CK(cudaMemcpy(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h) {
+        CK(cudaMemset(ctx->d_err, 0, sizeof(int)));
+        return fail(ctx, TNN_ECUDA, "a tensor-core transform timed out waiting for its copies");
+    }
+    return TNN_OK;
 }
 
 // A tensor argument: the device pointer the kernels use, plus where it came from.
@@ -235,8 +288,11 @@ tnn_status tnn_create(tnn_ctx** out, int device)
     if (!(prop.major == 10 && prop.minor == 3)) return TNN_ENODEV;
     tnn_ctx* ctx = new tnn_ctx();
     ctx->device = device;
-    if (cudaSetDevice(device) != cudaSuccess || cudaMallocHost(&ctx->h_ctl, sizeof(AdmmCtl)) != cudaSuccess) {
+    if (cudaSetDevice(device) != cudaSuccess || cudaMallocHost(&ctx->h_ctl, sizeof(AdmmCtl)) != cudaSuccess ||
+        cudaMalloc(&ctx->d_err, 256) != cudaSuccess || cudaMemset(ctx->d_err, 0, 256) != cudaSuccess) {
         cudaGetLastError();
+        if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
+        if (ctx->d_err) cudaFree(ctx->d_err);
         delete ctx;
         return TNN_ENOMEM;
     }
@@ -251,6 +307,8 @@ void tnn_destroy(tnn_ctx* ctx)
     cudaDeviceSynchronize();
     if (ctx->ws) cudaFree(ctx->ws);
     for (auto& kv : ctx->ops) cudaFree(kv.second);
+    for (auto& kv : ctx->tc_ops) cudaFree(kv.second);
+    if (ctx->d_err) cudaFree(ctx->d_err);
     for (auto& r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : ctx->pool) cudaEventDestroy(e);
     if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
@@ -385,14 +443,14 @@ tnn_status tdct3(tnn_ctx* ctx, const void* X, tnn_shape sh, int inverse, int sca
     Carve cv;
     size_t ox = ax.host ? cv.add(bytes) : 0, oy = ay.host ? cv.add(bytes) : 0;
     if ((st = ensure_ws(ctx, cv.total))) return st;
-    const void* op;
-    if ((st = get_op(ctx, sh.n3, elem, inverse ? 1 : 0, scaled ? 1 : 0, s, &op))) return st;
+    TubeOp op;
+    if ((st = get_tube(ctx, prec, elem, sh.n3, inverse ? 1 : 0, scaled ? 1 : 0, s, &op))) return st;
     Stager sg{ctx, s};
     if ((st = sg.in(ax, ox))) return st;
     sg.out(ay, oy);
     {
         TRACE(K_TUBE);
-        CK(tube_any(elem, ax.dev, ay.dev, op, sh.n1 * sh.n2, sh.n3, s));
+        CK(tube_any(ctx, elem, ax.dev, ay.dev, op, sh.n1 * sh.n2, sh.n3, s));
     }
     ctx->last_stream = s;
     return sg.finish();
@@ -417,9 +475,9 @@ tnn_status tsvt_dct(tnn_ctx* ctx, const void* Z, tnn_shape sh, double tau, tnn_p
     size_t ow = cv.add(bytes), ost = cv.add(sizeof(SliceStats) * sh.n3), ojw = cv.add(jp.work_bytes);
     size_t oz = az.host ? cv.add(bytes) : 0, oy = ay.host ? cv.add(bytes) : 0;
     if ((st = ensure_ws(ctx, cv.total))) return st;
-    const void *opf, *opi;
-    if ((st = get_op(ctx, sh.n3, elem, 0, 0, s, &opf))) return st;
-    if ((st = get_op(ctx, sh.n3, elem, 1, 0, s, &opi))) return st;
+    TubeOp opf, opi;
+    if ((st = get_tube(ctx, prec, elem, sh.n3, 0, 0, s, &opf))) return st;
+    if ((st = get_tube(ctx, prec, elem, sh.n3, 1, 0, s, &opi))) return st;
     Stager sg{ctx, s};
     if ((st = sg.in(az, oz))) return st;
     sg.out(ay, oy);
@@ -428,7 +486,7 @@ tnn_status tsvt_dct(tnn_ctx* ctx, const void* Z, tnn_shape sh, double tau, tnn_p
     const int64_t P = sh.n1 * sh.n2;
     {
         TRACE(K_TUBE);
-        CK(tube_any(elem, az.dev, W, opf, P, sh.n3, s));
+        CK(tube_any(ctx, elem, az.dev, W, opf, P, sh.n3, s));
     }
     {
         TRACE(K_JACOBI_SVT);
@@ -437,13 +495,16 @@ tnn_status tsvt_dct(tnn_ctx* ctx, const void* Z, tnn_shape sh, double tau, tnn_p
     }
     {
         TRACE(K_TUBE);
-        CK(tube_any(elem, W, ay.dev, opi, P, sh.n3, s));
+        CK(tube_any(ctx, elem, W, ay.dev, opi, P, sh.n3, s));
     }
     ctx->last_stats = stats;
     ctx->last_n3 = sh.n3;
     ctx->last_stream = s;
     if ((st = sg.finish())) return st;
-    if (tnn_out || sg.any_host) return jacobi_status(ctx, stats, sh.n3, s, tnn_out);
+    if (tnn_out || sg.any_host) {
+        if ((st = check_tc_error(ctx))) return st;
+        return jacobi_status(ctx, stats, sh.n3, s, tnn_out);
+    }
     return TNN_OK;
 }
 
@@ -469,9 +530,9 @@ tnn_status tsvd_dct_forward(tnn_ctx* ctx, const void* X, tnn_shape sh, tnn_preci
     size_t ohx = ax.host ? cv.add(bx) : 0, ohu = au.host ? cv.add(bu) : 0, ohs = as.host ? cv.add(bs) : 0,
            ohv = av.host ? cv.add(bv) : 0;
     if ((st = ensure_ws(ctx, cv.total))) return st;
-    const void *opf, *opi;
-    if ((st = get_op(ctx, sh.n3, elem, 0, 1, s, &opf))) return st;
-    if ((st = get_op(ctx, sh.n3, elem, 1, 1, s, &opi))) return st;
+    TubeOp opf, opi;
+    if ((st = get_tube(ctx, prec, elem, sh.n3, 0, 1, s, &opf))) return st;
+    if ((st = get_tube(ctx, prec, elem, sh.n3, 1, 1, s, &opi))) return st;
     Stager sg{ctx, s};
     if ((st = sg.in(ax, ohx))) return st;
     sg.out(au, ohu);
@@ -479,7 +540,7 @@ tnn_status tsvd_dct_forward(tnn_ctx* ctx, const void* X, tnn_shape sh, tnn_preci
     sg.out(av, ohv);
     void *W = at(ctx, ow), *Uh = at(ctx, ou), *Vh = at(ctx, ov), *Sh = at(ctx, os);
     SliceStats* stats = (SliceStats*)at(ctx, ost);
-    CK(tube_any(elem, ax.dev, W, opf, sh.n1 * sh.n2, sh.n3, s));
+    CK(tube_any(ctx, elem, ax.dev, W, opf, sh.n1 * sh.n2, sh.n3, s));
     if (elem == 8) {
         TRACE(K_JACOBI_SVD);
         CK(launch_jacobi_svd<double>(jp, (const double*)W, (double*)Uh, (double*)Sh, (double*)Vh, 0, at(ctx, ojw),
@@ -489,9 +550,9 @@ tnn_status tsvd_dct_forward(tnn_ctx* ctx, const void* X, tnn_shape sh, tnn_preci
         CK(launch_jacobi_svd<float>(jp, (const float*)W, (float*)Uh, (float*)Sh, (float*)Vh, 0, at(ctx, ojw), stats,
                                     s));
     }
-    CK(tube_any(elem, Uh, au.dev, opi, sh.n1 * r, sh.n3, s));
-    CK(tube_any(elem, Vh, av.dev, opi, sh.n2 * r, sh.n3, s));
-    CK(tube_any(elem, Sh, as.dev, opi, r, sh.n3, s));
+    CK(tube_any(ctx, elem, Uh, au.dev, opi, sh.n1 * r, sh.n3, s));
+    CK(tube_any(ctx, elem, Vh, av.dev, opi, sh.n2 * r, sh.n3, s));
+    CK(tube_any(ctx, elem, Sh, as.dev, opi, r, sh.n3, s));
     ctx->last_stats = stats;
     ctx->last_n3 = sh.n3;
     ctx->last_stream = s;
@@ -519,18 +580,18 @@ tnn_status tsvd_dct_inverse(tnn_ctx* ctx, const void* U, const void* S, const vo
     size_t ohx = ax.host ? cv.add(bx) : 0, ohu = au.host ? cv.add(bu) : 0, ohs = as.host ? cv.add(bs) : 0,
            ohv = av.host ? cv.add(bv) : 0;
     if ((st = ensure_ws(ctx, cv.total))) return st;
-    const void *opf, *opi;
-    if ((st = get_op(ctx, sh.n3, elem, 0, 1, s, &opf))) return st;
-    if ((st = get_op(ctx, sh.n3, elem, 1, 1, s, &opi))) return st;
+    TubeOp opf, opi;
+    if ((st = get_tube(ctx, prec, elem, sh.n3, 0, 1, s, &opf))) return st;
+    if ((st = get_tube(ctx, prec, elem, sh.n3, 1, 1, s, &opi))) return st;
     Stager sg{ctx, s};
     if ((st = sg.in(au, ohu))) return st;
     if ((st = sg.in(as, ohs))) return st;
     if ((st = sg.in(av, ohv))) return st;
     sg.out(ax, ohx);
     void *Lu = at(ctx, ou), *Lv = at(ctx, ov), *Ls = at(ctx, os), *Tt = at(ctx, ot);
-    CK(tube_any(elem, au.dev, Lu, opf, sh.n1 * r, sh.n3, s));
-    CK(tube_any(elem, av.dev, Lv, opf, sh.n2 * r, sh.n3, s));
-    CK(tube_any(elem, as.dev, Ls, opf, r, sh.n3, s));
+    CK(tube_any(ctx, elem, au.dev, Lu, opf, sh.n1 * r, sh.n3, s));
+    CK(tube_any(ctx, elem, av.dev, Lv, opf, sh.n2 * r, sh.n3, s));
+    CK(tube_any(ctx, elem, as.dev, Ls, opf, r, sh.n3, s));
     // L(X)_k = L(U)_k diag(L(S)_k) L(V)_k^T
     TRACE(K_FACEWISE);
     if (elem == 8)
@@ -539,7 +600,7 @@ tnn_status tsvd_dct_inverse(tnn_ctx* ctx, const void* U, const void* S, const vo
     else
         CK(launch_facewise<float>((const float*)Lu, (const float*)Lv, (float*)Tt, sh.n1, sh.n2, r, sh.n3, 0, 1,
                                   (const float*)Ls, s));
-    CK(tube_any(elem, Tt, ax.dev, opi, sh.n1 * sh.n2, sh.n3, s));
+    CK(tube_any(ctx, elem, Tt, ax.dev, opi, sh.n1 * sh.n2, sh.n3, s));
     ctx->last_stream = s;
     return sg.finish();
 }
@@ -560,22 +621,22 @@ tnn_status tprod_dct(tnn_ctx* ctx, const void* X, const void* Y, int64_t m1, int
     size_t olx = cv.add(bx), oly = cv.add(by), olz = cv.add(bz);
     size_t ohx = ax.host ? cv.add(bx) : 0, ohy = ay.host ? cv.add(by) : 0, ohz = az.host ? cv.add(bz) : 0;
     if ((st = ensure_ws(ctx, cv.total))) return st;
-    const void *opf, *opi;
-    if ((st = get_op(ctx, m3, elem, 0, 1, s, &opf))) return st;
-    if ((st = get_op(ctx, m3, elem, 1, 1, s, &opi))) return st;
+    TubeOp opf, opi;
+    if ((st = get_tube(ctx, prec, elem, m3, 0, 1, s, &opf))) return st;
+    if ((st = get_tube(ctx, prec, elem, m3, 1, 1, s, &opi))) return st;
     Stager sg{ctx, s};
     if ((st = sg.in(ax, ohx))) return st;
     if ((st = sg.in(ay, ohy))) return st;
     sg.out(az, ohz);
     void *Lx = at(ctx, olx), *Ly = at(ctx, oly), *Lz = at(ctx, olz);
-    CK(tube_any(elem, ax.dev, Lx, opf, m1 * m2, m3, s));
-    CK(tube_any(elem, ay.dev, Ly, opf, m2 * m4, m3, s));
+    CK(tube_any(ctx, elem, ax.dev, Lx, opf, m1 * m2, m3, s));
+    CK(tube_any(ctx, elem, ay.dev, Ly, opf, m2 * m4, m3, s));
     TRACE(K_FACEWISE);
     if (elem == 8)
         CK(launch_facewise<double>((const double*)Lx, (const double*)Ly, (double*)Lz, m1, m4, m2, m3, 0, 0, nullptr, s));
     else
         CK(launch_facewise<float>((const float*)Lx, (const float*)Ly, (float*)Lz, m1, m4, m2, m3, 0, 0, nullptr, s));
-    CK(tube_any(elem, Lz, az.dev, opi, m1 * m4, m3, s));
+    CK(tube_any(ctx, elem, Lz, az.dev, opi, m1 * m4, m3, s));
     ctx->last_stream = s;
     return sg.finish();
 }
@@ -587,15 +648,16 @@ namespace {
 // ADMM driver shared by tnn_complete and tnn_admm_iterate.  X, M device
 // pointers already hold the state; B and mask are device pointers.
 tnn_status admm_run(tnn_ctx* ctx, const void* B, const uint8_t* mask, const tnn_shape& sh,
-                    const tnn_admm_params* prm, int elem, void* X, void* M, double beta0, int max_iter,
+                    const tnn_admm_params* prm, tnn_precision prec, int elem, void* X, void* M, double beta0,
+                    int max_iter,
                     AdmmCtl* d_ctl, void* W, double* partials, SliceStats* stats, void* jwork,
                     const JacobiPlan& jp, cudaStream_t s, AdmmCtl* out)
 {
     const int64_t P = sh.n1 * sh.n2, n3 = sh.n3;
-    const void *opf, *opi;
+    TubeOp opf, opi;
     tnn_status st;
-    if ((st = get_op(ctx, n3, elem, 0, 0, s, &opf))) return st;
-    if ((st = get_op(ctx, n3, elem, 1, 0, s, &opi))) return st;
+    if ((st = get_tube(ctx, prec, elem, n3, 0, 0, s, &opf))) return st;
+    if ((st = get_tube(ctx, prec, elem, n3, 1, 0, s, &opi))) return st;
     {
         TRACE(K_CTL_INIT);
         CK(launch_ctl_init(d_ctl, beta0, prm->rho, prm->beta_max, prm->tol, max_iter, s));
@@ -608,21 +670,29 @@ tnn_status admm_run(tnn_ctx* ctx, const void* B, const uint8_t* mask, const tnn_
             if (elem == 8) {
                 { TRACE(K_TUBE_FWD_ADMM);
                   CK(launch_tube_fwd_admm_op<double>((const double*)X, (const double*)M, (double*)W,
-                                                     (const double*)opf, P, n3, d_ctl, s)); }
+                                                     (const double*)opf.op, P, n3, d_ctl, s)); }
                 { TRACE(K_JACOBI_SVT);
                   CK(launch_jacobi_svt<double>(jp, (double*)W, 0.0, d_ctl, sweeps, jwork, stats, s)); }
                 { TRACE(K_TUBE_INV_ADMM);
                   CK(launch_tube_inv_admm_op<double>((const double*)W, (double*)X, (double*)M, (const double*)B, mask,
-                                                     (const double*)opi, P, n3, d_ctl, partials, &nblk, s)); }
+                                                     (const double*)opi.op, P, n3, d_ctl, partials, &nblk, s)); }
             } else {
                 { TRACE(K_TUBE_FWD_ADMM);
-                  CK(launch_tube_fwd_admm_op<float>((const float*)X, (const float*)M, (float*)W, (const float*)opf,
-                                                    P, n3, d_ctl, s)); }
+                  if (opf.tc)
+                      CK(launch_tube_tc_fwd_admm((const float*)X, (const float*)M, (float*)W, opf.img, P, n3, d_ctl,
+                                                 ctx->d_err, s));
+                  else
+                      CK(launch_tube_fwd_admm_op<float>((const float*)X, (const float*)M, (float*)W,
+                                                        (const float*)opf.op, P, n3, d_ctl, s)); }
                 { TRACE(K_JACOBI_SVT);
                   CK(launch_jacobi_svt<float>(jp, (float*)W, 0.0, d_ctl, sweeps, jwork, stats, s)); }
                 { TRACE(K_TUBE_INV_ADMM);
-                  CK(launch_tube_inv_admm_op<float>((const float*)W, (float*)X, (float*)M, (const float*)B, mask,
-                                                    (const float*)opi, P, n3, d_ctl, partials, &nblk, s)); }
+                  if (opi.tc)
+                      CK(launch_tube_tc_inv_admm((const float*)W, (float*)X, (float*)M, (const float*)B, mask,
+                                                 opi.img, P, n3, d_ctl, partials, &nblk, ctx->d_err, s));
+                  else
+                      CK(launch_tube_inv_admm_op<float>((const float*)W, (float*)X, (float*)M, (const float*)B, mask,
+                                                        (const float*)opi.op, P, n3, d_ctl, partials, &nblk, s)); }
             }
             { TRACE(K_FINALIZE); CK(launch_admm_finalize(d_ctl, partials, nblk, stats, n3, s)); }
         }
@@ -631,6 +701,7 @@ tnn_status admm_run(tnn_ctx* ctx, const void* B, const uint8_t* mask, const tnn_
         if (ctx->h_ctl->done || queued >= max_iter) break;
         if (chunk < 16) chunk *= 2;
     }
+    if ((st = check_tc_error(ctx))) return st;
     *out = *ctx->h_ctl;
     ctx->last_stats = stats;
     ctx->last_n3 = n3;
@@ -695,7 +766,7 @@ tnn_status tnn_complete(tnn_ctx* ctx, const void* B, const uint8_t* mask, tnn_sh
                                                (int64_t)N, s));
     else CK(launch_admm_init<float>((const float*)ab.dev, (const uint8_t*)am.dev, (float*)X, (float*)M, (int64_t)N, s));
     AdmmCtl res;
-    st = admm_run(ctx, ab.dev, (const uint8_t*)am.dev, sh, params, elem, X, M, params->beta0, params->max_iter,
+    st = admm_run(ctx, ab.dev, (const uint8_t*)am.dev, sh, params, prec, elem, X, M, params->beta0, params->max_iter,
                   (AdmmCtl*)at(ctx, oC), at(ctx, oW), (double*)at(ctx, oP), (SliceStats*)at(ctx, oS), at(ctx, oJ), jp,
                   s, &res);
     if (st) return st;
@@ -738,7 +809,7 @@ tnn_status tnn_admm_iterate(tnn_ctx* ctx, const void* B, const uint8_t* mask, tn
     sg.out(amm, ohmm);
     int max_iter = params->max_iter < iters ? params->max_iter : iters;
     AdmmCtl res;
-    st = admm_run(ctx, ab.dev, (const uint8_t*)am.dev, sh, params, elem, ax.dev, amm.dev, *beta, max_iter,
+    st = admm_run(ctx, ab.dev, (const uint8_t*)am.dev, sh, params, prec, elem, ax.dev, amm.dev, *beta, max_iter,
                   (AdmmCtl*)at(ctx, oC), at(ctx, oW), (double*)at(ctx, oP), (SliceStats*)at(ctx, oS), at(ctx, oJ), jp,
                   s, &res);
     if (st) return st;

@@ -600,7 +600,6 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
     const size_t wsz = (size_t)ldA * npad;
     constexpr int GPW = 32 / L;  // groups per warp
     const int hl = lane % L;
-    const int gid = warp * GPW + lane / L;
     const int NG = W * GPW;
 
     T* Aw;

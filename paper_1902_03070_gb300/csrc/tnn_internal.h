@@ -78,6 +78,22 @@ cudaError_t launch_admm_init(const T* B, const uint8_t* mask, T* X, T* M, int64_
 cudaError_t launch_ctl_init(AdmmCtl* ctl, double beta, double rho, double beta_max, double tol, int max_iter,
                             cudaStream_t s);
 
+// ---- tube transforms on tcgen05 tensor cores (tube_tc.cu), FP32 data -------
+// 3xTF32 split; the operator is passed as prebuilt hi/lo images in the MMA's
+// shared-memory layout (launch_build_operator_tc, tube_tc_image_floats floats).
+// *err is set to 1 if a bounded wait timed out.
+bool tube_tc_supported(int64_t n3);
+size_t tube_tc_image_floats(int64_t n3);
+int tube_tc_partials_count(int64_t P);
+cudaError_t launch_build_operator_tc(float* img, int64_t n3, int inverse, int scaled, cudaStream_t s);
+cudaError_t launch_tube_tc(const float* X, float* Y, const float* img, int64_t P, int64_t n3, int* err,
+                           cudaStream_t s);
+cudaError_t launch_tube_tc_fwd_admm(const float* X, const float* M, float* Zbar, const float* img, int64_t P,
+                                    int64_t n3, const AdmmCtl* ctl, int* err, cudaStream_t s);
+cudaError_t launch_tube_tc_inv_admm(const float* Ybar, float* X, float* M, const float* B, const uint8_t* mask,
+                                    const float* img, int64_t P, int64_t n3, const AdmmCtl* ctl, double* partials,
+                                    int* nblocks, int* err, cudaStream_t s);
+
 // ---- Jacobi SVT / SVD (jacobi.cu) -------------------------------------------
 enum JacobiMode { JAC_SVT = 0, JAC_SVD = 1 };
 

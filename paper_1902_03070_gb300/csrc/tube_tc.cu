@@ -1,0 +1,394 @@
+// Tube transforms on the tcgen05 tensor cores (FP32 data, 3xTF32 split).
+//
+// out(p, q) = sum_j in(p, j) op(j, q) as a GEMM with M = pixels (a CTA owns
+// 128 of them, the MMA's M), N = output tube positions (n3 rounded up to 16,
+// all of them in one TMEM accumulator) and K = input tube positions, taken in
+// chunks of 32.  FP32 accuracy from TF32 products: x = x_hi + x_lo with x_hi
+// the TF32 part (low 13 mantissa bits cleared) and x_lo = x - x_hi, and
+// out = A_hi B_hi + A_hi B_lo + A_lo B_hi (the dropped A_lo B_lo term is
+// about 2^-22 relative).
+//
+// Staging: the 128 threads load the input strip with coalesced loads (the
+// ADMM prologue Z = X - M/beta is applied here), split it and write the
+// K-major core-matrix layout (8 rows x 16 bytes per core matrix, no swizzle);
+// the operator's hi/lo images are prebuilt in the same layout, chunk by chunk,
+// and each chunk is copied in by bulk asynchronous copies (TMA engine) that
+// complete on an mbarrier.  One thread issues the MMAs and commits them to a
+// second mbarrier; the epilogue reads the accumulator with tcgen05.ld (warp w
+// owns TMEM lanes 32w..32w+31 = pixels) and writes the output coalesced,
+// with the ADMM update fused in the inverse direction.
+//
+// Every mbarrier wait is bounded: on timeout the kernel records an error,
+// stops issuing work, waits (bounded) for what it has in flight, frees its
+// TMEM and returns.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "tnn_internal.h"
+
+namespace tnn {
+namespace {
+
+constexpr int TBM = 128;          // pixels per CTA (MMA M)
+constexpr int TKC = 32;           // K chunk (input tube positions per stage)
+constexpr int TTHREADS = 128;     // one thread per pixel row
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+// Shared-memory matrix descriptor, K-major, no swizzle: start address, byte
+// offset between core matrices adjacent along K (lbo) and along M/N (sbo).
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo & 0x3FFFFu) >> 4) << 16;
+    d |= (uint64_t)((sbo & 0x3FFFFu) >> 4) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version
+    return d;
+}
+
+// Instruction descriptor: D in F32, A and B in TF32, both K-major, M x N.
+__host__ __device__ constexpr uint32_t make_idesc_tf32(int M, int N)
+{
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// Bounded wait for the given phase parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+{
+    const uint32_t a = smem_u32(bar);
+    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(
+            dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Byte offset of element (row, k) of a K-major tile of TKC columns.
+__device__ __forceinline__ uint32_t kmajor_off(int row, int k)
+{
+    return (uint32_t)((k >> 2) * 128 + (row >> 3) * (TKC / 4 * 128) + (row & 7) * 16 + (k & 3) * 4);
+}
+
+// MODE 0: plain; MODE 1: forward with Z = X - M/beta; MODE 2: inverse with the ADMM update.
+template <int MODE>
+__global__ void __launch_bounds__(TTHREADS)
+tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, float* __restrict__ out,
+               const float* __restrict__ bimg, int64_t P, int n3, int NP, int nchunks, uint32_t tmem_cols,
+               const AdmmCtl* __restrict__ ctl, float* __restrict__ Xs, float* __restrict__ Ms,
+               const float* __restrict__ Bs, const uint8_t* __restrict__ mask, double* __restrict__ partials,
+               int* __restrict__ err)
+{
+    if (MODE != 0 && ctl->done) return;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar_b, bar_mma;
+    __shared__ uint32_t s_taddr;
+    __shared__ double red[4][4];
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t p0 = (int64_t)blockIdx.x * TBM;
+    const uint32_t a_bytes = TBM * TKC * 4;          // one A tile (hi or lo)
+    const uint32_t b_bytes = (uint32_t)NP * TKC * 4; // one B tile (hi or lo)
+    float* Ahi = reinterpret_cast<float*>(smem);
+    float* Alo = reinterpret_cast<float*>(smem + a_bytes);
+    float* Bhi = reinterpret_cast<float*>(smem + 2 * a_bytes);
+    float* Blo = reinterpret_cast<float*>(smem + 2 * a_bytes + b_bytes);
+
+    float rbeta = 1.f;
+    if (MODE != 0) rbeta = (float)ctl->beta;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_taddr)),
+                     "r"(tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        mbar_init(&bar_b, 1);
+        mbar_init(&bar_mma, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t taddr = s_taddr;
+    const uint32_t idesc = make_idesc_tf32(TBM, NP);
+    const int64_t p = p0 + tid;
+    const bool prow = p < P;
+
+    uint32_t phase_b = 0, phase_m = 0;
+    bool ok = true;
+    bool mma_pending = false;  // thread 0: a commit not yet awaited (for the failure path)
+    for (int c = 0; c < nchunks && ok; ++c) {
+        // operator chunk: bulk copies into the B tiles
+        if (tid == 0) {
+            mbar_expect_tx(&bar_b, 2 * b_bytes);
+            const float* src = bimg + (size_t)c * 2 * NP * TKC;
+            bulk_g2s(Bhi, src, b_bytes, &bar_b);
+            bulk_g2s(Blo, src + (size_t)NP * TKC, b_bytes, &bar_b);
+        }
+        // input strip chunk: 32 tube positions of this thread's pixel, split, K-major
+        const int k0 = c * TKC;
+#pragma unroll
+        for (int g = 0; g < TKC / 4; ++g) {
+            float v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j = k0 + g * 4 + u;
+                float x = 0.f;
+                if (prow && j < n3) {
+                    const size_t e = (size_t)p + (size_t)P * j;
+                    x = in[e];
+                    if (MODE == 1) x = x - in2[e] / rbeta;
+                }
+                v[u] = x;
+            }
+            float4 hi, lo;
+            hi.x = tf32_hi(v[0]); lo.x = v[0] - hi.x;
+            hi.y = tf32_hi(v[1]); lo.y = v[1] - hi.y;
+            hi.z = tf32_hi(v[2]); lo.z = v[2] - hi.z;
+            hi.w = tf32_hi(v[3]); lo.w = v[3] - hi.w;
+            const uint32_t off = kmajor_off(tid, g * 4);
+            *reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(Ahi) + off) = hi;
+            *reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(Alo) + off) = lo;
+        }
+        // make the generic-proxy writes visible to the tensor cores
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        int fail = 0;
+        if (tid == 0) {
+            if (!mbar_wait(&bar_b, phase_b)) {
+                fail = 1;
+            } else {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t sbo = TKC / 4 * 128, lbo = 128;
+#pragma unroll
+                for (int s = 0; s < TKC / 8; ++s) {
+                    const uint32_t koff = (uint32_t)s * 2 * 128;
+                    const uint64_t ah = make_desc(smem_u32(Ahi) + koff, lbo, sbo);
+                    const uint64_t al = make_desc(smem_u32(Alo) + koff, lbo, sbo);
+                    const uint64_t bh = make_desc(smem_u32(Bhi) + koff, lbo, sbo);
+                    const uint64_t bl = make_desc(smem_u32(Blo) + koff, lbo, sbo);
+                    mma_tf32(taddr, ah, bh, idesc, (c > 0 || s > 0) ? 1u : 0u);
+                    mma_tf32(taddr, ah, bl, idesc, 1u);
+                    mma_tf32(taddr, al, bh, idesc, 1u);
+                }
+                mma_commit(&bar_mma);
+                mma_pending = true;
+            }
+            phase_b ^= 1;
+        }
+        if (__syncthreads_or(fail)) {
+            ok = false;
+            break;
+        }
+        // the tiles are rewritten by the next chunk only after these MMAs completed
+        const int late = mbar_wait(&bar_mma, phase_m) ? 0 : 1;
+        phase_m ^= 1;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (__syncthreads_or(late)) {
+            ok = false;
+            break;
+        }
+        if (tid == 0) mma_pending = false;
+    }
+
+    if (ok) {
+        // epilogue: warp w reads TMEM lanes 32w..32w+31 (its pixels), 16 columns at a time
+        float sdx = 0.f, sxx = 0.f, syx = 0.f, snx = 0.f;
+        for (int q0 = 0; q0 < NP; q0 += 16) {
+            float v[16];
+            tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)q0, v);
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int q = q0 + u;
+                if (!prow || q >= n3) continue;
+                const size_t e = (size_t)p + (size_t)P * q;
+                if (MODE != 2) {
+                    out[e] = v[u];
+                } else {
+                    // Algorithm 1, Eq. 25 and the multiplier update of Eq. 20
+                    const float y = v[u];
+                    const float x = Xs[e], mm = Ms[e];
+                    const float xn = mask[e] ? Bs[e] : y + mm / rbeta;
+                    const float mn = mm + rbeta * (y - xn);
+                    const float dx = xn - x, dy = y - xn;
+                    sdx = fmaf(dx, dx, sdx);
+                    sxx = fmaf(x, x, sxx);
+                    syx = fmaf(dy, dy, syx);
+                    snx = fmaf(xn, xn, snx);
+                    Xs[e] = xn;
+                    Ms[e] = mn;
+                }
+            }
+        }
+        if (MODE == 2) {
+            double sv[4] = {(double)sdx, (double)sxx, (double)syx, (double)snx};
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int t = 0; t < 4; ++t) sv[t] += __shfl_xor_sync(0xffffffffu, sv[t], o);
+            if (lane == 0)
+#pragma unroll
+                for (int t = 0; t < 4; ++t) red[warp][t] = sv[t];
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (MODE == 2 && tid < 4) {
+        double t = 0.0;
+        for (int w = 0; w < TTHREADS / 32; ++w) t += ok ? red[w][tid] : 0.0;
+        partials[(size_t)blockIdx.x * 4 + tid] = t;
+    }
+    if (!ok && tid == 0) {
+        atomicExch(err, 1);
+        // let in-flight copies and MMAs land before the shared memory goes away (bounded)
+        if (!mma_pending) mbar_wait(&bar_b, phase_b ^ 1u);
+        else mbar_wait(&bar_mma, phase_m ^ 1u);
+    }
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(tmem_cols));
+}
+
+// Operator images: for each K chunk, the hi and lo TF32 parts of op(k, n)
+// (k = input position, n = output position) in the K-major core-matrix
+// layout of an NP x TKC tile; zero outside n3 x n3.
+__global__ void build_operator_tc(float* img, int n3, int NP, int nchunks, int inverse, int scaled)
+{
+    const int total = nchunks * NP * TKC;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const int c = idx / (NP * TKC), r = idx % (NP * TKC);
+        const int n = r / TKC, kk = r % TKC, k = c * TKC + kk;
+        double v = 0.0;
+        if (n < n3 && k < n3) {
+            auto Cf = [n3](int a, int b) {
+                const double s = (a == 0) ? sqrt(1.0 / n3) : sqrt(2.0 / n3);
+                return s * cospi((double)((2 * b + 1) * a) / (2.0 * n3));
+            };
+            if (!inverse) {  // out_n = sum_k C[n, k] in_k
+                v = Cf(n, k);
+                if (scaled) v /= Cf(n, 0);
+            } else {         // out_n = sum_k C[k, n] in_k
+                v = Cf(k, n);
+                if (scaled) v *= Cf(k, 0);
+            }
+        }
+        const float hi = __uint_as_float(__float_as_uint((float)v) & 0xFFFFE000u);
+        const float lo = (float)(v - (double)hi);
+        const uint32_t off = (uint32_t)((kk >> 2) * 128 + (n >> 3) * (TKC / 4 * 128) + (n & 7) * 16 + (kk & 3) * 4) / 4;
+        img[(size_t)c * 2 * NP * TKC + off] = hi;
+        img[(size_t)c * 2 * NP * TKC + (size_t)NP * TKC + off] = lo;
+    }
+}
+
+}  // namespace
+
+bool tube_tc_supported(int64_t n3) { return n3 >= 1 && n3 <= 256; }
+
+int tube_tc_np(int64_t n3) { return (int)((n3 + 15) / 16 * 16); }
+int tube_tc_chunks(int64_t n3) { return (int)((n3 + TKC - 1) / TKC); }
+size_t tube_tc_image_floats(int64_t n3) { return (size_t)tube_tc_chunks(n3) * 2 * tube_tc_np(n3) * TKC; }
+int tube_tc_partials_count(int64_t P) { return (int)((P + TBM - 1) / TBM); }
+
+cudaError_t launch_build_operator_tc(float* img, int64_t n3, int inverse, int scaled, cudaStream_t s)
+{
+    const int NP = tube_tc_np(n3), nc = tube_tc_chunks(n3);
+    const int total = nc * NP * TKC;
+    build_operator_tc<<<(total + 255) / 256, 256, 0, s>>>(img, (int)n3, NP, nc, inverse, scaled);
+    return cudaGetLastError();
+}
+
+template <int MODE>
+static cudaError_t launch_tc(const float* in, const float* in2, float* out, const float* img, int64_t P, int64_t n3,
+                             const AdmmCtl* ctl, float* X, float* M, const float* B, const uint8_t* mask,
+                             double* partials, int* err, cudaStream_t s)
+{
+    const int NP = tube_tc_np(n3), nc = tube_tc_chunks(n3);
+    uint32_t cols = 32;
+    while ((int)cols < NP) cols <<= 1;
+    const size_t smem = 2 * (size_t)TBM * TKC * 4 + 2 * (size_t)NP * TKC * 4;
+    auto kern = tube_tc_kernel<MODE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const unsigned grid = (unsigned)((P + TBM - 1) / TBM);
+    kern<<<grid, TTHREADS, smem, s>>>(in, in2, out, img, P, (int)n3, NP, nc, cols, ctl, X, M, B, mask, partials, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tube_tc(const float* X, float* Y, const float* img, int64_t P, int64_t n3, int* err, cudaStream_t s)
+{
+    return launch_tc<0>(X, nullptr, Y, img, P, n3, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, err, s);
+}
+
+cudaError_t launch_tube_tc_fwd_admm(const float* X, const float* M, float* Zbar, const float* img, int64_t P, int64_t n3,
+                                    const AdmmCtl* ctl, int* err, cudaStream_t s)
+{
+    return launch_tc<1>(X, M, Zbar, img, P, n3, ctl, nullptr, nullptr, nullptr, nullptr, nullptr, err, s);
+}
+
+cudaError_t launch_tube_tc_inv_admm(const float* Ybar, float* X, float* M, const float* B, const uint8_t* mask,
+                                    const float* img, int64_t P, int64_t n3, const AdmmCtl* ctl, double* partials,
+                                    int* nblocks, int* err, cudaStream_t s)
+{
+    *nblocks = tube_tc_partials_count(P);
+    return launch_tc<2>(Ybar, nullptr, nullptr, img, P, n3, ctl, X, M, B, mask, partials, err, s);
+}
+
+}  // namespace tnn

@@ -72,7 +72,7 @@ def test_admm_invariants_and_resume_bit_exact(ctx):
     assert not M1[~m].any()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
 def test_completion_48x48x16(ctx, prec):
     """Tubal rank 3, 40% observed, beta0 1e-4, rho 1.1, tol 1e-8, <= 300 iterations."""
     from paper_1902_03070_gb300 import tnn

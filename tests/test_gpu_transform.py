@@ -10,7 +10,7 @@ from paper_1902_03070_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 SHAPES = [(48, 48, 16), (7, 5, 31), (3, 1, 1), (1, 9, 2), (129, 3, 65), (144, 176, 100), (20, 30, 130)]
-TOL = {"fp64": 1e-13, "fp32": 2e-6}
+TOL = {"fp64": 1e-13, "fp32": 2e-6, "tf32x3": 2e-6}
 
 
 @pytest.fixture(scope="module")
@@ -21,7 +21,7 @@ def ctx():
         yield c
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("inverse,scaled", [(0, 0), (1, 0), (0, 1), (1, 1)])
 def test_tdct3_matches_oracle(ctx, prec, shape, inverse, scaled):
@@ -31,13 +31,13 @@ def test_tdct3_matches_oracle(ctx, prec, shape, inverse, scaled):
     Xd = tnn.to_fortran(X, dtype=dtype_of(prec))
     Yd = tnn.fortran_empty(shape, dtype_of(prec))
     ctx.tdct3(Xd, Yd, inverse=inverse, scaled=scaled, prec=prec)
-    ref = O.tube_transform(X.astype(np.float32).astype(np.float64) if prec == "fp32" else X,
+    ref = O.tube_transform(X.astype(np.float32).astype(np.float64) if prec != "fp64" else X,
                            inverse=bool(inverse), scaled=bool(scaled))
     Y = tnn.to_numpy(Yd).astype(np.float64)
     assert np.linalg.norm(Y - ref) <= TOL[prec] * np.linalg.norm(ref)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
 @pytest.mark.parametrize("dims", [(4, 3, 5, 6), (48, 3, 48, 16), (1, 7, 2, 3), (70, 65, 66, 9)])
 def test_tprod_matches_oracle(ctx, prec, dims):
     from paper_1902_03070_gb300 import tnn
@@ -45,7 +45,7 @@ def test_tprod_matches_oracle(ctx, prec, dims):
     rng = np.random.default_rng(m1 * m2 + m4)
     X = inputs.random_tensor((m1, m2, m3), rng)
     Y = inputs.random_tensor((m2, m4, m3), rng)
-    if prec == "fp32":
+    if prec != "fp64":
         X = X.astype(np.float32).astype(np.float64)
         Y = Y.astype(np.float32).astype(np.float64)
     Z = tnn.fortran_empty((m1, m4, m3), dtype_of(prec))

@@ -20,7 +20,7 @@ def ctx():
         yield c
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
 @pytest.mark.parametrize("shape", [(6, 4, 5), (4, 6, 5), (48, 48, 16), (33, 70, 3), (9, 1, 2), (100, 60, 7)])
 def test_tsvd_properties_and_tubes(ctx, prec, shape):
     from paper_1902_03070_gb300 import tnn
@@ -28,7 +28,7 @@ def test_tsvd_properties_and_tubes(ctx, prec, shape):
     r = min(n1, n2)
     rng = np.random.default_rng(n1 + 7 * n2 + 31 * n3)
     X = inputs.random_tensor(shape, rng)
-    if prec == "fp32":
+    if prec != "fp64":
         X = X.astype(np.float32).astype(np.float64)
     dt = dtype_of(prec)
     U = tnn.fortran_empty((n1, r, n3), dt)
@@ -48,7 +48,7 @@ def test_tsvd_properties_and_tubes(ctx, prec, shape):
     assert np.abs(S - So).max() <= tol * np.abs(So).max()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
 def test_tsvd_inverse_roundtrip(ctx, prec):
     from paper_1902_03070_gb300 import tnn
     rng = np.random.default_rng(3)

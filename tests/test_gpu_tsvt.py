@@ -21,7 +21,7 @@ from paper_1902_03070_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "fp32": 1e-5}
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "tf32x3": 1e-5}
 
 SHAPES = [
     (48, 48, 16),    # the 48 x 48 x 16 completion workload
@@ -51,13 +51,13 @@ def _run(ctx, Z, tau, prec, want_tnn=False):
     return tnn.to_numpy(out).astype(np.float64)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("q", [0.3, 0.8])
 def test_tsvt_matches_oracle(ctx, prec, shape, q):
     rng = np.random.default_rng(shape[0] * 1000 + shape[1] * 10 + shape[2])
     Z = inputs.random_tensor(shape, rng)
-    if prec == "fp32":
+    if prec != "fp64":
         Z = Z.astype(np.float32).astype(np.float64)
     tau = tau_at_quantile(Z, q)
     Y = _run(ctx, Z, tau, prec)
@@ -68,18 +68,18 @@ def test_tsvt_matches_oracle(ctx, prec, shape, q):
         assert err_y <= TOL["fp64"]
     else:
         err_z = np.linalg.norm(Y - ref) / np.linalg.norm(Z)
-        assert err_z <= TOL["fp32"], (err_z, err_y)
-        assert err_y <= (TOL["fp32"] if q <= 0.5 else 1e-4), (err_z, err_y)
+        assert err_z <= TOL[prec], (err_z, err_y)
+        assert err_y <= (TOL[prec] if q <= 0.5 else 1e-4), (err_z, err_y)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
 def test_tsvt_low_rank_plus_noise(ctx, prec):
     # a 48 x 48 x 16 tubal-rank-3 tensor plus noise, threshold above the noise edge
     rng = np.random.default_rng(7)
     A, F = inputs.lowrank_factors(48, 48, 16, 3, rng)
     Z = O.tprod(A, F) + 1e-3 * rng.standard_normal((48, 48, 16))
     Z = np.asfortranarray(Z)
-    if prec == "fp32":
+    if prec != "fp64":
         Z = Z.astype(np.float32).astype(np.float64)
     tau = 0.05
     Y, tnn_gpu = _run(ctx, Z, tau, prec, want_tnn=True)
@@ -89,24 +89,26 @@ def test_tsvt_low_rank_plus_noise(ctx, prec):
     assert abs(tnn_gpu - tnn_ref) <= (1e-12 if prec == "fp64" else 1e-5) * tnn_ref
 
 
-def test_tsvt_video_shaped_fp32(ctx):
-    """The 144 x 176 x 100 video-shaped tensor at full size, FP32."""
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+def test_tsvt_video_shaped(ctx, prec):
+    """The 144 x 176 x 100 video-shaped tensor at full size."""
     parts = inputs.config2_parts()
     T = inputs.config2_assemble(O.tprod(parts["A"], parts["F"]), parts)
     Z = T.astype(np.float32).astype(np.float64)
     for q in (0.5, 0.95):
         tau = tau_at_quantile(Z, q)
-        Y = _run(ctx, Z, tau, "fp32")
+        Y = _run(ctx, Z, tau, prec)
         ref = O.tsvt(Z, tau, nthreads=THREADS)
-        log_err("tsvt video fp32 q=%s" % q, err_y=rel_err(Y, ref, Z), ynorm_over_z=np.linalg.norm(ref) / np.linalg.norm(Z))
-        assert rel_err(Y, ref, Z) <= TOL["fp32"], q
+        log_err("tsvt video %s q=%s" % (prec, q), err_y=rel_err(Y, ref, Z),
+                ynorm_over_z=np.linalg.norm(ref) / np.linalg.norm(Z))
+        assert rel_err(Y, ref, Z) <= TOL[prec], q
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
 def test_tsvt_special_cases(ctx, prec):
     rng = np.random.default_rng(11)
     Z = inputs.random_tensor((20, 12, 6), rng)
-    if prec == "fp32":
+    if prec != "fp64":
         Z = Z.astype(np.float32).astype(np.float64)
     tol = 1e-13 if prec == "fp64" else 2e-6
     # tau = 0: Y = Z

@@ -162,7 +162,8 @@ tnn_status tprod_dct(tnn_ctx* ctx, const void* X, const void* Y, int64_t m1, int
                      int64_t m3, tnn_precision prec, void* Z, void* stream);
 
 /* Algorithm 1: ADMM for the completion model (Eq. 17) from X = B on the
- * mask, M = 0, beta = beta0.  B (n1 x n2 x n3) is read only where mask != 0.
+ * mask, M = 0, beta = beta0.  B (n1 x n2 x n3, a full-size buffer) may be
+ * read everywhere but its values off the mask never affect the result.
  * mask is n1*n2*n3 bytes in the tensor's layout (nonzero = observed).
  * X_out receives the recovered tensor and may be the same buffer as B.
  * rep (may be NULL) receives the run's report.  Synchronises the stream.

@@ -41,7 +41,11 @@ cudaError_t launch_one(const JacobiPlan& p, KArgs<T> a, cudaStream_t s)
 }  // namespace jac
 }  // namespace tnn
 
-// One supported (L, R) variant of a (T, WITHV) family; the plan's key is L * 100 + R.
+// One supported (L, R, K) variant of a (T, WITHV) family; the plan's key is
+// L * 1000 + R * 10 + K.
 #define TNN_JAC_CASE(T, L, R, WITHV) \
-    case L * 100 + R:                \
+    case L * 1000 + R * 10 + jac::pick_K((int)sizeof(T), R, WITHV): \
         return jac::launch_one<T, jac::pick_K((int)sizeof(T), R, WITHV), R, L, WITHV>(p, a, s);
+#define TNN_JAC_CASE_K(T, L, R, K, WITHV) \
+    case L * 1000 + R * 10 + K:           \
+        return jac::launch_one<T, K, R, L, WITHV>(p, a, s);

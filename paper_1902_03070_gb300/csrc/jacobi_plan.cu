@@ -11,32 +11,34 @@ namespace tnn {
 namespace {
 
 struct Variant {
-    int L, R;
+    int L, R, K;  // K = 0: the default block width for (elem, R)
 };
 
 // Smallest variant whose L * R rows cover m (the first listed wins), unless
-// TNN_JACOBI_VARIANT="L,R" names a compiled variant that covers m (a tuning
-// override for benchmarking the variants against each other).
+// TNN_JACOBI_VARIANT="L,R[,K]" names a compiled variant that covers m (a
+// tuning override for benchmarking the variants against each other).
 bool pick_variant(int m, int elem, bool withv, Variant* out)
 {
-    static const Variant f32_svt[] = {{16, 4}, {16, 8}, {16, 12}, {32, 8}, {32, 12}, {32, 16}, {32, 4}, {32, 6}};
-    static const Variant f64_svt[] = {{16, 2}, {16, 4}, {16, 6}, {32, 4}, {32, 6}, {32, 8}, {32, 16}};
-    static const Variant f32_svd[] = {{32, 2}, {32, 4}, {32, 6}, {32, 8}, {32, 12}, {32, 16}};
-    static const Variant f64_svd[] = {{32, 1}, {32, 2}, {32, 4}, {32, 6}, {32, 8}};
+    static const Variant f32_svt[] = {{16, 4, 0}, {16, 8, 0}, {16, 12, 0}, {32, 8, 0}, {32, 12, 0},
+                                       {32, 16, 0}, {32, 4, 0}, {32, 6, 0}, {16, 12, 2}};
+    static const Variant f64_svt[] = {{16, 2, 0}, {16, 4, 0}, {16, 6, 0}, {32, 4, 0}, {32, 6, 0}, {32, 8, 0},
+                                       {32, 16, 0}};
+    static const Variant f32_svd[] = {{32, 2, 0}, {32, 4, 0}, {32, 6, 0}, {32, 8, 0}, {32, 12, 0}, {32, 16, 0}};
+    static const Variant f64_svd[] = {{32, 1, 0}, {32, 2, 0}, {32, 4, 0}, {32, 6, 0}, {32, 8, 0}};
     const Variant* t;
     int cnt;
     if (elem == 4) {
         t = withv ? f32_svd : f32_svt;
-        cnt = withv ? 6 : 8;
+        cnt = withv ? 6 : 9;
     } else {
         t = withv ? f64_svd : f64_svt;
         cnt = withv ? 5 : 7;
     }
     if (const char* env = getenv("TNN_JACOBI_VARIANT")) {
-        int L = 0, R = 0;
-        if (sscanf(env, "%d,%d", &L, &R) == 2)
+        int L = 0, R = 0, K = 0;
+        if (sscanf(env, "%d,%d,%d", &L, &R, &K) >= 2)
             for (int i = 0; i < cnt; ++i)
-                if (t[i].L == L && t[i].R == R && L * R >= m) {
+                if (t[i].L == L && t[i].R == R && t[i].K == K && L * R >= m) {
                     *out = t[i];
                     return true;
                 }
@@ -59,7 +61,7 @@ bool jacobi_plan_mode(int64_t n1, int64_t n2, int64_t n3, int elem, bool withv, 
     if (m > 512) return false;
     Variant v;
     if (!pick_variant((int)m, elem, withv, &v)) return false;
-    const int K = jac::pick_K(elem, v.R, withv);
+    const int K = v.K ? v.K : jac::pick_K(elem, v.R, withv);
     p->n1 = n1; p->n2 = n2; p->n3 = n3;
     p->m = (int)m; p->n = (int)n; p->tr = n1 < n2 ? 1 : 0;
     p->K = K; p->RA = v.R; p->L = v.L;

@@ -13,7 +13,7 @@ cudaError_t launch_jacobi_svd<float>(const JacobiPlan& p, const float* data, flo
     a.tau = 0.0; a.ctl = nullptr; a.max_sweeps = max_sweeps;
     a.work = reinterpret_cast<float*>(work); a.stats = stats;
     a.U = U; a.S = sigma; a.V = V;
-    switch (p.L * 100 + p.RA) {
+    switch (p.L * 1000 + p.RA * 10 + p.K) {
         TNN_JAC_CASE(float, 32, 2, true)
         TNN_JAC_CASE(float, 32, 4, true)
         TNN_JAC_CASE(float, 32, 6, true)

@@ -13,7 +13,7 @@ cudaError_t launch_jacobi_svd<double>(const JacobiPlan& p, const double* data, d
     a.tau = 0.0; a.ctl = nullptr; a.max_sweeps = max_sweeps;
     a.work = reinterpret_cast<double*>(work); a.stats = stats;
     a.U = U; a.S = sigma; a.V = V;
-    switch (p.L * 100 + p.RA) {
+    switch (p.L * 1000 + p.RA * 10 + p.K) {
         TNN_JAC_CASE(double, 32, 1, true)
         TNN_JAC_CASE(double, 32, 2, true)
         TNN_JAC_CASE(double, 32, 4, true)

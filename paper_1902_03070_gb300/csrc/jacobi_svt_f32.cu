@@ -12,7 +12,7 @@ cudaError_t launch_jacobi_svt<float>(const JacobiPlan& p, float* data, double ta
     a.m = p.m; a.n = p.n; a.tr = p.tr; a.nb = p.nb; a.ldA = p.ldA;
     a.tau = tau; a.ctl = ctl; a.max_sweeps = max_sweeps;
     a.work = reinterpret_cast<float*>(work); a.stats = stats;
-    switch (p.L * 100 + p.RA) {
+    switch (p.L * 1000 + p.RA * 10 + p.K) {
         TNN_JAC_CASE(float, 16, 4, false)
         TNN_JAC_CASE(float, 16, 8, false)
         TNN_JAC_CASE(float, 16, 12, false)
@@ -21,6 +21,7 @@ cudaError_t launch_jacobi_svt<float>(const JacobiPlan& p, float* data, double ta
         TNN_JAC_CASE(float, 32, 16, false)
         TNN_JAC_CASE(float, 32, 4, false)
         TNN_JAC_CASE(float, 32, 6, false)
+        TNN_JAC_CASE_K(float, 16, 12, 2, false)
     default: return cudaErrorInvalidValue;
     }
 }

@@ -12,7 +12,7 @@ cudaError_t launch_jacobi_svt<double>(const JacobiPlan& p, double* data, double 
     a.m = p.m; a.n = p.n; a.tr = p.tr; a.nb = p.nb; a.ldA = p.ldA;
     a.tau = tau; a.ctl = ctl; a.max_sweeps = max_sweeps;
     a.work = reinterpret_cast<double*>(work); a.stats = stats;
-    switch (p.L * 100 + p.RA) {
+    switch (p.L * 1000 + p.RA * 10 + p.K) {
         TNN_JAC_CASE(double, 16, 2, false)
         TNN_JAC_CASE(double, 16, 4, false)
         TNN_JAC_CASE(double, 16, 6, false)

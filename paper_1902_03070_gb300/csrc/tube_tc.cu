@@ -4,9 +4,9 @@
 // 128 of them, the MMA's M), N = output tube positions (n3 rounded up to 16,
 // all of them in one TMEM accumulator) and K = input tube positions, taken in
 // chunks of 32.  FP32 accuracy from TF32 products: x = x_hi + x_lo with x_hi
-// the TF32 part (low 13 mantissa bits cleared) and x_lo = x - x_hi, and
-// out = A_hi B_hi + A_hi B_lo + A_lo B_hi (the dropped A_lo B_lo term is
-// about 2^-22 relative).
+// x rounded to TF32 (10 mantissa bits) and x_lo = x - x_hi (exact in FP32,
+// at most 2^-11 |x|), and out = A_hi B_hi + A_hi B_lo + A_lo B_hi (the
+// dropped A_lo B_lo term is below 2^-22 relative).
 //
 // Staging: the 128 threads load the input strip with coalesced loads (the
 // ADMM prologue Z = X - M/beta is applied here), split it and write the
@@ -40,7 +40,13 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p)
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+// x rounded to the nearest TF32 value (10 mantissa bits), ties away from zero.
+__device__ __forceinline__ float tf32_hi(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
 
 // Shared-memory matrix descriptor, K-major, no swizzle: start address, byte
 // offset between core matrices adjacent along K (lbo) and along M/N (sbo).
@@ -139,7 +145,7 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
 {
     if (MODE != 0 && ctl->done) return;
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bar_b, bar_mma;
+    __shared__ __align__(8) uint64_t bar_b[2], bar_mma;
     __shared__ uint32_t s_taddr;
     __shared__ double red[4][4];
 
@@ -149,11 +155,14 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
     const uint32_t b_bytes = (uint32_t)NP * TKC * 4; // one B tile (hi or lo)
     float* Ahi = reinterpret_cast<float*>(smem);
     float* Alo = reinterpret_cast<float*>(smem + a_bytes);
-    float* Bhi = reinterpret_cast<float*>(smem + 2 * a_bytes);
-    float* Blo = reinterpret_cast<float*>(smem + 2 * a_bytes + b_bytes);
+    // two stages of operator tiles: stage t holds hi at Bst(t), lo right after
+    auto Bst = [&](int t) { return reinterpret_cast<float*>(smem + 2 * a_bytes + (size_t)t * 2 * b_bytes); };
 
-    float rbeta = 1.f;
-    if (MODE != 0) rbeta = (float)ctl->beta;
+    float rbeta = 1.f, rinv = 1.f;
+    if (MODE != 0) {
+        rbeta = (float)ctl->beta;
+        rinv = (float)(1.0 / ctl->beta);  // M / beta as M * (1 / beta): within an ulp, no division per element
+    }
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_taddr)),
@@ -161,7 +170,8 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        mbar_init(&bar_b, 1);
+        mbar_init(&bar_b[0], 1);
+        mbar_init(&bar_b[1], 1);
         mbar_init(&bar_mma, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -173,38 +183,52 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
     const int64_t p = p0 + tid;
     const bool prow = p < P;
 
-    uint32_t phase_b = 0, phase_m = 0;
+    uint32_t phase_b[2] = {0u, 0u}, phase_m = 0;
+    bool b_pending[2] = {false, false};  // thread 0: a stage copy not yet awaited
+    bool mma_pending = false;            // thread 0: a commit not yet awaited
     bool ok = true;
-    bool mma_pending = false;  // thread 0: a commit not yet awaited (for the failure path)
-    for (int c = 0; c < nchunks && ok; ++c) {
-        // operator chunk: bulk copies into the B tiles
-        if (tid == 0) {
-            mbar_expect_tx(&bar_b, 2 * b_bytes);
-            const float* src = bimg + (size_t)c * 2 * NP * TKC;
-            bulk_g2s(Bhi, src, b_bytes, &bar_b);
-            bulk_g2s(Blo, src + (size_t)NP * TKC, b_bytes, &bar_b);
-        }
-        // input strip chunk: 32 tube positions of this thread's pixel, split, K-major
+    auto issue_b = [&](int chunk) {
+        const int t = chunk & 1;
+        mbar_expect_tx(&bar_b[t], 2 * b_bytes);
+        const float* src = bimg + (size_t)chunk * 2 * NP * TKC;
+        bulk_g2s(Bst(t), src, b_bytes, &bar_b[t]);
+        bulk_g2s(Bst(t) + (size_t)NP * TKC, src + (size_t)NP * TKC, b_bytes, &bar_b[t]);
+        b_pending[t] = true;
+    };
+    if (tid == 0) issue_b(0);
+    for (int c = 0; c < nchunks; ++c) {
+        // this chunk's inputs: all loads first, in flight while the previous chunk's MMAs run
         const int k0 = c * TKC;
+        float v[TKC], w[TKC];
+#pragma unroll
+        for (int u = 0; u < TKC; ++u) {
+            const int j = k0 + u;
+            const bool ld = prow && j < n3;
+            const size_t e = (size_t)p + (size_t)P * (ld ? j : 0);
+            v[u] = ld ? __ldg(in + e) : 0.f;
+            if (MODE == 1) w[u] = ld ? __ldg(in2 + e) : 0.f;
+        }
+        if (c > 0) {
+            // the A tiles are rewritten only after the previous chunk's MMAs completed
+            const int late = mbar_wait(&bar_mma, phase_m) ? 0 : 1;
+            phase_m ^= 1;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (__syncthreads_or(late)) {
+                ok = false;
+                break;
+            }
+            if (tid == 0) mma_pending = false;
+        }
 #pragma unroll
         for (int g = 0; g < TKC / 4; ++g) {
-            float v[4];
+            float x[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int j = k0 + g * 4 + u;
-                float x = 0.f;
-                if (prow && j < n3) {
-                    const size_t e = (size_t)p + (size_t)P * j;
-                    x = in[e];
-                    if (MODE == 1) x = x - in2[e] / rbeta;
-                }
-                v[u] = x;
-            }
+            for (int u = 0; u < 4; ++u) x[u] = (MODE == 1) ? fmaf(-w[g * 4 + u], rinv, v[g * 4 + u]) : v[g * 4 + u];
             float4 hi, lo;
-            hi.x = tf32_hi(v[0]); lo.x = v[0] - hi.x;
-            hi.y = tf32_hi(v[1]); lo.y = v[1] - hi.y;
-            hi.z = tf32_hi(v[2]); lo.z = v[2] - hi.z;
-            hi.w = tf32_hi(v[3]); lo.w = v[3] - hi.w;
+            hi.x = tf32_hi(x[0]); lo.x = x[0] - hi.x;
+            hi.y = tf32_hi(x[1]); lo.y = x[1] - hi.y;
+            hi.z = tf32_hi(x[2]); lo.z = x[2] - hi.z;
+            hi.w = tf32_hi(x[3]); lo.w = x[3] - hi.w;
             const uint32_t off = kmajor_off(tid, g * 4);
             *reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(Ahi) + off) = hi;
             *reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(Alo) + off) = lo;
@@ -214,40 +238,43 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
         __syncthreads();
         int fail = 0;
         if (tid == 0) {
-            if (!mbar_wait(&bar_b, phase_b)) {
+            const int t = c & 1;
+            if (!mbar_wait(&bar_b[t], phase_b[t])) {
                 fail = 1;
             } else {
+                b_pending[t] = false;
+                phase_b[t] ^= 1;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t sbo = TKC / 4 * 128, lbo = 128;
+                const uint32_t bh0 = smem_u32(Bst(t)), bl0 = bh0 + b_bytes;
 #pragma unroll
                 for (int s = 0; s < TKC / 8; ++s) {
                     const uint32_t koff = (uint32_t)s * 2 * 128;
                     const uint64_t ah = make_desc(smem_u32(Ahi) + koff, lbo, sbo);
                     const uint64_t al = make_desc(smem_u32(Alo) + koff, lbo, sbo);
-                    const uint64_t bh = make_desc(smem_u32(Bhi) + koff, lbo, sbo);
-                    const uint64_t bl = make_desc(smem_u32(Blo) + koff, lbo, sbo);
+                    const uint64_t bh = make_desc(bh0 + koff, lbo, sbo);
+                    const uint64_t bl = make_desc(bl0 + koff, lbo, sbo);
                     mma_tf32(taddr, ah, bh, idesc, (c > 0 || s > 0) ? 1u : 0u);
                     mma_tf32(taddr, ah, bl, idesc, 1u);
                     mma_tf32(taddr, al, bh, idesc, 1u);
                 }
                 mma_commit(&bar_mma);
                 mma_pending = true;
+                // the other stage was read by chunk c-1's MMAs, which completed above
+                if (c + 1 < nchunks) issue_b(c + 1);
             }
-            phase_b ^= 1;
         }
         if (__syncthreads_or(fail)) {
             ok = false;
             break;
         }
-        // the tiles are rewritten by the next chunk only after these MMAs completed
+    }
+    if (ok) {
         const int late = mbar_wait(&bar_mma, phase_m) ? 0 : 1;
         phase_m ^= 1;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (__syncthreads_or(late)) {
-            ok = false;
-            break;
-        }
-        if (tid == 0) mma_pending = false;
+        if (__syncthreads_or(late)) ok = false;
+        else if (tid == 0) mma_pending = false;
     }
 
     if (ok) {
@@ -256,19 +283,37 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
         for (int q0 = 0; q0 < NP; q0 += 16) {
             float v[16];
             tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)q0, v);
+            if (MODE != 2) {
 #pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                const int q = q0 + u;
-                if (!prow || q >= n3) continue;
-                const size_t e = (size_t)p + (size_t)P * q;
-                if (MODE != 2) {
-                    out[e] = v[u];
-                } else {
-                    // Algorithm 1, Eq. 25 and the multiplier update of Eq. 20
+                for (int u = 0; u < 16; ++u) {
+                    const int q = q0 + u;
+                    if (prow && q < n3) out[(size_t)p + (size_t)P * q] = v[u];
+                }
+            } else {
+                // the group's X, M, B, mask loads first, then Algorithm 1's update
+                // (Eq. 25 and the multiplier update of Eq. 20), then the stores
+                float xv[16], mv[16], bv[16];
+                uint8_t kv[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int q = q0 + u;
+                    const bool ld = prow && q < n3;
+                    const size_t e = (size_t)p + (size_t)P * (ld ? q : 0);
+                    xv[u] = ld ? Xs[e] : 0.f;
+                    mv[u] = ld ? Ms[e] : 0.f;
+                    kv[u] = ld ? mask[e] : (uint8_t)0;
+                    // B is loaded everywhere (no wait on the mask) but only selected on the mask
+                    bv[u] = ld ? __ldg(Bs + e) : 0.f;
+                }
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int q = q0 + u;
+                    if (!prow || q >= n3) continue;
+                    const size_t e = (size_t)p + (size_t)P * q;
                     const float y = v[u];
-                    const float x = Xs[e], mm = Ms[e];
-                    const float xn = mask[e] ? Bs[e] : y + mm / rbeta;
-                    const float mn = mm + rbeta * (y - xn);
+                    const float x = xv[u], mm = mv[u];
+                    const float xn = kv[u] ? bv[u] : fmaf(mm, rinv, y);
+                    const float mn = fmaf(rbeta, y - xn, mm);
                     const float dx = xn - x, dy = y - xn;
                     sdx = fmaf(dx, dx, sdx);
                     sxx = fmaf(x, x, sxx);
@@ -300,8 +345,9 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
     if (!ok && tid == 0) {
         atomicExch(err, 1);
         // let in-flight copies and MMAs land before the shared memory goes away (bounded)
-        if (!mma_pending) mbar_wait(&bar_b, phase_b ^ 1u);
-        else mbar_wait(&bar_mma, phase_m ^ 1u);
+        for (int t = 0; t < 2; ++t)
+            if (b_pending[t]) mbar_wait(&bar_b[t], phase_b[t]);
+        if (mma_pending) mbar_wait(&bar_mma, phase_m);
     }
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(tmem_cols));
@@ -330,8 +376,8 @@ __global__ void build_operator_tc(float* img, int n3, int NP, int nchunks, int i
                 if (scaled) v *= Cf(k, 0);
             }
         }
-        const float hi = __uint_as_float(__float_as_uint((float)v) & 0xFFFFE000u);
-        const float lo = (float)(v - (double)hi);
+        const float hi = tf32_hi((float)v);
+        const float lo = tf32_hi((float)(v - (double)hi));
         const uint32_t off = (uint32_t)((kk >> 2) * 128 + (n >> 3) * (TKC / 4 * 128) + (n & 7) * 16 + (kk & 3) * 4) / 4;
         img[(size_t)c * 2 * NP * TKC + off] = hi;
         img[(size_t)c * 2 * NP * TKC + (size_t)NP * TKC + off] = lo;
@@ -363,7 +409,7 @@ static cudaError_t launch_tc(const float* in, const float* in2, float* out, cons
     const int NP = tube_tc_np(n3), nc = tube_tc_chunks(n3);
     uint32_t cols = 32;
     while ((int)cols < NP) cols <<= 1;
-    const size_t smem = 2 * (size_t)TBM * TKC * 4 + 2 * (size_t)NP * TKC * 4;
+    const size_t smem = 2 * (size_t)TBM * TKC * 4 + 4 * (size_t)NP * TKC * 4;  // A hi/lo + two B stages
     auto kern = tube_tc_kernel<MODE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -148,3 +148,19 @@ def test_tsvt_invalid_arguments(ctx):
     with pytest.raises(tnn.TnnError) as e:
         ctx.tsvt(tnn.fortran_empty((600, 600, 1), dtype_of("fp32")), 1.0, prec="fp32")
     assert e.value.status == tnn.EINVAL
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+def test_tsvt_msi_shaped(ctx, prec):
+    """The 512 x 512 x 31 multispectral-shaped tensor at full size (slices too
+    large for shared memory: the Jacobi working copies live in L2-resident
+    global scratch)."""
+    d = inputs.config3()
+    Z = d["T"].astype(np.float32).astype(np.float64)
+    for q in (0.9, 0.99):
+        tau = tau_at_quantile(Z, q)
+        Y = _run(ctx, Z, tau, prec)
+        ref = O.tsvt(Z, tau, nthreads=THREADS)
+        err = rel_err(Y, ref, Z)
+        log_err("tsvt msi %s q=%s" % (prec, q), err_y=err, ynorm_over_z=np.linalg.norm(ref) / np.linalg.norm(Z))
+        assert err <= TOL[prec], (q, err)

@@ -159,14 +159,26 @@ struct Regs {
 // sqrt(1 + zeta^2)), c = 1 / sqrt(1 + t^2); reciprocal and reciprocal-square-
 // root forms (no division or square-root slow paths), and one Newton step
 // y <- y (3 - x y^2) / 2 on c so that c^2 (1 + t^2) = 1 to working precision.
+//
+// The tangent is evaluated as t = 2 gam / (D + sign(D) sqrt(D^2 + 4 gam^2))
+// with D = aj - ai (the same value: multiply Rutishauser's numerator and
+// denominator by 2 |gam|), which needs one reciprocal square root and one
+// reciprocal; if D^2 + 4 gam^2 overflows, the zeta form is used.
 template <typename T>
 __device__ __forceinline__ void rot_params(T ai, T aj, T gam, T& t, T& c)
 {
-    const T zeta = (aj - ai) * (T(0.5) * rcp(gam));
-    const T az = fabs(zeta);
-    const T q = T(1) + az * az;
-    const T tt = (az > T(1e15)) ? T(0.5) * rcp(az) : rcp(az + q * rsqrt(q));
-    t = copysign(tt, zeta);
+    const T D = aj - ai, g2 = gam + gam;
+    const T h2 = fma(D, D, g2 * g2);
+    if (h2 < T(INFINITY)) {
+        const T h = h2 * rsqrt(h2);
+        t = g2 * rcp(D + copysign(h, D));
+    } else {
+        const T zeta = D * (T(0.5) * rcp(gam));
+        const T az = fabs(zeta);
+        const T q = T(1) + az * az;
+        const T tt = (az > T(1e15)) ? T(0.5) * rcp(az) : rcp(az + q * rsqrt(q));
+        t = copysign(tt, zeta);
+    }
     const T x = T(1) + t * t;
     T y = rsqrt(x);
     y = y * (T(1.5) - T(0.5) * x * y * y);
@@ -332,10 +344,11 @@ __device__ __forceinline__ void cross_round(Regs<T, K, R, WITHV>& S, Slot<T>& st
         T1[q] = __shfl_sync(FULL, t1, q * G, L);
         T2[q] = __shfl_sync(FULL, t2, q * G, L);
     }
+    // one vote per round; a pair without a rotation has t1 = t2 = 0 and is left exactly as it is
+    if (__any_sync(FULL, t1 != T(0) || t2 != T(0))) {
 #pragma unroll
-    for (int q = 0; q < K; ++q) {
-        const int j = K + (q + r) % K;
-        if (__any_sync(FULL, (T1[q] != T(0)) || (T2[q] != T(0)))) {
+        for (int q = 0; q < K; ++q) {
+            const int j = K + (q + r) % K;
 #pragma unroll
             for (int k = 0; k < R; ++k) {
                 const T x = S.a[q][k], y = S.a[j][k];

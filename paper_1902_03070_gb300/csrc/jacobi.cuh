@@ -130,7 +130,13 @@ template <bool CROSS>
 __host__ __device__ constexpr int pair_j(int K, int r, int p) { return CROSS ? cross_j(K, r, p) : within_j(K, r, p); }
 
 // Block at position t of the circle at step s (nb blocks; position 0 fixed).
-__device__ __forceinline__ int block_at(int nb, int t, int s) { return t == 0 ? 0 : 1 + (t - 1 + s) % (nb - 1); }
+__device__ __forceinline__ int block_at(int nb, int t, int s)
+{
+    if (t == 0) return 0;
+    int v = t - 1 + s;  // < 2 (nb - 1): one conditional subtraction instead of a modulo
+    if (v >= nb - 1) v -= nb - 1;
+    return 1 + v;
+}
 
 // pairs visited, rotations applied, and rotations of pairs whose relative
 // off-diagonality exceeded twice the threshold (only those keep a sweep from

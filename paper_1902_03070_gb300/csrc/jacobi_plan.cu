@@ -20,7 +20,7 @@ struct Variant {
 bool pick_variant(int m, int elem, bool withv, Variant* out)
 {
     static const Variant f32_svt[] = {{16, 4, 0}, {16, 8, 0}, {16, 12, 0}, {32, 8, 0}, {32, 12, 0},
-                                       {32, 16, 0}, {32, 4, 0}, {32, 6, 0}, {16, 12, 2}};
+                                       {32, 16, 0}, {32, 4, 0}, {32, 6, 0}, {16, 12, 2}, {32, 6, 8}};
     static const Variant f64_svt[] = {{16, 2, 0}, {16, 4, 0}, {16, 6, 0}, {32, 4, 0}, {32, 6, 0}, {32, 8, 0},
                                        {32, 16, 0}};
     static const Variant f32_svd[] = {{32, 2, 0}, {32, 4, 0}, {32, 6, 0}, {32, 8, 0}, {32, 12, 0}, {32, 16, 0}};
@@ -29,7 +29,7 @@ bool pick_variant(int m, int elem, bool withv, Variant* out)
     int cnt;
     if (elem == 4) {
         t = withv ? f32_svd : f32_svt;
-        cnt = withv ? 6 : 9;
+        cnt = withv ? 6 : 10;
     } else {
         t = withv ? f64_svd : f64_svt;
         cnt = withv ? 5 : 7;

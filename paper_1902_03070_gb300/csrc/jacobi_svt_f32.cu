@@ -22,6 +22,7 @@ cudaError_t launch_jacobi_svt<float>(const JacobiPlan& p, float* data, double ta
         TNN_JAC_CASE(float, 32, 4, false)
         TNN_JAC_CASE(float, 32, 6, false)
         TNN_JAC_CASE_K(float, 16, 12, 2, false)
+        TNN_JAC_CASE_K(float, 32, 6, 8, false)
     default: return cudaErrorInvalidValue;
     }
 }

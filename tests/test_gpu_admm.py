@@ -88,3 +88,25 @@ def test_completion_48x48x16(ctx, prec):
     if prec == "fp64":
         assert rep["iters"] == rep_o["iters"]
         assert np.linalg.norm(tnn.to_numpy(Xd) - Xo) <= 1e-9 * np.linalg.norm(Xo)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+def test_completion_video_shaped_matches_oracle_final_error(ctx, prec):
+    """144 x 176 x 100 video-shaped completion, 20% observed, 200 iterations:
+    the final relative error against the ground truth is within 1e-4 of the
+    FP64 oracle's (stored by tests/golden/make_admm_golden.py, which calls
+    only the oracle)."""
+    import json
+    import os
+    from paper_1902_03070_gb300 import tnn
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "admm_video_144x176x100.json")
+    gold = json.load(open(path))
+    d = inputs.config2(O.tprod)
+    T, B, mask, prm = d["T"], d["B"], d["mask"], d["admm"]
+    dt = dtype_of(prec)
+    Xd = tnn.fortran_empty(B.shape, dt)
+    st, rep = ctx.complete(tnn.to_fortran(B, dtype=dt), tnn.to_fortran(mask), Xd, ctx.params(**prm), prec=prec)
+    err = np.linalg.norm(tnn.to_numpy(Xd) - T) / np.linalg.norm(T)
+    if prec == "fp64":
+        assert rep["iters"] == gold["iters"]
+    assert abs(err - gold["rel_err_vs_ground_truth"]) <= 1e-4, (err, gold)

@@ -213,6 +213,54 @@ tnn_status tnn_last_jacobi_stats(tnn_ctx* ctx, int64_t out[6]);
 #define TNN_STATIC_SCRATCH_BYTES ((size_t)16 << 20)
 tnn_status tsvt_dct_static(const void* Z, tnn_shape shape, double tau, tnn_precision prec, void* Y, void* stream);
 
+/* Batched t-SVT: one t-SVT (as tsvt_dct) for each of `count` tensors of
+ * different shapes, with the slices of all tensors in the same launches.
+ * A plan is built once for fixed device buffers (items[i].Z in, items[i].Y
+ * out, may be the same buffer; shapes; thresholds tau >= 0) and then run any
+ * number of times on the buffers' current contents.  The plan owns device
+ * memory for the transformed tensors and its launch tables (allocated here,
+ * freed by tnn_tsvt_batch_destroy).  A run launches, on one stream, the
+ * forward tube transforms of all tensors (one grid), one Jacobi SVT launch
+ * per group of slices sharing a kernel variant, and the inverse transforms;
+ * with TNN_BATCH_GRAPH the sequence is recorded once as a CUDA graph and a
+ * run is a single graph launch.  With TNN_BATCH_AUTOTUNE the plan times
+ * every compiled Jacobi variant that covers a group on its own data when it
+ * is created and keeps the fastest (cached per shape class for the process).
+ * Precisions: TNN_FP64 and TNN_FP32 (TNN_FP32_TF32X3 runs as TNN_FP32 here).
+ * Host pointers are rejected (TNN_EINVAL).  Creation synchronises `stream`
+ * and writes no item buffer; runs are stream-ordered and must not overlap one
+ * another (they share the plan's buffers).  Slices are 512 x 512 at most. */
+typedef struct {
+    const void* Z;
+    void* Y;
+    tnn_shape shape;
+    double tau;
+} tnn_tsvt_item;
+typedef struct tnn_tsvt_batch tnn_tsvt_batch;
+#define TNN_BATCH_GRAPH 1
+#define TNN_BATCH_AUTOTUNE 2
+tnn_status tnn_tsvt_batch_create(tnn_ctx* ctx, const tnn_tsvt_item* items, int32_t count, tnn_precision prec,
+                                 int32_t flags, void* stream, tnn_tsvt_batch** plan);
+tnn_status tnn_tsvt_batch_run(tnn_tsvt_batch* plan, void* stream);
+/* out[0] = Jacobi launch groups, out[1] = launches per run (1 with a graph),
+ * out[2] = slices, out[3] = 1 if runs replay a CUDA graph. */
+tnn_status tnn_tsvt_batch_info(const tnn_tsvt_batch* plan, int32_t out[4]);
+/* Group g (0 <= g < groups): out = {L, R, K, slices, 1 if the working
+ * copies are in shared memory, largest m}; (L, R, K) names the Jacobi
+ * variant (L lanes per column-block pair, R rows per lane, K columns per
+ * block). */
+tnn_status tnn_tsvt_batch_group(const tnn_tsvt_batch* plan, int32_t g, int32_t out[6]);
+/* One run without the graph, every launch in order on `stream` with CUDA
+ * events between them; ms[0] = forward transforms, ms[1 + g] = group g's
+ * Jacobi launch, ms[groups + 1] = inverse transforms (groups + 2 values).
+ * Synchronises `stream`; writes the item outputs like a run. */
+tnn_status tnn_tsvt_batch_profile(tnn_tsvt_batch* plan, void* stream, double* ms);
+/* Synchronises `stream`, then sums the statistics of the last run:
+ * out = {slices that hit the sweep cap, slices with a NaN/Inf, rotations,
+ * most sweeps of a slice}.  Returns TNN_ENONFINITE if out[1] > 0. */
+tnn_status tnn_tsvt_batch_stats(tnn_tsvt_batch* plan, void* stream, int64_t out[4]);
+void tnn_tsvt_batch_destroy(tnn_tsvt_batch* plan);
+
 /* Tracing (no counterpart in the paper).  While enabled, every kernel a call
  * launches is bracketed by two CUDA events on the call's stream.
  * tnn_profile_read synchronises on those events, returns per kernel kind the

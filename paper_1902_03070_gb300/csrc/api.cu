@@ -841,6 +841,16 @@ tnn_status tnn_last_jacobi_stats(tnn_ctx* ctx, int64_t out[6])
     return TNN_OK;
 }
 
+}  // extern "C"
+
+namespace tnn {
+tnn_status ctx_fail(tnn_ctx* ctx, tnn_status s, const char* msg) { return fail(ctx, s, "%s", msg); }
+int ctx_device(const tnn_ctx* ctx) { return ctx->device; }
+bool is_device_pointer(const void* p) { return is_device_ptr(p); }
+}  // namespace tnn
+
+extern "C" {
+
 tnn_status tnn_profile(tnn_ctx* ctx, int enable)
 {
     if (!ctx) return TNN_EINVAL;

@@ -583,6 +583,7 @@ struct KArgs {
     T* U;               // SVD outputs
     T* S;
     T* V;
+    const SliceItem* items;  // batched SVT: per-CTA slice parameters (replace the fields above)
 };
 
 // Shared-memory carve-up (bytes) for a launch: dsc, sig, cf, carried norms
@@ -604,7 +605,7 @@ struct Bound {
     static constexpr int value = t > 1024 ? 1024 : t;
 };
 
-template <typename T, int K, int R, int L, bool SMEM, bool WITHV>
+template <typename T, int K, int R, int L, bool SMEM, bool WITHV, bool ITEMS = false>
 __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KArgs<T> a)
 {
     if (a.ctl && a.ctl->done) return;
@@ -613,10 +614,14 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
     const int W = blockDim.x >> 5;
     const int nthr = blockDim.x;
     const int slice = blockIdx.x;
-    const int m = a.m, n = a.n, nb = a.nb, ldA = a.ldA, tr = a.tr;
+    const SliceItem* item = ITEMS ? a.items + slice : nullptr;  // batched: per-CTA slice parameters
+    const int m = item ? item->m : a.m, n = item ? item->n : a.n, nb = item ? item->nb : a.nb;
+    const int ldA = a.ldA, tr = item ? item->tr : a.tr;
     const int npad = nb * K;
-    const int64_t n1 = a.n1;
+    const int64_t n1 = item ? item->n1 : a.n1, n2 = item ? item->n2 : a.n2;
     const size_t wsz = (size_t)ldA * npad;
+    // per-CTA working copy stride in global scratch: sized for the launch's largest slice
+    const size_t wstride = (size_t)ldA * a.nb * K;
     constexpr int GPW = 32 / L;  // groups per warp
     const int hl = lane % L;
     const int NG = W * GPW;
@@ -629,7 +634,7 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
         if (WITHV) Vw = Aw + wsz;
         rest = smem_raw + (WITHV ? 2 : 1) * ((wsz * sizeof(T) + 255) & ~(size_t)255);
     } else {
-        Aw = a.work + (size_t)slice * (WITHV ? 2 : 1) * wsz;
+        Aw = a.work + (size_t)slice * (WITHV ? 2 : 1) * wstride;
         if (WITHV) Vw = Aw + wsz;
         rest = smem_raw;
     }
@@ -644,7 +649,7 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
     __shared__ double s_nuc;
     __shared__ unsigned long long s_pairs, s_rots;
 
-    T* src = a.data + (size_t)slice * n1 * a.n2;
+    T* src = item ? static_cast<T*>(item->data) : a.data + (size_t)slice * n1 * n2;
 
     // ---- load the oriented slice; pad rows and columns with zeros
     for (size_t e = tid; e < wsz; e += nthr) Aw[e] = T(0);
@@ -654,7 +659,7 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
             Vw[e] = (r == c && c < n) ? T(1) : T(0);
         }
     __syncthreads();
-    const int64_t S = n1 * a.n2;
+    const int64_t S = n1 * n2;
     for (int64_t e = tid; e < S; e += nthr) {
         int i = (int)(e % n1), j = (int)(e / n1);
         // oriented (row, col): (i, j) if n1 >= n2 else (j, i)
@@ -722,7 +727,7 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
     }
     __syncthreads();
 
-    const T tau = a.ctl ? (T)(1.0 / a.ctl->beta) : (T)a.tau;
+    const T tau = a.ctl ? (T)(1.0 / a.ctl->beta) : (T)(item ? item->tau : a.tau);
 
     if (!WITHV) {
         // ---- SVT: kept columns (sigma > tau) and their coefficients
@@ -833,7 +838,6 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
         }
         __syncthreads();
         const int r = n;  // thin: r = min(n1, n2) = n
-        const int64_t n2 = a.n2;
         for (int c = warp; c < n; c += W) {
             const int pos = rank[c];
             const T nrm = sqrt(cf[c]);
@@ -863,7 +867,8 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
         st.converged = converged;
         st.nonfinite = s_nonfinite;
         st.kept = WITHV ? n : s_keep;
-        a.stats[slice] = st;
+        if (item) *item->stats = st;
+        else a.stats[slice] = st;
     }
 }
 

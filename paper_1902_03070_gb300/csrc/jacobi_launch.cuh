@@ -14,10 +14,11 @@ __host__ __device__ constexpr int pick_K(int elem, int R, bool withv)
     return elem == 4 ? (withv ? (R <= 8 ? 4 : 2) : 4) : (withv ? (R <= 4 ? 4 : 2) : (R <= 8 ? 4 : 2));
 }
 
-template <typename T, int K, int R, int L, bool WITHV>
+template <typename T, int K, int R, int L, bool WITHV, bool ITEMS = false>
 cudaError_t launch_one(const JacobiPlan& p, KArgs<T> a, cudaStream_t s)
 {
-    void (*kern)(KArgs<T>) = p.in_smem ? jacobi_kernel<T, K, R, L, true, WITHV> : jacobi_kernel<T, K, R, L, false, WITHV>;
+    void (*kern)(KArgs<T>) = p.in_smem ? jacobi_kernel<T, K, R, L, true, WITHV, ITEMS>
+                                       : jacobi_kernel<T, K, R, L, false, WITHV, ITEMS>;
     cudaFuncAttributes attr;
     cudaError_t e = cudaFuncGetAttributes(&attr, kern);
     if (e != cudaSuccess) return e;
@@ -49,3 +50,10 @@ cudaError_t launch_one(const JacobiPlan& p, KArgs<T> a, cudaStream_t s)
 #define TNN_JAC_CASE_K(T, L, R, K, WITHV) \
     case L * 1000 + R * 10 + K:           \
         return jac::launch_one<T, K, R, L, WITHV>(p, a, s);
+// The same for the batched (item-table) SVT kernels.
+#define TNN_JAC_CASE_I(T, L, R) \
+    case L * 1000 + R * 10 + jac::pick_K((int)sizeof(T), R, false): \
+        return jac::launch_one<T, jac::pick_K((int)sizeof(T), R, false), R, L, false, true>(p, a, s);
+#define TNN_JAC_CASE_KI(T, L, R, K) \
+    case L * 1000 + R * 10 + K:     \
+        return jac::launch_one<T, K, R, L, false, true>(p, a, s);

@@ -53,14 +53,47 @@ bool pick_variant(int m, int elem, bool withv, Variant* out)
 
 }  // namespace
 
+static bool plan_with(int64_t n1, int64_t n2, int64_t n3, int elem, bool withv, Variant v, JacobiPlan* p);
+
 bool jacobi_plan_mode(int64_t n1, int64_t n2, int64_t n3, int elem, bool withv, JacobiPlan* p)
 {
     if (n1 <= 0 || n2 <= 0 || n3 <= 0) return false;
     const int64_t m = n1 >= n2 ? n1 : n2;
-    const int64_t n = n1 >= n2 ? n2 : n1;
     if (m > 512) return false;
     Variant v;
     if (!pick_variant((int)m, elem, withv, &v)) return false;
+    return plan_with(n1, n2, n3, elem, withv, v, p);
+}
+
+int jacobi_svt_variants(int elem, int* L, int* R, int* K, int max)
+{
+    static const Variant f32[] = {{16, 4, 4}, {16, 8, 4}, {16, 12, 4}, {32, 8, 4}, {32, 12, 4},
+                                  {32, 16, 4}, {32, 4, 4}, {32, 6, 4}, {16, 12, 2}, {32, 6, 8}};
+    static const Variant f64[] = {{16, 2, 4}, {16, 4, 4}, {16, 6, 4}, {32, 4, 4}, {32, 6, 4}, {32, 8, 4},
+                                  {32, 16, 2}};
+    const Variant* t = elem == 4 ? f32 : f64;
+    const int cnt = elem == 4 ? 10 : 7;
+    for (int i = 0; i < cnt && i < max; ++i) {
+        L[i] = t[i].L;
+        R[i] = t[i].R;
+        K[i] = t[i].K;
+    }
+    return cnt;
+}
+
+bool jacobi_plan_variant(int64_t n1, int64_t n2, int64_t n3, int elem, int L, int R, int K, JacobiPlan* p)
+{
+    if (n1 <= 0 || n2 <= 0 || n3 <= 0) return false;
+    const int64_t m = n1 >= n2 ? n1 : n2;
+    if (m > (int64_t)L * R) return false;
+    Variant v{L, R, K};
+    return plan_with(n1, n2, n3, elem, false, v, p);
+}
+
+static bool plan_with(int64_t n1, int64_t n2, int64_t n3, int elem, bool withv, Variant v, JacobiPlan* p)
+{
+    const int64_t m = n1 >= n2 ? n1 : n2;
+    const int64_t n = n1 >= n2 ? n2 : n1;
     const int K = v.K ? v.K : jac::pick_K(elem, v.R, withv);
     p->n1 = n1; p->n2 = n2; p->n3 = n3;
     p->m = (int)m; p->n = (int)n; p->tr = n1 < n2 ? 1 : 0;

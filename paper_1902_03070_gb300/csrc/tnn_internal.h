@@ -95,6 +95,16 @@ cudaError_t launch_tube_tc_inv_admm(const float* Ybar, float* X, float* M, const
                                     int* nblocks, int* err, cudaStream_t s);
 
 // ---- Jacobi SVT / SVD (jacobi.cu) -------------------------------------------
+// One frontal slice of a batched SVT launch (slices of different tensors and
+// shapes in one grid, one CTA each).
+struct SliceItem {
+    void* data;         // the slice (n1 x n2, leading dimension n1), overwritten by its SVT
+    int n1, n2;         // slice shape
+    int m, n, tr, nb;   // oriented shape (m >= n), transposed flag, column blocks
+    double tau;         // threshold
+    SliceStats* stats;  // where the slice's statistics go
+};
+
 enum JacobiMode { JAC_SVT = 0, JAC_SVD = 1 };
 
 struct JacobiPlan {
@@ -123,11 +133,45 @@ template <typename T>
 cudaError_t launch_jacobi_svt(const JacobiPlan& plan, T* data, double tau, const AdmmCtl* ctl, int max_sweeps,
                               void* work, SliceStats* stats, cudaStream_t s);
 
+// SVT of a list of slices (device array of `count` SliceItems) that all use
+// the variant of `plan` (K, RA, L, ldA, in_smem); plan.nb and plan.n3 must be
+// the largest block count and the item count.  `work` holds count x the
+// per-slice working copy when the variant does not keep it in shared memory.
+template <typename T>
+cudaError_t launch_jacobi_svt_items(const JacobiPlan& plan, const SliceItem* items, int count, int max_sweeps,
+                                    void* work, cudaStream_t s);
+
 // SVD of every frontal slice of `data` (not modified):  U (n1 x r per slice),
 // sigma (r per slice, descending), V (n2 x r per slice), r = min(n1, n2).
 template <typename T>
 cudaError_t launch_jacobi_svd(const JacobiPlan& plan, const T* data, T* U, T* sigma, T* V, int max_sweeps,
                               void* work, SliceStats* stats, cudaStream_t s);
+
+// Compiled SVT variants for an element size: fills up to `max` (L, R, K)
+// triples, returns how many exist.
+int jacobi_svt_variants(int elem, int* L, int* R, int* K, int max);
+// Plan for one given variant (false if it does not cover the shape).
+bool jacobi_plan_variant(int64_t n1, int64_t n2, int64_t n3, int elem, int L, int R, int K, JacobiPlan* plan);
+
+// ---- batched tube transforms (batch.cu) -------------------------------------
+// One 128-pixel tile of one tensor's plain tube transform.
+struct TubeItem {
+    const void* in;
+    void* out;
+    const void* op;  // that tensor's n3 x n3 operator (launch_build_operator)
+    int64_t P;       // pixels of the tensor
+    int64_t p0;      // first pixel of the tile
+    int n3;
+    int pad_;
+};
+template <typename T>
+cudaError_t launch_tube_batched(const TubeItem* items, int count, cudaStream_t s);
+int tube_batched_tile();
+
+// ---- context hooks for entry points outside api.cu ------------------------------
+tnn_status ctx_fail(tnn_ctx* ctx, tnn_status s, const char* msg);
+int ctx_device(const tnn_ctx* ctx);
+bool is_device_pointer(const void* p);
 
 // ---- facewise products (facewise.cu) -------------------------------------------
 // C_k = op(A_k) * B_k for k < nb, A_k m x kk (or kk x m if transA), B_k kk x n,

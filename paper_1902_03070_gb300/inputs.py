@@ -140,6 +140,14 @@ def config4(tprod, count=64, seed_offset=0):
     return tensors
 
 
+def config4_tau(n1, n2, noise=1e-3, factor=2.0):
+    """Per-tensor threshold of the batched workload: `factor` times the edge
+    sqrt(n1) + sqrt(n2) of the singular values of an n1 x n2 slice of i.i.d.
+    N(0, noise^2) entries (the orthonormal DCT along tubes keeps the noise
+    i.i.d.), so the t-SVT removes the noise and keeps the low-rank part."""
+    return float(factor * noise * (np.sqrt(n1) + np.sqrt(n2)))
+
+
 def random_tensor(shape, rng, dist="normal"):
     if dist == "normal":
         return fortran(rng.standard_normal(shape))

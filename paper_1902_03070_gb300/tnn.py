@@ -85,13 +85,38 @@ _lib.tnn_profile_read.argtypes = [_vp, _ct.POINTER(_ct.c_double), _ct.POINTER(_c
 _lib.tnn_profile_read.restype = _st
 _lib.tsvt_dct_static.argtypes = [_vp, Shape, _ct.c_double, _ct.c_int, _vp, _vp]
 _lib.tsvt_dct_static.restype = _st
+
+
+class TsvtItem(_ct.Structure):
+    _fields_ = [("Z", _vp), ("Y", _vp), ("shape", Shape), ("tau", _ct.c_double)]
+
+
+_lib.tnn_tsvt_batch_create.argtypes = [_vp, _ct.POINTER(TsvtItem), _ct.c_int32, _ct.c_int, _ct.c_int32, _vp,
+                                       _ct.POINTER(_vp)]
+_lib.tnn_tsvt_batch_create.restype = _st
+_lib.tnn_tsvt_batch_run.argtypes = [_vp, _vp]
+_lib.tnn_tsvt_batch_run.restype = _st
+_lib.tnn_tsvt_batch_info.argtypes = [_vp, _ct.POINTER(_ct.c_int32)]
+_lib.tnn_tsvt_batch_info.restype = _st
+_lib.tnn_tsvt_batch_group.argtypes = [_vp, _ct.c_int32, _ct.POINTER(_ct.c_int32)]
+_lib.tnn_tsvt_batch_group.restype = _st
+_lib.tnn_tsvt_batch_profile.argtypes = [_vp, _vp, _ct.POINTER(_ct.c_double)]
+_lib.tnn_tsvt_batch_profile.restype = _st
+_lib.tnn_tsvt_batch_stats.argtypes = [_vp, _vp, _ct.POINTER(_ct.c_int64)]
+_lib.tnn_tsvt_batch_stats.restype = _st
+_lib.tnn_tsvt_batch_destroy.argtypes = [_vp]
+_lib.tnn_tsvt_batch_destroy.restype = None
+BATCH_GRAPH = 1
+BATCH_AUTOTUNE = 2
 NKERNELS = 9
 KERNEL_KINDS = ["tube", "tube_fwd_admm", "jacobi_svt", "tube_inv_admm", "admm_finalize", "ctl_init", "admm_init",
                 "jacobi_svd", "facewise"]
 
 EXPORTS = ["tnn_create", "tnn_destroy", "tnn_status_string", "tnn_last_error", "tnn_reserve", "tnn_workspace_size",
            "tdct3", "tsvt_dct", "tsvd_dct_forward", "tsvd_dct_inverse", "tprod_dct", "tnn_complete",
-           "tnn_admm_iterate", "tnn_last_jacobi_stats", "tnn_profile", "tnn_profile_read", "tsvt_dct_static"]
+           "tnn_admm_iterate", "tnn_last_jacobi_stats", "tnn_profile", "tnn_profile_read", "tsvt_dct_static",
+           "tnn_tsvt_batch_create", "tnn_tsvt_batch_run", "tnn_tsvt_batch_info", "tnn_tsvt_batch_group",
+           "tnn_tsvt_batch_profile", "tnn_tsvt_batch_stats", "tnn_tsvt_batch_destroy"]
 
 
 class TnnError(RuntimeError):
@@ -301,6 +326,29 @@ class Context:
         self._chk(st, "tnn_admm_iterate")
         return b.value, rep.as_dict()
 
+    def tsvt_batch(self, Zs, taus, Ys=None, prec="fp32", graph=True, autotune=False):
+        """Plan for Y_i = t-SVT_{tau_i}(Z_i) over device tensors of different
+        shapes (Theorem 5 per tensor).  Returns a TsvtBatch; call .run()."""
+        if Ys is None:
+            Ys = Zs
+        if not (len(Zs) == len(Ys) == len(taus)) or not Zs:
+            raise ValueError("Zs, Ys and taus must be non-empty and of equal length")
+        arr = (TsvtItem * len(Zs))()
+        for i, (Z, Y, t) in enumerate(zip(Zs, Ys, taus)):
+            if len(Z.shape) != 3:
+                raise ValueError("pass 3-way tensors (n1, n2, n3)")
+            _check_layout(Z, Z.shape)
+            _check_layout(Y, Z.shape)
+            _dtype_ok(Z, prec)
+            _dtype_ok(Y, prec)
+            arr[i] = TsvtItem(_ptr(Z)[0], _ptr(Y)[0], Shape(*Z.shape), float(t))
+        flags = (BATCH_GRAPH if graph else 0) | (BATCH_AUTOTUNE if autotune else 0)
+        h = _vp()
+        stream = _stream(list(Zs) + list(Ys))
+        self._chk(_lib.tnn_tsvt_batch_create(self._h, arr, len(Zs), PRECISIONS[prec], flags, stream, _ct.byref(h)),
+                  "tnn_tsvt_batch_create")
+        return TsvtBatch(h, list(Zs), list(Ys))
+
     def last_jacobi_stats(self):
         out = (_ct.c_int64 * 6)()
         self._chk(_lib.tnn_last_jacobi_stats(self._h, out), "tnn_last_jacobi_stats")
@@ -317,3 +365,65 @@ class Context:
         cnt = (_ct.c_int64 * NKERNELS)()
         self._chk(_lib.tnn_profile_read(self._h, ms, cnt), "tnn_profile_read")
         return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_KINDS) if cnt[i]}
+
+
+class TsvtBatch:
+    """A batched t-SVT plan (tnn_tsvt_batch_*); keeps its tensors alive."""
+
+    def __init__(self, h, Zs, Ys):
+        self._h = h
+        self._keep = (Zs, Ys)
+
+    def _stream(self):
+        return _stream(self._keep[0])
+
+    def run(self):
+        st = _lib.tnn_tsvt_batch_run(self._h, self._stream())
+        if st != OK:
+            raise TnnError(st, "tnn_tsvt_batch_run")
+
+    def info(self):
+        out = (_ct.c_int32 * 4)()
+        st = _lib.tnn_tsvt_batch_info(self._h, out)
+        if st != OK:
+            raise TnnError(st, "tnn_tsvt_batch_info")
+        return dict(zip(["groups", "launches", "slices", "graph"], list(out)))
+
+    def groups(self):
+        res = []
+        for g in range(self.info()["groups"]):
+            out = (_ct.c_int32 * 6)()
+            st = _lib.tnn_tsvt_batch_group(self._h, g, out)
+            if st != OK:
+                raise TnnError(st, "tnn_tsvt_batch_group")
+            res.append(dict(zip(["L", "R", "K", "slices", "in_smem", "m"], list(out))))
+        return res
+
+    def profile(self):
+        """Milliseconds of each launch of one serial run:
+        {"forward": ms, "groups": [ms, ...], "inverse": ms}."""
+        n = self.info()["groups"]
+        ms = (_ct.c_double * (n + 2))()
+        st = _lib.tnn_tsvt_batch_profile(self._h, self._stream(), ms)
+        if st != OK:
+            raise TnnError(st, "tnn_tsvt_batch_profile")
+        return {"forward": ms[0], "groups": list(ms[1:n + 1]), "inverse": ms[n + 1]}
+
+    def stats(self):
+        out = (_ct.c_int64 * 4)()
+        st = _lib.tnn_tsvt_batch_stats(self._h, self._stream(), out)
+        if st not in (OK, ENONFINITE):
+            raise TnnError(st, "tnn_tsvt_batch_stats")
+        return dict(zip(["unconverged", "nonfinite", "rotations", "max_sweeps"], list(out)))
+
+    def close(self):
+        if self._h:
+            _lib.tnn_tsvt_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

@@ -248,7 +248,8 @@ tnn_status tnn_tsvt_batch_info(const tnn_tsvt_batch* plan, int32_t out[4]);
 /* Group g (0 <= g < groups): out = {L, R, K, slices, 1 if the working
  * copies are in shared memory, largest m}; (L, R, K) names the Jacobi
  * variant (L lanes per column-block pair, R rows per lane, K columns per
- * block). */
+ * block).  Slices too large for one CTA are spread over thread-block
+ * clusters (their group reports in_smem = 1 + cluster size). */
 tnn_status tnn_tsvt_batch_group(const tnn_tsvt_batch* plan, int32_t g, int32_t out[6]);
 /* One run without the graph, every launch in order on `stream` with CUDA
  * events between them; ms[0] = forward transforms, ms[1 + g] = group g's

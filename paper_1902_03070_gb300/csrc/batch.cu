@@ -169,9 +169,11 @@ std::vector<SliceItem> group_slices(const tnn_tsvt_batch& b, const std::vector<i
     });
     std::vector<SliceItem> out;
     int so = stats_off;
+    // block count of a slice: even; with clusters of C, a multiple of 4C
+    const int q = gp.cluster > 1 ? 4 * gp.cluster : 2;
     for (int t : order) {
         const Shape s = shape_of(b.items[t].shape);
-        const int nb = 2 * ((s.n + 2 * gp.K - 1) / (2 * gp.K));
+        const int nb = q * ((s.n + q * gp.K - 1) / (q * gp.K));
         for (int k = 0; k < s.n3; ++k) {
             SliceItem it;
             it.data = wbuf[t] + (size_t)k * s.n1 * s.n2 * b.elem;
@@ -298,14 +300,15 @@ tnn_status tnn_tsvt_batch_create(tnn_ctx* ctx, const tnn_tsvt_item* items, int32
         if ((call) != cudaSuccess) return bail(TNN_ECUDA, msg); \
     } while (0)
 
-    // ---- groups: tensors by the variant each would use alone and by
-    // whether its working copies fit in shared memory (a slice that fits is
-    // never moved to global memory by a larger one in its group)
-    std::map<std::pair<int, int>, std::vector<int>> by_variant;
+    // ---- groups: tensors by the plan each would get alone: variant,
+    // whether its working copies fit in one CTA's shared memory, and the
+    // cluster that holds a slice too large for one CTA (a slice that fits is
+    // never moved to global memory or a cluster by a larger one in its group)
+    std::map<std::tuple<int, int, int>, std::vector<int>> by_variant;
     for (int i = 0; i < count; ++i) {
         JacobiPlan jp;
-        jacobi_plan(items[i].shape.n1, items[i].shape.n2, items[i].shape.n3, elem, &jp);
-        by_variant[std::make_pair(variant_key(jp), (int)jp.in_smem)].push_back(i);
+        jacobi_plan_mode(items[i].shape.n1, items[i].shape.n2, items[i].shape.n3, elem, false, &jp, true);
+        by_variant[std::make_tuple(variant_key(jp), (int)jp.in_smem, jp.cluster)].push_back(i);
     }
 
     // ---- memory A: transformed tensors, operators, statistics, tube tables
@@ -375,12 +378,13 @@ tnn_status tnn_tsvt_batch_create(tnn_ctx* ctx, const tnn_tsvt_item* items, int32
     }
 
     // ---- group plans (default variant, or the autotuner's choice)
-    struct G { std::vector<int> tensors; int mmax = 0, nmax = 0, count = 0; double cost = 0; int key = 0; };
+    struct G { std::vector<int> tensors; int mmax = 0, nmax = 0, count = 0; double cost = 0; int key = 0, cluster = 0; };
     std::vector<G> gs;
     for (auto& kv : by_variant) {
         G g;
         g.tensors = kv.second;
-        g.key = kv.first.first;
+        g.key = std::get<0>(kv.first);
+        g.cluster = std::get<2>(kv.first);
         for (int t : g.tensors) {
             Shape sh = shape_of(items[t].shape);
             g.mmax = std::max(g.mmax, sh.m);
@@ -406,6 +410,10 @@ tnn_status tnn_tsvt_batch_create(tnn_ctx* ctx, const tnn_tsvt_item* items, int32
         int stats_off = 0;
         for (size_t gi = 0; gi < gs.size(); ++gi) {
             const G& g = gs[gi];
+            if (g.cluster > 1) {  // cluster groups keep their variant
+                stats_off += g.count;
+                continue;
+            }
             const auto key = std::make_tuple(elem, g.mmax, g.nmax, g.count);
             {
                 std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -462,9 +470,14 @@ tnn_status tnn_tsvt_batch_create(tnn_ctx* ctx, const tnn_tsvt_item* items, int32
     std::vector<size_t> woff(gs.size(), 0);
     for (size_t gi = 0; gi < gs.size(); ++gi) {
         tnn_tsvt_batch::Group grp;
-        if (!group_plan(elem, std::get<0>(chosen[gi]), std::get<1>(chosen[gi]), std::get<2>(chosen[gi]), gs[gi].mmax,
-                        gs[gi].nmax, gs[gi].count, &grp.plan))
+        if (gs[gi].cluster > 1) {
+            if (!jacobi_plan_mode(gs[gi].mmax, gs[gi].nmax, gs[gi].count, elem, false, &grp.plan, true) ||
+                grp.plan.cluster != gs[gi].cluster || variant_key(grp.plan) != gs[gi].key)
+                return bail(TNN_EINVAL, "batch: no cluster plan covers a group");
+        } else if (!group_plan(elem, std::get<0>(chosen[gi]), std::get<1>(chosen[gi]), std::get<2>(chosen[gi]),
+                               gs[gi].mmax, gs[gi].nmax, gs[gi].count, &grp.plan)) {
             return bail(TNN_EINVAL, "batch: no variant covers a group");
+        }
         grp.off = (int)all.size();
         grp.count = gs[gi].count;
         grp.cost = gs[gi].cost;
@@ -549,7 +562,7 @@ tnn_status tnn_tsvt_batch_group(const tnn_tsvt_batch* b, int32_t g, int32_t out[
     out[1] = gr.plan.RA;
     out[2] = gr.plan.K;
     out[3] = gr.count;
-    out[4] = gr.plan.in_smem;
+    out[4] = gr.plan.cluster > 1 ? 1 + gr.plan.cluster : gr.plan.in_smem;
     out[5] = gr.plan.m;
     return TNN_OK;
 }

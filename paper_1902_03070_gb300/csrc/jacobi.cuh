@@ -419,8 +419,13 @@ __device__ __forceinline__ void do_rounds(Regs<T, K, R, WITHV>& S, const T tol, 
 // Load the 2K columns of blocks bI, bJ into the group's registers and the
 // slot state (carried squared norm and scale of I_p and J_p) into the slot.
 template <typename T, int K, int R, int L, bool WITHV>
-__device__ __forceinline__ void load_cols(Regs<T, K, R, WITHV>& S, Slot<T>& st, const T* Aw, const T* Vw,
-                                          const T* dsc, const T* asm_, int ldA, int bI, int bJ, int hl, bool active)
+// Block bI's columns are read from AwI (scales dscI), block bJ's from AwJ
+// (dscJ): the same array for a slice held by one CTA; for a slice spread over
+// a cluster, each base is the owning CTA's array (offset so that global
+// column indices address it).
+__device__ __forceinline__ void load_cols(Regs<T, K, R, WITHV>& S, Slot<T>& st, const T* AwI, const T* AwJ,
+                                          const T* Vw, const T* dscI, const T* dscJ, int ldA, int bI, int bJ,
+                                          int hl, bool active)
 {
     constexpr int VN = VecOf<T, R>::N;
     constexpr int G = L / K;
@@ -428,7 +433,7 @@ __device__ __forceinline__ void load_cols(Regs<T, K, R, WITHV>& S, Slot<T>& st, 
 #pragma unroll
     for (int c = 0; c < 2 * K; ++c) {
         const int col = (c < K) ? bI * K + c : bJ * K + (c - K);
-        const T* src = Aw + (size_t)col * ldA;
+        const T* src = ((c < K) ? AwI : AwJ) + (size_t)col * ldA;
 #pragma unroll
         for (int g = 0; g < R / VN; ++g) {
             const VT x = *reinterpret_cast<const VT*>(src + grow<L, VN>(hl, g * VN));
@@ -449,8 +454,8 @@ __device__ __forceinline__ void load_cols(Regs<T, K, R, WITHV>& S, Slot<T>& st, 
     }
     const int slot = hl / G;
     const int cI = bI * K + slot, cJ = bJ * K + slot;
-    st.dI = dsc[cI];
-    st.dJ = dsc[cJ];
+    st.dI = dscI[cI];
+    st.dJ = dscJ[cJ];
     // fresh squared norms of the 2K columns, ordered (I_0, J_0, I_1, J_1, ...)
     // so that the reduce-scatter leaves I_p and J_p in the two halves of slot p
     T nv[2 * K];
@@ -474,7 +479,6 @@ __device__ __forceinline__ void load_cols(Regs<T, K, R, WITHV>& S, Slot<T>& st, 
     // norms: every off-diagonality test is then NaN, so it never rotates
     st.aI = active ? st.dI * st.dI * sI : T(-1);
     st.aJ = active ? st.dJ * st.dJ * sJ : T(-1);
-    (void)asm_;
 }
 
 // Redundant copy of the 2K column states in every lane (for the within-block
@@ -510,8 +514,8 @@ __device__ __forceinline__ void scatter_state(const Regs<T, K, R, WITHV>& S, Slo
 
 // Write the columns and the slot state back; fold tiny scales into the data.
 template <typename T, int K, int R, int L, bool WITHV>
-__device__ __forceinline__ void store_cols(Regs<T, K, R, WITHV>& S, Slot<T>& st, T* Aw, T* Vw, T* dsc, T* asm_,
-                                           int ldA, int bI, int bJ, int hl, bool active)
+__device__ __forceinline__ void store_cols(Regs<T, K, R, WITHV>& S, Slot<T>& st, T* AwI, T* AwJ, T* Vw, T* dscI,
+                                           T* dscJ, int ldA, int bI, int bJ, int hl, bool active)
 {
     constexpr int VN = VecOf<T, R>::N;
     constexpr int G = L / K;
@@ -542,7 +546,7 @@ __device__ __forceinline__ void store_cols(Regs<T, K, R, WITHV>& S, Slot<T>& st,
 #pragma unroll
     for (int c = 0; c < 2 * K; ++c) {
         const int col = (c < K) ? bI * K + c : bJ * K + (c - K);
-        T* dst = Aw + (size_t)col * ldA;
+        T* dst = ((c < K) ? AwI : AwJ) + (size_t)col * ldA;
 #pragma unroll
         for (int g = 0; g < R / VN; ++g) {
             VT x;
@@ -564,10 +568,9 @@ __device__ __forceinline__ void store_cols(Regs<T, K, R, WITHV>& S, Slot<T>& st,
         }
     }
     if (hl % G == 0) {
-        dsc[bI * K + slot] = st.dI;
-        dsc[bJ * K + slot] = st.dJ;
+        dscI[bI * K + slot] = st.dI;
+        dscJ[bJ * K + slot] = st.dJ;
     }
-    (void)asm_;
 }
 
 template <typename T>
@@ -690,14 +693,14 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
                 Regs<T, K, R, WITHV> Sr;
                 Slot<T> st;
                 const Counters cnt0 = cnt;
-                load_cols<T, K, R, L, WITHV>(Sr, st, Aw, Vw, dsc, anorm, ldA, bI, bJ, hl, active);
+                load_cols<T, K, R, L, WITHV>(Sr, st, Aw, Aw, Vw, dsc, dsc, ldA, bI, bJ, hl, active);
                 if (step == 0) {
                     gather_state<T, K, R, L, WITHV>(Sr, st);
                     do_rounds<T, K, R, L, WITHV, false>(Sr, tol, hl, cnt, std::make_integer_sequence<int, K - 1>{});
                     scatter_state<T, K, R, L, WITHV>(Sr, st, hl);
                 }
                 cross_rounds<T, K, R, L, WITHV>(Sr, st, tol, hl, cnt, std::make_integer_sequence<int, K>{});
-                store_cols<T, K, R, L, WITHV>(Sr, st, Aw, Vw, dsc, anorm, ldA, bI, bJ, hl, active);
+                store_cols<T, K, R, L, WITHV>(Sr, st, Aw, Aw, Vw, dsc, dsc, ldA, bI, bJ, hl, active);
                 if (!active) cnt = cnt0;  // an inactive group's work is discarded, and so are its counts
             }
             __syncthreads();

@@ -1,4 +1,5 @@
 // Batched Jacobi SVT launches (one CTA per SliceItem), float slices.
+#include "jacobi_cluster.cuh"
 #include "jacobi_launch.cuh"
 
 namespace tnn {
@@ -14,6 +15,7 @@ cudaError_t launch_jacobi_svt_items<float>(const JacobiPlan& plan, const SliceIt
     a.nb = p.nb; a.ldA = p.ldA; a.n3 = count;
     a.max_sweeps = max_sweeps;
     a.work = reinterpret_cast<float*>(work);
+    if (p.cluster > 1) return launch_jacobi_svt_cluster<float>(p, a, true, s);
     switch (p.L * 1000 + p.RA * 10 + p.K) {
         TNN_JAC_CASE_I(float, 16, 4)
         TNN_JAC_CASE_I(float, 16, 8)

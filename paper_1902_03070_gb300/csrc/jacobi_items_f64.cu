@@ -1,4 +1,5 @@
 // Batched Jacobi SVT launches (one CTA per SliceItem), double slices.
+#include "jacobi_cluster.cuh"
 #include "jacobi_launch.cuh"
 
 namespace tnn {
@@ -14,6 +15,7 @@ cudaError_t launch_jacobi_svt_items<double>(const JacobiPlan& plan, const SliceI
     a.nb = p.nb; a.ldA = p.ldA; a.n3 = count;
     a.max_sweeps = max_sweeps;
     a.work = reinterpret_cast<double*>(work);
+    if (p.cluster > 1) return launch_jacobi_svt_cluster<double>(p, a, true, s);
     switch (p.L * 1000 + p.RA * 10 + p.K) {
         TNN_JAC_CASE_I(double, 16, 2)
         TNN_JAC_CASE_I(double, 16, 4)

@@ -4,6 +4,7 @@
 #include <stdio.h>
 #include <stdlib.h>
 
+#include "jacobi_cluster.cuh"
 #include "jacobi_launch.cuh"
 
 namespace tnn {
@@ -53,16 +54,17 @@ bool pick_variant(int m, int elem, bool withv, Variant* out)
 
 }  // namespace
 
-static bool plan_with(int64_t n1, int64_t n2, int64_t n3, int elem, bool withv, Variant v, JacobiPlan* p);
+static bool plan_with(int64_t n1, int64_t n2, int64_t n3, int elem, bool withv, Variant v, bool cluster,
+                      JacobiPlan* p);
 
-bool jacobi_plan_mode(int64_t n1, int64_t n2, int64_t n3, int elem, bool withv, JacobiPlan* p)
+bool jacobi_plan_mode(int64_t n1, int64_t n2, int64_t n3, int elem, bool withv, JacobiPlan* p, bool cluster)
 {
     if (n1 <= 0 || n2 <= 0 || n3 <= 0) return false;
     const int64_t m = n1 >= n2 ? n1 : n2;
     if (m > 512) return false;
     Variant v;
     if (!pick_variant((int)m, elem, withv, &v)) return false;
-    return plan_with(n1, n2, n3, elem, withv, v, p);
+    return plan_with(n1, n2, n3, elem, withv, v, cluster, p);
 }
 
 int jacobi_svt_variants(int elem, int* L, int* R, int* K, int max)
@@ -87,10 +89,14 @@ bool jacobi_plan_variant(int64_t n1, int64_t n2, int64_t n3, int elem, int L, in
     const int64_t m = n1 >= n2 ? n1 : n2;
     if (m > (int64_t)L * R) return false;
     Variant v{L, R, K};
-    return plan_with(n1, n2, n3, elem, false, v, p);
+    return plan_with(n1, n2, n3, elem, false, v, false, p);
 }
 
-static bool plan_with(int64_t n1, int64_t n2, int64_t n3, int elem, bool withv, Variant v, JacobiPlan* p)
+bool jacobi_cluster_variant_f32(int L, int R, int K);
+bool jacobi_cluster_variant_f64(int L, int R, int K);
+
+static bool plan_with(int64_t n1, int64_t n2, int64_t n3, int elem, bool withv, Variant v, bool cluster,
+                      JacobiPlan* p)
 {
     const int64_t m = n1 >= n2 ? n1 : n2;
     const int64_t n = n1 >= n2 ? n2 : n1;
@@ -112,6 +118,35 @@ static bool plan_with(int64_t n1, int64_t n2, int64_t n3, int elem, bool withv, 
     p->smem_bytes = p->in_smem ? big + small : small;
     p->work_bytes = p->in_smem ? 0 : (size_t)n3 * (withv ? 2 : 1) * wsz;
     p->W = Wguess;
+    p->cluster = 0;
+    // A slice too large for one CTA's shared memory is spread over a cluster
+    // (the smallest of 2, 4, 8 CTAs that holds it).  TNN_JACOBI_CLUSTER=C
+    // spreads every slice over C CTAs where the variant allows (a tuning
+    // override for benchmarking).
+    const bool has = !withv && (elem == 4 ? jacobi_cluster_variant_f32(v.L, v.R, K)
+                                          : jacobi_cluster_variant_f64(v.L, v.R, K));
+    int force = 0;
+    if (const char* env = getenv("TNN_JACOBI_CLUSTER")) force = atoi(env);
+    if (cluster && has && (!p->in_smem || force > 1)) {
+        for (int C = 2; C <= jac::kMaxCluster; C *= 2) {
+            if (force > 1 && C != force) continue;
+            // 2C super-blocks of an even number s of blocks
+            const int nbC = 4 * C * (int)((n + 4 * C * K - 1) / (4 * C * K));
+            const int npadC = nbC * K, sK = nbC / (2 * C) * K;
+            int W = (nbC / (2 * C) + gpw - 1) / gpw;
+            if (W > 32) W = 32;
+            const size_t smem = jac::cluster_smem_bytes(p->ldA, sK, npadC, elem);
+            if (smem > 226 * 1024) continue;
+            if ((size_t)W * jac::rebuild_jb(v.R, v.L) * npadC > jac::cluster_buf_elems(p->ldA, sK, elem)) continue;
+            p->cluster = C;
+            p->nb = nbC;
+            p->in_smem = 1;
+            p->smem_bytes = smem;
+            p->work_bytes = 0;
+            p->W = W;
+            break;
+        }
+    }
     return true;
 }
 

@@ -1,4 +1,5 @@
 // Jacobi SVT launches, float slices.
+#include "jacobi_cluster.cuh"
 #include "jacobi_launch.cuh"
 
 namespace tnn {
@@ -12,6 +13,7 @@ cudaError_t launch_jacobi_svt<float>(const JacobiPlan& p, float* data, double ta
     a.m = p.m; a.n = p.n; a.tr = p.tr; a.nb = p.nb; a.ldA = p.ldA;
     a.tau = tau; a.ctl = ctl; a.max_sweeps = max_sweeps;
     a.work = reinterpret_cast<float*>(work); a.stats = stats;
+    if (p.cluster > 1) return launch_jacobi_svt_cluster<float>(p, a, false, s);
     switch (p.L * 1000 + p.RA * 10 + p.K) {
         TNN_JAC_CASE(float, 16, 4, false)
         TNN_JAC_CASE(float, 16, 8, false)

@@ -119,13 +119,15 @@ struct JacobiPlan {
     size_t smem_bytes; // dynamic shared memory per CTA
     size_t work_bytes; // global scratch per launch
     int elem;          // sizeof(T)
+    int cluster;       // > 1: each slice spread over a cluster of this many CTAs (SVT only)
 };
 
 // Plan a Jacobi launch for n1 x n2 slices of element size elem (4 or 8).
 // Returns false if the shape is beyond what the kernels support.
 bool jacobi_plan(int64_t n1, int64_t n2, int64_t n3, int elem, JacobiPlan* plan);
 // Same, for the SVD launch (singular vectors kept) when withv is true.
-bool jacobi_plan_mode(int64_t n1, int64_t n2, int64_t n3, int elem, bool withv, JacobiPlan* plan);
+bool jacobi_plan_mode(int64_t n1, int64_t n2, int64_t n3, int elem, bool withv, JacobiPlan* plan,
+                      bool cluster = true);
 
 // SVT of every frontal slice of `data` in place:  data_k <- U (S - tau)_+ V^T.
 // tau = 1 / ctl->beta when ctl is not null (and the launch exits if ctl->done).

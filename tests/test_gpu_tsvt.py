@@ -153,8 +153,7 @@ def test_tsvt_invalid_arguments(ctx):
 @pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
 def test_tsvt_msi_shaped(ctx, prec):
     """The 512 x 512 x 31 multispectral-shaped tensor at full size (slices too
-    large for shared memory: the Jacobi working copies live in L2-resident
-    global scratch)."""
+    large for one CTA's shared memory: each is spread over a cluster of 8)."""
     d = inputs.config3()
     Z = d["T"].astype(np.float32).astype(np.float64)
     for q in (0.9, 0.99):
@@ -164,3 +163,65 @@ def test_tsvt_msi_shaped(ctx, prec):
         err = rel_err(Y, ref, Z)
         log_err("tsvt msi %s q=%s" % (prec, q), err_y=err, ynorm_over_z=np.linalg.norm(ref) / np.linalg.norm(Z))
         assert err <= TOL[prec], (q, err)
+
+
+# slices larger than one CTA's shared memory: spread over clusters of 2, 4
+# or 8 CTAs (tall, wide and ragged column counts).  Gaussian slices this
+# large have dense spectra, and FP32 one-sided Jacobi leaves the columns
+# orthogonal only to the rotation threshold sqrt(m) u (u = 2^-24) each, so
+# the rebuilt slice carries an error of order sqrt(m n) u ||Z||: the FP32
+# bound here is 2 sqrt(m n) u ||Z||_F.
+U32 = 2.0 ** -24
+CLUSTER_SHAPES = [("fp32", (300, 280, 3)), ("fp32", (150, 400, 2)), ("fp32", (512, 512, 2)),
+                  ("fp32", (260, 250, 4)), ("fp64", (200, 150, 3)), ("fp64", (140, 250, 2)),
+                  ("fp64", (400, 300, 2)), ("fp64", (512, 512, 2))]
+
+
+@pytest.mark.parametrize("prec,shape", CLUSTER_SHAPES)
+@pytest.mark.parametrize("q", [0.3, 0.8])
+def test_tsvt_cluster_slices(ctx, prec, shape, q):
+    rng = np.random.default_rng(shape[0] * 7 + shape[1] * 3 + shape[2])
+    Z = inputs.random_tensor(shape, rng)
+    if prec != "fp64":
+        Z = Z.astype(np.float32).astype(np.float64)
+    tau = tau_at_quantile(Z, q)
+    Y = _run(ctx, Z, tau, prec)
+    st = ctx.last_jacobi_stats()
+    assert st["unconverged"] == 0
+    ref = O.tsvt(Z, tau, nthreads=THREADS)
+    err_y = rel_err(Y, ref, Z)
+    err_z = np.linalg.norm(Y - ref) / np.linalg.norm(Z)
+    log_err("tsvt cluster %s %s q=%s" % (prec, shape, q), err_y=err_y, err_z=err_z)
+    if prec == "fp64":
+        assert err_y <= TOL["fp64"]
+    else:
+        m, n = max(shape[:2]), min(shape[:2])
+        assert err_z <= 2.0 * np.sqrt(m * n) * U32, (err_z, err_y)
+
+
+@pytest.mark.parametrize("C", ["2", "4", "8"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_tsvt_forced_cluster(ctx, monkeypatch, prec, C):
+    # slices that fit one CTA, spread over a cluster anyway (a different but
+    # equally cyclic pair ordering): same bounds against the oracle, and the
+    # nuclear norm of the result agrees with the single-CTA kernel's
+    rng = np.random.default_rng(21)
+    shape = (176, 128, 6) if prec == "fp32" else (190, 64, 4)
+    Z = inputs.random_tensor(shape, rng)
+    if prec != "fp64":
+        Z = Z.astype(np.float32).astype(np.float64)
+    tau = tau_at_quantile(Z, 0.5)
+    Y1, t1 = _run(ctx, Z, tau, prec, want_tnn=True)
+    monkeypatch.setenv("TNN_JACOBI_CLUSTER", C)
+    Y2, t2 = _run(ctx, Z, tau, prec, want_tnn=True)
+    assert ctx.last_jacobi_stats()["unconverged"] == 0
+    monkeypatch.delenv("TNN_JACOBI_CLUSTER")
+    ref = O.tsvt(Z, tau, nthreads=THREADS)
+    if prec == "fp64":
+        assert rel_err(Y2, ref, Z) <= TOL["fp64"]
+        assert rel_err(Y1, ref, Z) <= TOL["fp64"]
+    else:
+        bound = 2.0 * np.sqrt(shape[0] * shape[1]) * U32 * np.linalg.norm(Z)
+        assert np.linalg.norm(Y2 - ref) <= bound
+        assert np.linalg.norm(Y1 - ref) <= bound
+    assert abs(t1 - t2) <= (1e-12 if prec == "fp64" else 1e-5) * abs(t1)

@@ -23,7 +23,7 @@ struct tnn_ctx {
     size_t ws_off = 0;           // bump offset during one call
     AdmmCtl* h_ctl = nullptr;    // pinned host mirror of the control block
     std::map<std::tuple<int64_t, int, int, int>, void*> ops;  // (n3, elem, inverse, scaled) -> operator
-    std::map<std::tuple<int64_t, int, int>, float*> tc_ops;   // (n3, inverse, scaled) -> tensor-core images
+    std::map<std::tuple<int64_t, int, int, int>, float*> tc_ops;  // (n3, inverse, scaled, bf16) -> tensor-core images
     int* d_err = nullptr;        // set by a tensor-core kernel whose bounded wait timed out
     SliceStats* last_stats = nullptr;
     int64_t last_n3 = 0;
@@ -184,21 +184,22 @@ tnn_status get_op(tnn_ctx* ctx, int64_t n3, int elem, int inverse, int scaled, c
     return TNN_OK;
 }
 
-// Tensor-core operator images for (n3, inverse, scaled), built once per context.
-tnn_status get_op_tc(tnn_ctx* ctx, int64_t n3, int inverse, int scaled, cudaStream_t s, const float** out)
+// Tensor-core operator images for (n3, inverse, scaled, BF16 or TF32 split),
+// built once per context.
+tnn_status get_op_tc(tnn_ctx* ctx, int64_t n3, int inverse, int scaled, bool bf, cudaStream_t s, const float** out)
 {
-    auto key = std::make_tuple(n3, inverse, scaled);
+    auto key = std::make_tuple(n3, inverse, scaled, bf ? 1 : 0);
     auto it = ctx->tc_ops.find(key);
     if (it != ctx->tc_ops.end()) {
         *out = it->second;
         return TNN_OK;
     }
     float* p = nullptr;
-    if (cudaMalloc(&p, tube_tc_image_floats(n3) * sizeof(float)) != cudaSuccess) {
+    if (cudaMalloc(&p, tube_tc_image_floats(n3, bf) * sizeof(float)) != cudaSuccess) {
         cudaGetLastError();
         return fail(ctx, TNN_ENOMEM, "operator image allocation failed");
     }
-    cudaError_t e = launch_build_operator_tc(p, n3, inverse, scaled, s);
+    cudaError_t e = launch_build_operator_tc(p, n3, inverse, scaled, bf, s);
     if (e != cudaSuccess) {
         cudaFree(p);
         return fail(ctx, TNN_ECUDA, "build_operator_tc: %s", cudaGetErrorString(e));
@@ -209,27 +210,32 @@ tnn_status get_op_tc(tnn_ctx* ctx, int64_t n3, int inverse, int scaled, cudaStre
     return TNN_OK;
 }
 
-bool use_tc(tnn_precision prec, int64_t n3) { return prec == TNN_FP32_TF32X3 && tube_tc_supported(n3); }
+bool use_tc(tnn_precision prec, int64_t n3)
+{
+    return (prec == TNN_FP32_TF32X3 || prec == TNN_FP32_BF16SPLIT) && tube_tc_supported(n3);
+}
 
 // One tube transform direction of a call: CUDA-core operator or tensor-core images.
 struct TubeOp {
     const void* op = nullptr;   // CUDA-core operator (n3 x n3)
     const float* img = nullptr; // tensor-core images
     bool tc = false;
+    bool bf = false;            // BF16 hi/lo split (else 3xTF32)
 };
 
 tnn_status get_tube(tnn_ctx* ctx, tnn_precision prec, int elem, int64_t n3, int inverse, int scaled, cudaStream_t s,
                     TubeOp* t)
 {
     t->tc = use_tc(prec, n3);
-    if (t->tc) return get_op_tc(ctx, n3, inverse, scaled, s, &t->img);
+    t->bf = prec == TNN_FP32_BF16SPLIT;
+    if (t->tc) return get_op_tc(ctx, n3, inverse, scaled, t->bf, s, &t->img);
     return get_op(ctx, n3, elem, inverse, scaled, s, &t->op);
 }
 
 cudaError_t tube_any(tnn_ctx* ctx, int elem, const void* X, void* Y, const TubeOp& t, int64_t P, int64_t n3,
                      cudaStream_t s)
 {
-    if (t.tc) return launch_tube_tc((const float*)X, (float*)Y, t.img, P, n3, ctx->d_err, s);
+    if (t.tc) return launch_tube_tc((const float*)X, (float*)Y, t.img, P, n3, t.bf, ctx->d_err, s);
     return elem == 8 ? launch_tube_op<double>((const double*)X, (double*)Y, (const double*)t.op, P, n3, s)
                      : launch_tube_op<float>((const float*)X, (float*)Y, (const float*)t.op, P, n3, s);
 }
@@ -679,7 +685,7 @@ tnn_status admm_run(tnn_ctx* ctx, const void* B, const uint8_t* mask, const tnn_
             } else {
                 { TRACE(K_TUBE_FWD_ADMM);
                   if (opf.tc)
-                      CK(launch_tube_tc_fwd_admm((const float*)X, (const float*)M, (float*)W, opf.img, P, n3, d_ctl,
+                      CK(launch_tube_tc_fwd_admm((const float*)X, (const float*)M, (float*)W, opf.img, P, n3, opf.bf, d_ctl,
                                                  ctx->d_err, s));
                   else
                       CK(launch_tube_fwd_admm_op<float>((const float*)X, (const float*)M, (float*)W,
@@ -689,7 +695,7 @@ tnn_status admm_run(tnn_ctx* ctx, const void* B, const uint8_t* mask, const tnn_
                 { TRACE(K_TUBE_INV_ADMM);
                   if (opi.tc)
                       CK(launch_tube_tc_inv_admm((const float*)W, (float*)X, (float*)M, (const float*)B, mask,
-                                                 opi.img, P, n3, d_ctl, partials, &nblk, ctx->d_err, s));
+                                                 opi.img, P, n3, opi.bf, d_ctl, partials, &nblk, ctx->d_err, s));
                   else
                       CK(launch_tube_inv_admm_op<float>((const float*)W, (float*)X, (float*)M, (const float*)B, mask,
                                                         (const float*)opi.op, P, n3, d_ctl, partials, &nblk, s)); }

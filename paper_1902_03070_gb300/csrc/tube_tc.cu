@@ -1,4 +1,5 @@
-// Tube transforms on the tcgen05 tensor cores (FP32 data, 3xTF32 split).
+// Tube transforms on the tcgen05 tensor cores (FP32 data, 3xTF32 split or
+// BF16 hi/lo split).
 //
 // out(p, q) = sum_j in(p, j) op(j, q) as a GEMM with M = pixels (a CTA owns
 // 128 of them, the MMA's M), N = output tube positions (n3 rounded up to 16,
@@ -6,7 +7,11 @@
 // chunks of 32.  FP32 accuracy from TF32 products: x = x_hi + x_lo with x_hi
 // x rounded to TF32 (10 mantissa bits) and x_lo = x - x_hi (exact in FP32,
 // at most 2^-11 |x|), and out = A_hi B_hi + A_hi B_lo + A_lo B_hi (the
-// dropped A_lo B_lo term is below 2^-22 relative).
+// dropped A_lo B_lo term is below 2^-22 relative).  The BF16 form splits
+// the same way into two BF16 parts (8 significant bits each, x_lo at most
+// 2^-9 |x|) and runs the three products as kind::f16 MMAs with FP32
+// accumulation: what it drops (A_lo B_lo and the part of x below x_hi + x_lo)
+// is of order 2^-16 relative, a transform error of a few 1e-6.
 //
 // Staging: the 128 threads load the input strip with coalesced loads (the
 // ADMM prologue Z = X - M/beta is applied here), split it and write the
@@ -21,6 +26,7 @@
 // Every mbarrier wait is bounded: on timeout the kernel records an error,
 // stops issuing work, waits (bounded) for what it has in flight, frees its
 // TMEM and returns.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -66,6 +72,16 @@ __host__ __device__ constexpr uint32_t make_idesc_tf32(int M, int N)
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// The same for kind::f16 with A and B both BF16.
+__host__ __device__ constexpr uint32_t make_idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// BF16 bits of x rounded to nearest even, and the rounded value.
+__device__ __forceinline__ uint16_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+__device__ __forceinline__ float bf16_val(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
+
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
@@ -109,6 +125,15 @@ __device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_
         : "memory");
 }
 
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+            dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t* bar)
 {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -128,14 +153,19 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Byte offset of element (row, k) of a K-major tile of TKC columns.
-__device__ __forceinline__ uint32_t kmajor_off(int row, int k)
+// Byte offset of element (row, k) of a K-major tile of TKC columns: core
+// matrices of 8 rows x 16 bytes (4 TF32 or 8 BF16 values of K per row).
+template <bool BF>
+__host__ __device__ __forceinline__ uint32_t kmajor_off(int row, int k)
 {
-    return (uint32_t)((k >> 2) * 128 + (row >> 3) * (TKC / 4 * 128) + (row & 7) * 16 + (k & 3) * 4);
+    constexpr int E = BF ? 8 : 4;  // K values per 16-byte core-matrix row
+    constexpr int ES = BF ? 2 : 4;
+    return (uint32_t)((k / E) * 128 + (row >> 3) * (TKC / E * 128) + (row & 7) * 16 + (k % E) * ES);
 }
 
-// MODE 0: plain; MODE 1: forward with Z = X - M/beta; MODE 2: inverse with the ADMM update.
-template <int MODE>
+// MODE 0: plain; MODE 1: forward with Z = X - M/beta; MODE 2: inverse with the
+// ADMM update.  BF: BF16 hi/lo split (kind::f16) instead of 3xTF32.
+template <int MODE, bool BF>
 __global__ void __launch_bounds__(TTHREADS)
 tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, float* __restrict__ out,
                const float* __restrict__ bimg, int64_t P, int n3, int NP, int nchunks, uint32_t tmem_cols,
@@ -151,12 +181,13 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t p0 = (int64_t)blockIdx.x * TBM;
-    const uint32_t a_bytes = TBM * TKC * 4;          // one A tile (hi or lo)
-    const uint32_t b_bytes = (uint32_t)NP * TKC * 4; // one B tile (hi or lo)
-    float* Ahi = reinterpret_cast<float*>(smem);
-    float* Alo = reinterpret_cast<float*>(smem + a_bytes);
+    constexpr uint32_t ES = BF ? 2 : 4;                // bytes per staged value
+    const uint32_t a_bytes = TBM * TKC * ES;           // one A tile (hi or lo)
+    const uint32_t b_bytes = (uint32_t)NP * TKC * ES;  // one B tile (hi or lo)
+    unsigned char* Ahi = smem;
+    unsigned char* Alo = smem + a_bytes;
     // two stages of operator tiles: stage t holds hi at Bst(t), lo right after
-    auto Bst = [&](int t) { return reinterpret_cast<float*>(smem + 2 * a_bytes + (size_t)t * 2 * b_bytes); };
+    auto Bst = [&](int t) { return smem + 2 * a_bytes + (size_t)t * 2 * b_bytes; };
 
     float rbeta = 1.f, rinv = 1.f;
     if (MODE != 0) {
@@ -179,7 +210,7 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t taddr = s_taddr;
-    const uint32_t idesc = make_idesc_tf32(TBM, NP);
+    const uint32_t idesc = BF ? make_idesc_bf16(TBM, NP) : make_idesc_tf32(TBM, NP);
     const int64_t p = p0 + tid;
     const bool prow = p < P;
 
@@ -190,9 +221,9 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
     auto issue_b = [&](int chunk) {
         const int t = chunk & 1;
         mbar_expect_tx(&bar_b[t], 2 * b_bytes);
-        const float* src = bimg + (size_t)chunk * 2 * NP * TKC;
+        const unsigned char* src = reinterpret_cast<const unsigned char*>(bimg) + (size_t)chunk * 2 * b_bytes;
         bulk_g2s(Bst(t), src, b_bytes, &bar_b[t]);
-        bulk_g2s(Bst(t) + (size_t)NP * TKC, src + (size_t)NP * TKC, b_bytes, &bar_b[t]);
+        bulk_g2s(Bst(t) + b_bytes, src + b_bytes, b_bytes, &bar_b[t]);
         b_pending[t] = true;
     };
     if (tid == 0) issue_b(0);
@@ -219,19 +250,41 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
             }
             if (tid == 0) mma_pending = false;
         }
+        if (!BF) {
 #pragma unroll
-        for (int g = 0; g < TKC / 4; ++g) {
-            float x[4];
+            for (int g = 0; g < TKC / 4; ++g) {
+                float x[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) x[u] = (MODE == 1) ? fmaf(-w[g * 4 + u], rinv, v[g * 4 + u]) : v[g * 4 + u];
-            float4 hi, lo;
-            hi.x = tf32_hi(x[0]); lo.x = x[0] - hi.x;
-            hi.y = tf32_hi(x[1]); lo.y = x[1] - hi.y;
-            hi.z = tf32_hi(x[2]); lo.z = x[2] - hi.z;
-            hi.w = tf32_hi(x[3]); lo.w = x[3] - hi.w;
-            const uint32_t off = kmajor_off(tid, g * 4);
-            *reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(Ahi) + off) = hi;
-            *reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(Alo) + off) = lo;
+                for (int u = 0; u < 4; ++u) x[u] = (MODE == 1) ? fmaf(-w[g * 4 + u], rinv, v[g * 4 + u]) : v[g * 4 + u];
+                float4 hi, lo;
+                hi.x = tf32_hi(x[0]); lo.x = x[0] - hi.x;
+                hi.y = tf32_hi(x[1]); lo.y = x[1] - hi.y;
+                hi.z = tf32_hi(x[2]); lo.z = x[2] - hi.z;
+                hi.w = tf32_hi(x[3]); lo.w = x[3] - hi.w;
+                const uint32_t off = kmajor_off<false>(tid, g * 4);
+                *reinterpret_cast<float4*>(Ahi + off) = hi;
+                *reinterpret_cast<float4*>(Alo + off) = lo;
+            }
+        } else {
+#pragma unroll
+            for (int g = 0; g < TKC / 8; ++g) {
+                uint32_t hw[4], lw[4];
+#pragma unroll
+                for (int u = 0; u < 8; u += 2) {
+                    float x0 = v[g * 8 + u], x1 = v[g * 8 + u + 1];
+                    if (MODE == 1) {
+                        x0 = fmaf(-w[g * 8 + u], rinv, x0);
+                        x1 = fmaf(-w[g * 8 + u + 1], rinv, x1);
+                    }
+                    const uint16_t h0 = bf16_bits(x0), h1 = bf16_bits(x1);
+                    const uint16_t l0 = bf16_bits(x0 - bf16_val(h0)), l1 = bf16_bits(x1 - bf16_val(h1));
+                    hw[u / 2] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+                    lw[u / 2] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+                }
+                const uint32_t off = kmajor_off<true>(tid, g * 8);
+                *reinterpret_cast<uint4*>(Ahi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+                *reinterpret_cast<uint4*>(Alo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+            }
         }
         // make the generic-proxy writes visible to the tensor cores
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -245,18 +298,25 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
                 b_pending[t] = false;
                 phase_b[t] ^= 1;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t sbo = TKC / 4 * 128, lbo = 128;
+                // an MMA takes 32 bytes of K (8 TF32 or 16 BF16 values): two core matrices
+                const uint32_t sbo = TKC / (BF ? 8 : 4) * 128, lbo = 128;
                 const uint32_t bh0 = smem_u32(Bst(t)), bl0 = bh0 + b_bytes;
 #pragma unroll
-                for (int s = 0; s < TKC / 8; ++s) {
+                for (int s = 0; s < TKC * (int)ES / 32; ++s) {
                     const uint32_t koff = (uint32_t)s * 2 * 128;
                     const uint64_t ah = make_desc(smem_u32(Ahi) + koff, lbo, sbo);
                     const uint64_t al = make_desc(smem_u32(Alo) + koff, lbo, sbo);
                     const uint64_t bh = make_desc(bh0 + koff, lbo, sbo);
                     const uint64_t bl = make_desc(bl0 + koff, lbo, sbo);
-                    mma_tf32(taddr, ah, bh, idesc, (c > 0 || s > 0) ? 1u : 0u);
-                    mma_tf32(taddr, ah, bl, idesc, 1u);
-                    mma_tf32(taddr, al, bh, idesc, 1u);
+                    if (BF) {
+                        mma_bf16(taddr, ah, bh, idesc, (c > 0 || s > 0) ? 1u : 0u);
+                        mma_bf16(taddr, ah, bl, idesc, 1u);
+                        mma_bf16(taddr, al, bh, idesc, 1u);
+                    } else {
+                        mma_tf32(taddr, ah, bh, idesc, (c > 0 || s > 0) ? 1u : 0u);
+                        mma_tf32(taddr, ah, bl, idesc, 1u);
+                        mma_tf32(taddr, al, bh, idesc, 1u);
+                    }
                 }
                 mma_commit(&bar_mma);
                 mma_pending = true;
@@ -353,10 +413,10 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(tmem_cols));
 }
 
-// Operator images: for each K chunk, the hi and lo TF32 parts of op(k, n)
-// (k = input position, n = output position) in the K-major core-matrix
-// layout of an NP x TKC tile; zero outside n3 x n3.
-__global__ void build_operator_tc(float* img, int n3, int NP, int nchunks, int inverse, int scaled)
+// Operator images: for each K chunk, the hi and lo parts (TF32, or BF16
+// when bf) of op(k, n) (k = input position, n = output position) in the
+// K-major core-matrix layout of an NP x TKC tile; zero outside n3 x n3.
+__global__ void build_operator_tc(float* img, int n3, int NP, int nchunks, int inverse, int scaled, int bf)
 {
     const int total = nchunks * NP * TKC;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
@@ -376,11 +436,20 @@ __global__ void build_operator_tc(float* img, int n3, int NP, int nchunks, int i
                 if (scaled) v *= Cf(k, 0);
             }
         }
-        const float hi = tf32_hi((float)v);
-        const float lo = tf32_hi((float)(v - (double)hi));
-        const uint32_t off = (uint32_t)((kk >> 2) * 128 + (n >> 3) * (TKC / 4 * 128) + (n & 7) * 16 + (kk & 3) * 4) / 4;
-        img[(size_t)c * 2 * NP * TKC + off] = hi;
-        img[(size_t)c * 2 * NP * TKC + (size_t)NP * TKC + off] = lo;
+        if (!bf) {
+            const float hi = tf32_hi((float)v);
+            const float lo = tf32_hi((float)(v - (double)hi));
+            const uint32_t off = kmajor_off<false>(n, kk) / 4;
+            img[(size_t)c * 2 * NP * TKC + off] = hi;
+            img[(size_t)c * 2 * NP * TKC + (size_t)NP * TKC + off] = lo;
+        } else {
+            const uint16_t hi = bf16_bits((float)v);
+            const uint16_t lo = bf16_bits((float)(v - (double)bf16_val(hi)));
+            uint16_t* b16 = reinterpret_cast<uint16_t*>(img);
+            const uint32_t off = kmajor_off<true>(n, kk) / 2;
+            b16[(size_t)c * 2 * NP * TKC + off] = hi;
+            b16[(size_t)c * 2 * NP * TKC + (size_t)NP * TKC + off] = lo;
+        }
     }
 }
 
@@ -390,27 +459,31 @@ bool tube_tc_supported(int64_t n3) { return n3 >= 1 && n3 <= 256; }
 
 int tube_tc_np(int64_t n3) { return (int)((n3 + 15) / 16 * 16); }
 int tube_tc_chunks(int64_t n3) { return (int)((n3 + TKC - 1) / TKC); }
-size_t tube_tc_image_floats(int64_t n3) { return (size_t)tube_tc_chunks(n3) * 2 * tube_tc_np(n3) * TKC; }
+size_t tube_tc_image_floats(int64_t n3, bool bf)
+{
+    return (size_t)tube_tc_chunks(n3) * 2 * tube_tc_np(n3) * TKC / (bf ? 2 : 1);
+}
 int tube_tc_partials_count(int64_t P) { return (int)((P + TBM - 1) / TBM); }
 
-cudaError_t launch_build_operator_tc(float* img, int64_t n3, int inverse, int scaled, cudaStream_t s)
+cudaError_t launch_build_operator_tc(float* img, int64_t n3, int inverse, int scaled, bool bf, cudaStream_t s)
 {
     const int NP = tube_tc_np(n3), nc = tube_tc_chunks(n3);
     const int total = nc * NP * TKC;
-    build_operator_tc<<<(total + 255) / 256, 256, 0, s>>>(img, (int)n3, NP, nc, inverse, scaled);
+    build_operator_tc<<<(total + 255) / 256, 256, 0, s>>>(img, (int)n3, NP, nc, inverse, scaled, bf ? 1 : 0);
     return cudaGetLastError();
 }
 
-template <int MODE>
-static cudaError_t launch_tc(const float* in, const float* in2, float* out, const float* img, int64_t P, int64_t n3,
-                             const AdmmCtl* ctl, float* X, float* M, const float* B, const uint8_t* mask,
-                             double* partials, int* err, cudaStream_t s)
+template <int MODE, bool BF>
+static cudaError_t launch_tc_as(const float* in, const float* in2, float* out, const float* img, int64_t P,
+                                int64_t n3, const AdmmCtl* ctl, float* X, float* M, const float* B,
+                                const uint8_t* mask, double* partials, int* err, cudaStream_t s)
 {
     const int NP = tube_tc_np(n3), nc = tube_tc_chunks(n3);
     uint32_t cols = 32;
     while ((int)cols < NP) cols <<= 1;
-    const size_t smem = 2 * (size_t)TBM * TKC * 4 + 4 * (size_t)NP * TKC * 4;  // A hi/lo + two B stages
-    auto kern = tube_tc_kernel<MODE>;
+    const size_t es = BF ? 2 : 4;
+    const size_t smem = 2 * (size_t)TBM * TKC * es + 4 * (size_t)NP * TKC * es;  // A hi/lo + two B stages
+    auto kern = tube_tc_kernel<MODE, BF>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)((P + TBM - 1) / TBM);
@@ -418,23 +491,33 @@ static cudaError_t launch_tc(const float* in, const float* in2, float* out, cons
     return cudaGetLastError();
 }
 
-cudaError_t launch_tube_tc(const float* X, float* Y, const float* img, int64_t P, int64_t n3, int* err, cudaStream_t s)
+template <int MODE>
+static cudaError_t launch_tc(bool bf, const float* in, const float* in2, float* out, const float* img, int64_t P,
+                             int64_t n3, const AdmmCtl* ctl, float* X, float* M, const float* B, const uint8_t* mask,
+                             double* partials, int* err, cudaStream_t s)
 {
-    return launch_tc<0>(X, nullptr, Y, img, P, n3, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, err, s);
+    return bf ? launch_tc_as<MODE, true>(in, in2, out, img, P, n3, ctl, X, M, B, mask, partials, err, s)
+              : launch_tc_as<MODE, false>(in, in2, out, img, P, n3, ctl, X, M, B, mask, partials, err, s);
+}
+
+cudaError_t launch_tube_tc(const float* X, float* Y, const float* img, int64_t P, int64_t n3, bool bf, int* err,
+                           cudaStream_t s)
+{
+    return launch_tc<0>(bf, X, nullptr, Y, img, P, n3, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, err, s);
 }
 
 cudaError_t launch_tube_tc_fwd_admm(const float* X, const float* M, float* Zbar, const float* img, int64_t P, int64_t n3,
-                                    const AdmmCtl* ctl, int* err, cudaStream_t s)
+                                    bool bf, const AdmmCtl* ctl, int* err, cudaStream_t s)
 {
-    return launch_tc<1>(X, M, Zbar, img, P, n3, ctl, nullptr, nullptr, nullptr, nullptr, nullptr, err, s);
+    return launch_tc<1>(bf, X, M, Zbar, img, P, n3, ctl, nullptr, nullptr, nullptr, nullptr, nullptr, err, s);
 }
 
 cudaError_t launch_tube_tc_inv_admm(const float* Ybar, float* X, float* M, const float* B, const uint8_t* mask,
-                                    const float* img, int64_t P, int64_t n3, const AdmmCtl* ctl, double* partials,
-                                    int* nblocks, int* err, cudaStream_t s)
+                                    const float* img, int64_t P, int64_t n3, bool bf, const AdmmCtl* ctl,
+                                    double* partials, int* nblocks, int* err, cudaStream_t s)
 {
     *nblocks = tube_tc_partials_count(P);
-    return launch_tc<2>(Ybar, nullptr, nullptr, img, P, n3, ctl, X, M, B, mask, partials, err, s);
+    return launch_tc<2>(bf, Ybar, nullptr, nullptr, img, P, n3, ctl, X, M, B, mask, partials, err, s);
 }
 
 }  // namespace tnn

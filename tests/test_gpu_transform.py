@@ -10,7 +10,9 @@ from paper_1902_03070_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 SHAPES = [(48, 48, 16), (7, 5, 31), (3, 1, 1), (1, 9, 2), (129, 3, 65), (144, 176, 100), (20, 30, 130)]
-TOL = {"fp64": 1e-13, "fp32": 2e-6, "tf32x3": 2e-6}
+# BF16 hi/lo split: each value kept to about 16 significant bits (x_hi +
+# x_lo), and the A_lo B_lo product dropped: 2^-16 relative per term
+TOL = {"fp64": 1e-13, "fp32": 2e-6, "tf32x3": 2e-6, "bf16split": 2.0 ** -16}
 
 
 @pytest.fixture(scope="module")
@@ -21,7 +23,7 @@ def ctx():
         yield c
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "bf16split"])
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("inverse,scaled", [(0, 0), (1, 0), (0, 1), (1, 1)])
 def test_tdct3_matches_oracle(ctx, prec, shape, inverse, scaled):
@@ -37,7 +39,7 @@ def test_tdct3_matches_oracle(ctx, prec, shape, inverse, scaled):
     assert np.linalg.norm(Y - ref) <= TOL[prec] * np.linalg.norm(ref)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "bf16split"])
 @pytest.mark.parametrize("dims", [(4, 3, 5, 6), (48, 3, 48, 16), (1, 7, 2, 3), (70, 65, 66, 9)])
 def test_tprod_matches_oracle(ctx, prec, dims):
     from paper_1902_03070_gb300 import tnn

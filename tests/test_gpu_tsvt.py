@@ -21,7 +21,10 @@ from paper_1902_03070_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-12, "fp32": 1e-5, "tf32x3": 1e-5}
+TOL = {"fp64": 1e-12, "fp32": 1e-5, "tf32x3": 1e-5,
+       # BF16 hi/lo transforms: about 2^-16 relative each way (the Jacobi
+       # stage is FP32 as in the other FP32 forms)
+       "bf16split": 2.0 ** -15}
 
 SHAPES = [
     (48, 48, 16),    # the 48 x 48 x 16 completion workload
@@ -51,7 +54,7 @@ def _run(ctx, Z, tau, prec, want_tnn=False):
     return tnn.to_numpy(out).astype(np.float64)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "bf16split"])
 @pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("q", [0.3, 0.8])
 def test_tsvt_matches_oracle(ctx, prec, shape, q):
@@ -72,7 +75,7 @@ def test_tsvt_matches_oracle(ctx, prec, shape, q):
         assert err_y <= (TOL[prec] if q <= 0.5 else 1e-4), (err_z, err_y)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "bf16split"])
 def test_tsvt_low_rank_plus_noise(ctx, prec):
     # a 48 x 48 x 16 tubal-rank-3 tensor plus noise, threshold above the noise edge
     rng = np.random.default_rng(7)
@@ -89,7 +92,7 @@ def test_tsvt_low_rank_plus_noise(ctx, prec):
     assert abs(tnn_gpu - tnn_ref) <= (1e-12 if prec == "fp64" else 1e-5) * tnn_ref
 
 
-@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "bf16split"])
 def test_tsvt_video_shaped(ctx, prec):
     """The 144 x 176 x 100 video-shaped tensor at full size."""
     parts = inputs.config2_parts()
@@ -104,13 +107,13 @@ def test_tsvt_video_shaped(ctx, prec):
         assert rel_err(Y, ref, Z) <= TOL[prec], q
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "bf16split"])
 def test_tsvt_special_cases(ctx, prec):
     rng = np.random.default_rng(11)
     Z = inputs.random_tensor((20, 12, 6), rng)
     if prec != "fp64":
         Z = Z.astype(np.float32).astype(np.float64)
-    tol = 1e-13 if prec == "fp64" else 2e-6
+    tol = {"fp64": 1e-13, "bf16split": 2.0 ** -15}.get(prec, 2e-6)
     # tau = 0: Y = Z
     Y = _run(ctx, Z, 0.0, prec)
     assert np.linalg.norm(Y - Z) <= tol * np.linalg.norm(Z)
@@ -150,7 +153,7 @@ def test_tsvt_invalid_arguments(ctx):
     assert e.value.status == tnn.EINVAL
 
 
-@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3", "bf16split"])
 def test_tsvt_msi_shaped(ctx, prec):
     """The 512 x 512 x 31 multispectral-shaped tensor at full size (slices too
     large for one CTA's shared memory: each is spread over a cluster of 8)."""

@@ -262,6 +262,48 @@ tnn_status tnn_tsvt_batch_profile(tnn_tsvt_batch* plan, void* stream, double* ms
 tnn_status tnn_tsvt_batch_stats(tnn_tsvt_batch* plan, void* stream, int64_t out[4]);
 void tnn_tsvt_batch_destroy(tnn_tsvt_batch* plan);
 
+/* Completion server (no counterpart in the paper: the serving layer around
+ * Algorithm 1).  A job is a completion problem with tnn_complete's
+ * arguments.  Queued jobs are admitted in submission order while the device
+ * footprint of the admitted ones stays within hbm_cap_bytes (and at most
+ * max_active run); an admitted job keeps B, the mask, X, M, the transformed
+ * tensor and its control block (beta, iteration, stop test) resident on the
+ * device until its result is taken.  Each tnn_server_step retires the jobs
+ * that stopped (stop test or max_iter), admits what now fits, and queues the
+ * next `chunk` iterations of every running job; jobs are spread over
+ * `streams` CUDA streams so their kernels overlap, and a step never waits on
+ * the GPU.  A job runs exactly tnn_complete's kernels on its own buffers, so
+ * its result does not depend on what else is running.  Not thread-safe: one
+ * host thread drives a server. */
+typedef struct {
+    uint64_t hbm_cap_bytes; /* 0: 150e9 */
+    int32_t max_active;     /* 0: no limit beyond the footprint cap */
+    int32_t streams;        /* 0: 8 */
+    int32_t chunk;          /* iterations queued per job per step; 0: 8 */
+    int32_t device;
+} tnn_server_params;
+typedef struct tnn_server tnn_server;
+tnn_status tnn_server_create(const tnn_server_params* params, tnn_server** server);
+/* B (FP64 for TNN_FP64, else FP32) and mask (uint8, 1 = observed), host or
+ * device, must stay valid and unchanged until the job is admitted (state 1).
+ * TNN_EINVAL if the job could never fit the cap or its slices are too large. */
+tnn_status tnn_server_submit(tnn_server* server, const void* B, const uint8_t* mask, tnn_shape shape,
+                             const tnn_admm_params* params, tnn_precision prec, int64_t* job_id);
+/* *finished = jobs that finished (or failed) in this pass (may be NULL). */
+tnn_status tnn_server_step(tnn_server* server, int32_t* finished);
+/* *state: 0 queued, 1 running, 2 finished (result waiting), 3 failed. */
+tnn_status tnn_server_job_state(tnn_server* server, int64_t job_id, int32_t* state);
+/* For a finished or failed job: copies X (host or device X_out, may be NULL),
+ * fills the report and times = {submitted, admitted, finished} in seconds
+ * since the server was created (either may be NULL), frees the job and
+ * returns its status (TNN_OK, TNN_ENOCONV, TNN_ENONFINITE, ...).  TNN_EINVAL
+ * while the job is still queued or running. */
+tnn_status tnn_server_take(tnn_server* server, int64_t job_id, void* X_out, tnn_admm_report* rep, double times[3]);
+/* out = {queued, running, finished not yet taken, device bytes admitted,
+ * peak device bytes admitted, jobs finished so far}. */
+tnn_status tnn_server_stats(const tnn_server* server, int64_t out[6]);
+void tnn_server_destroy(tnn_server* server);
+
 /* Tracing (no counterpart in the paper).  While enabled, every kernel a call
  * launches is bracketed by two CUDA events on the call's stream.
  * tnn_profile_read synchronises on those events, returns per kernel kind the

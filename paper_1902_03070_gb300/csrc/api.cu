@@ -215,14 +215,6 @@ bool use_tc(tnn_precision prec, int64_t n3)
     return (prec == TNN_FP32_TF32X3 || prec == TNN_FP32_BF16SPLIT) && tube_tc_supported(n3);
 }
 
-// One tube transform direction of a call: CUDA-core operator or tensor-core images.
-struct TubeOp {
-    const void* op = nullptr;   // CUDA-core operator (n3 x n3)
-    const float* img = nullptr; // tensor-core images
-    bool tc = false;
-    bool bf = false;            // BF16 hi/lo split (else 3xTF32)
-};
-
 tnn_status get_tube(tnn_ctx* ctx, tnn_precision prec, int elem, int64_t n3, int inverse, int scaled, cudaStream_t s,
                     TubeOp* t)
 {
@@ -653,64 +645,108 @@ namespace {
 
 // ADMM driver shared by tnn_complete and tnn_admm_iterate.  X, M device
 // pointers already hold the state; B and mask are device pointers.
-tnn_status admm_run(tnn_ctx* ctx, const void* B, const uint8_t* mask, const tnn_shape& sh,
-                    const tnn_admm_params* prm, tnn_precision prec, int elem, void* X, void* M, double beta0,
-                    int max_iter,
-                    AdmmCtl* d_ctl, void* W, double* partials, SliceStats* stats, void* jwork,
-                    const JacobiPlan& jp, cudaStream_t s, AdmmCtl* out)
+AdmmJob make_job(const tnn_shape& sh, tnn_precision prec, const tnn_admm_params& prm, const void* B, const void* mask,
+                 void* X, void* M, void* W, AdmmCtl* ctl, double* partials, SliceStats* stats, void* jwork,
+                 const JacobiPlan& jp)
 {
-    const int64_t P = sh.n1 * sh.n2, n3 = sh.n3;
-    TubeOp opf, opi;
+    AdmmJob j;
+    j.sh = sh;
+    j.prec = prec;
+    j.elem = elem_of(prec);
+    j.prm = prm;
+    j.B = B;
+    j.mask = (const uint8_t*)mask;
+    j.X = X;
+    j.M = M;
+    j.W = W;
+    j.ctl = ctl;
+    j.partials = partials;
+    j.stats = stats;
+    j.jwork = jwork;
+    j.jp = jp;
+    return j;
+}
+
+}  // namespace
+
+namespace tnn {
+
+// The job's transform operators (built once per context and n3).
+tnn_status admm_prepare_job(tnn_ctx* ctx, AdmmJob& j, cudaStream_t s)
+{
     tnn_status st;
-    if ((st = get_tube(ctx, prec, elem, n3, 0, 0, s, &opf))) return st;
-    if ((st = get_tube(ctx, prec, elem, n3, 1, 0, s, &opi))) return st;
+    if ((st = get_tube(ctx, j.prec, j.elem, j.sh.n3, 0, 0, s, &j.opf))) return st;
+    return get_tube(ctx, j.prec, j.elem, j.sh.n3, 1, 0, s, &j.opi);
+}
+
+// Queue `iters` iterations of Algorithm 1 for one job on stream s (every
+// kernel reads beta and `done` from the job's device control block).
+tnn_status admm_enqueue_iters(tnn_ctx* ctx, const AdmmJob& j, int iters, cudaStream_t s)
+{
+    const int64_t P = j.sh.n1 * j.sh.n2, n3 = j.sh.n3;
+    const int sweeps = j.prm.jacobi_max_sweeps;
+    const TubeOp& opf = j.opf;
+    const TubeOp& opi = j.opi;
+    for (int q = 0; q < iters; ++q) {
+        int nblk = 0;
+        if (j.elem == 8) {
+            { TRACE(K_TUBE_FWD_ADMM);
+              CK(launch_tube_fwd_admm_op<double>((const double*)j.X, (const double*)j.M, (double*)j.W,
+                                                 (const double*)opf.op, P, n3, j.ctl, s)); }
+            { TRACE(K_JACOBI_SVT);
+              CK(launch_jacobi_svt<double>(j.jp, (double*)j.W, 0.0, j.ctl, sweeps, j.jwork, j.stats, s)); }
+            { TRACE(K_TUBE_INV_ADMM);
+              CK(launch_tube_inv_admm_op<double>((const double*)j.W, (double*)j.X, (double*)j.M, (const double*)j.B,
+                                                 j.mask, (const double*)opi.op, P, n3, j.ctl, j.partials, &nblk, s)); }
+        } else {
+            { TRACE(K_TUBE_FWD_ADMM);
+              if (opf.tc)
+                  CK(launch_tube_tc_fwd_admm((const float*)j.X, (const float*)j.M, (float*)j.W, opf.img, P, n3, opf.bf,
+                                             j.ctl, ctx->d_err, s));
+              else
+                  CK(launch_tube_fwd_admm_op<float>((const float*)j.X, (const float*)j.M, (float*)j.W,
+                                                    (const float*)opf.op, P, n3, j.ctl, s)); }
+            { TRACE(K_JACOBI_SVT);
+              CK(launch_jacobi_svt<float>(j.jp, (float*)j.W, 0.0, j.ctl, sweeps, j.jwork, j.stats, s)); }
+            { TRACE(K_TUBE_INV_ADMM);
+              if (opi.tc)
+                  CK(launch_tube_tc_inv_admm((const float*)j.W, (float*)j.X, (float*)j.M, (const float*)j.B, j.mask,
+                                             opi.img, P, n3, opi.bf, j.ctl, j.partials, &nblk, ctx->d_err, s));
+              else
+                  CK(launch_tube_inv_admm_op<float>((const float*)j.W, (float*)j.X, (float*)j.M, (const float*)j.B,
+                                                    j.mask, (const float*)opi.op, P, n3, j.ctl, j.partials, &nblk, s)); }
+        }
+        { TRACE(K_FINALIZE); CK(launch_admm_finalize(j.ctl, j.partials, nblk, j.stats, n3, s)); }
+    }
+    return TNN_OK;
+}
+
+}  // namespace tnn
+
+namespace {
+
+tnn_status admm_run(tnn_ctx* ctx, AdmmJob& j, double beta0, int max_iter, cudaStream_t s, AdmmCtl* out)
+{
+    tnn_status st;
+    if ((st = admm_prepare_job(ctx, j, s))) return st;
     {
         TRACE(K_CTL_INIT);
-        CK(launch_ctl_init(d_ctl, beta0, prm->rho, prm->beta_max, prm->tol, max_iter, s));
+        CK(launch_ctl_init(j.ctl, beta0, j.prm.rho, j.prm.beta_max, j.prm.tol, max_iter, s));
     }
-    const int sweeps = prm->jacobi_max_sweeps;
     int queued = 0, chunk = 1;
     for (;;) {
-        for (int q = 0; q < chunk && queued < max_iter; ++q, ++queued) {
-            int nblk = 0;
-            if (elem == 8) {
-                { TRACE(K_TUBE_FWD_ADMM);
-                  CK(launch_tube_fwd_admm_op<double>((const double*)X, (const double*)M, (double*)W,
-                                                     (const double*)opf.op, P, n3, d_ctl, s)); }
-                { TRACE(K_JACOBI_SVT);
-                  CK(launch_jacobi_svt<double>(jp, (double*)W, 0.0, d_ctl, sweeps, jwork, stats, s)); }
-                { TRACE(K_TUBE_INV_ADMM);
-                  CK(launch_tube_inv_admm_op<double>((const double*)W, (double*)X, (double*)M, (const double*)B, mask,
-                                                     (const double*)opi.op, P, n3, d_ctl, partials, &nblk, s)); }
-            } else {
-                { TRACE(K_TUBE_FWD_ADMM);
-                  if (opf.tc)
-                      CK(launch_tube_tc_fwd_admm((const float*)X, (const float*)M, (float*)W, opf.img, P, n3, opf.bf, d_ctl,
-                                                 ctx->d_err, s));
-                  else
-                      CK(launch_tube_fwd_admm_op<float>((const float*)X, (const float*)M, (float*)W,
-                                                        (const float*)opf.op, P, n3, d_ctl, s)); }
-                { TRACE(K_JACOBI_SVT);
-                  CK(launch_jacobi_svt<float>(jp, (float*)W, 0.0, d_ctl, sweeps, jwork, stats, s)); }
-                { TRACE(K_TUBE_INV_ADMM);
-                  if (opi.tc)
-                      CK(launch_tube_tc_inv_admm((const float*)W, (float*)X, (float*)M, (const float*)B, mask,
-                                                 opi.img, P, n3, opi.bf, d_ctl, partials, &nblk, ctx->d_err, s));
-                  else
-                      CK(launch_tube_inv_admm_op<float>((const float*)W, (float*)X, (float*)M, (const float*)B, mask,
-                                                        (const float*)opi.op, P, n3, d_ctl, partials, &nblk, s)); }
-            }
-            { TRACE(K_FINALIZE); CK(launch_admm_finalize(d_ctl, partials, nblk, stats, n3, s)); }
-        }
-        CK(cudaMemcpyAsync(ctx->h_ctl, d_ctl, sizeof(AdmmCtl), cudaMemcpyDeviceToHost, s));
+        const int n = chunk < max_iter - queued ? chunk : max_iter - queued;
+        if ((st = admm_enqueue_iters(ctx, j, n, s))) return st;
+        queued += n;
+        CK(cudaMemcpyAsync(ctx->h_ctl, j.ctl, sizeof(AdmmCtl), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         if (ctx->h_ctl->done || queued >= max_iter) break;
         if (chunk < 16) chunk *= 2;
     }
     if ((st = check_tc_error(ctx))) return st;
     *out = *ctx->h_ctl;
-    ctx->last_stats = stats;
-    ctx->last_n3 = n3;
+    ctx->last_stats = j.stats;
+    ctx->last_n3 = j.sh.n3;
     ctx->last_stream = s;
     return TNN_OK;
 }
@@ -772,9 +808,9 @@ tnn_status tnn_complete(tnn_ctx* ctx, const void* B, const uint8_t* mask, tnn_sh
                                                (int64_t)N, s));
     else CK(launch_admm_init<float>((const float*)ab.dev, (const uint8_t*)am.dev, (float*)X, (float*)M, (int64_t)N, s));
     AdmmCtl res;
-    st = admm_run(ctx, ab.dev, (const uint8_t*)am.dev, sh, params, prec, elem, X, M, params->beta0, params->max_iter,
-                  (AdmmCtl*)at(ctx, oC), at(ctx, oW), (double*)at(ctx, oP), (SliceStats*)at(ctx, oS), at(ctx, oJ), jp,
-                  s, &res);
+    AdmmJob job = make_job(sh, prec, *params, ab.dev, am.dev, X, M, at(ctx, oW), (AdmmCtl*)at(ctx, oC),
+                           (double*)at(ctx, oP), (SliceStats*)at(ctx, oS), at(ctx, oJ), jp);
+    st = admm_run(ctx, job, params->beta0, params->max_iter, s, &res);
     if (st) return st;
     if ((st = sg.finish())) return st;
     fill_report(rep, res);
@@ -815,9 +851,9 @@ tnn_status tnn_admm_iterate(tnn_ctx* ctx, const void* B, const uint8_t* mask, tn
     sg.out(amm, ohmm);
     int max_iter = params->max_iter < iters ? params->max_iter : iters;
     AdmmCtl res;
-    st = admm_run(ctx, ab.dev, (const uint8_t*)am.dev, sh, params, prec, elem, ax.dev, amm.dev, *beta, max_iter,
-                  (AdmmCtl*)at(ctx, oC), at(ctx, oW), (double*)at(ctx, oP), (SliceStats*)at(ctx, oS), at(ctx, oJ), jp,
-                  s, &res);
+    AdmmJob job = make_job(sh, prec, *params, ab.dev, am.dev, ax.dev, amm.dev, at(ctx, oW), (AdmmCtl*)at(ctx, oC),
+                           (double*)at(ctx, oP), (SliceStats*)at(ctx, oS), at(ctx, oJ), jp);
+    st = admm_run(ctx, job, *beta, max_iter, s, &res);
     if (st) return st;
     if ((st = sg.finish())) return st;
     *beta = res.beta;
@@ -851,6 +887,7 @@ tnn_status tnn_last_jacobi_stats(tnn_ctx* ctx, int64_t out[6])
 
 namespace tnn {
 tnn_status ctx_fail(tnn_ctx* ctx, tnn_status s, const char* msg) { return fail(ctx, s, "%s", msg); }
+tnn_status ctx_check_tc(tnn_ctx* ctx) { return check_tc_error(ctx); }
 int ctx_device(const tnn_ctx* ctx) { return ctx->device; }
 bool is_device_pointer(const void* p) { return is_device_ptr(p); }
 }  // namespace tnn

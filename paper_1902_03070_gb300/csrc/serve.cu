@@ -1,0 +1,449 @@
+// Completion server: continuous batching of Algorithm 1 jobs on one GPU.
+//
+// Jobs wait in submission order until their device footprint fits under the
+// HBM cap; an admitted job gets one stream-ordered allocation holding B, the
+// mask, X, M, the transformed tensor, its partial sums, Jacobi statistics
+// and control block (beta, iteration, stop test), which stay resident until
+// the result is taken.  Every scheduling pass queues the next chunk of
+// iterations of every running job on its stream (jobs are spread over a
+// fixed set of streams, so different jobs' kernels overlap), then reads the
+// control block back asynchronously; a job whose stop test held or whose
+// iteration cap was reached leaves at the next pass, and its room goes to
+// the next queued job.  The host never waits on the GPU inside a pass.
+//
+// Each job runs exactly the kernels of tnn_complete, on its own buffers, so
+// its result is the same bit for bit whatever else is running.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <deque>
+#include <map>
+#include <memory>
+#include <vector>
+
+#include "tnn_internal.h"
+
+using namespace tnn;
+
+namespace {
+
+size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct SJob {
+    int64_t id = 0;
+    int state = 0;  // 0 queued, 1 running, 2 finished, 3 failed
+    tnn_status result = TNN_OK;
+    tnn_shape sh{};
+    tnn_precision prec = TNN_FP32;
+    tnn_admm_params prm{};
+    const void* B_user = nullptr;
+    const uint8_t* mask_user = nullptr;
+    size_t bytes = 0;
+    void* mem = nullptr;
+    AdmmJob aj{};
+    int lane = -1;
+    int queued = 0;
+    bool in_flight = false;
+    cudaEvent_t ev = nullptr;
+    AdmmCtl* h_ctl = nullptr;  // pinned slot
+    AdmmCtl last{};
+    double t_submit = 0, t_admit = -1, t_finish = -1;
+};
+
+// Device layout of one job (offsets into its allocation).
+struct Layout {
+    size_t B, mask, X, M, W, partials, stats, ctl, jwork, total;
+};
+
+Layout layout_of(const tnn_shape& sh, int elem, const JacobiPlan& jp)
+{
+    const size_t N = (size_t)sh.n1 * sh.n2 * sh.n3, bytes = N * elem;
+    Layout L;
+    size_t o = 0;
+    auto add = [&](size_t b) {
+        const size_t at = o;
+        o += up256(b);
+        return at;
+    };
+    L.B = add(bytes);
+    L.mask = add(N);
+    L.X = add(bytes);
+    L.M = add(bytes);
+    L.W = add(bytes);
+    L.partials = add((size_t)tube_partials_count(sh.n1 * sh.n2, sh.n3) * 4 * sizeof(double));
+    L.stats = add(sizeof(SliceStats) * sh.n3);
+    L.ctl = add(sizeof(AdmmCtl));
+    L.jwork = add(jp.work_bytes);
+    L.total = o;
+    return L;
+}
+
+}  // namespace
+
+struct tnn_server {
+    tnn_server_params p{};
+    tnn_ctx* ctx = nullptr;
+    std::vector<cudaStream_t> lanes;
+    std::vector<int> lane_load;
+    std::deque<int64_t> queue;
+    std::map<int64_t, std::unique_ptr<SJob>> jobs;
+    int64_t next_id = 1;
+    size_t bytes = 0, peak = 0;
+    int running = 0;
+    int64_t completed = 0;
+    std::vector<AdmmCtl*> pinned_blocks;  // 64 control-block slots each
+    std::vector<AdmmCtl*> free_slots;
+    std::chrono::steady_clock::time_point t0;
+
+    double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
+
+    AdmmCtl* slot()
+    {
+        if (free_slots.empty()) {
+            AdmmCtl* blk = nullptr;
+            if (cudaHostAlloc((void**)&blk, 64 * sizeof(AdmmCtl), cudaHostAllocDefault) != cudaSuccess) {
+                cudaGetLastError();
+                return nullptr;
+            }
+            pinned_blocks.push_back(blk);
+            for (int i = 63; i >= 0; --i) free_slots.push_back(blk + i);
+        }
+        AdmmCtl* s = free_slots.back();
+        free_slots.pop_back();
+        return s;
+    }
+};
+
+namespace {
+
+// Admit the job at the head of the queue; false if it must wait.
+bool admit(tnn_server* sv, SJob& j)
+{
+    const int elem = j.prec == TNN_FP64 ? 8 : 4;
+    JacobiPlan jp;
+    jacobi_plan(j.sh.n1, j.sh.n2, j.sh.n3, elem, &jp);
+    const Layout L = layout_of(j.sh, elem, jp);
+    int lane = 0;
+    for (int i = 1; i < (int)sv->lanes.size(); ++i)
+        if (sv->lane_load[i] < sv->lane_load[lane]) lane = i;
+    cudaStream_t s = sv->lanes[lane];
+    void* mem = nullptr;
+    if (cudaMallocAsync(&mem, L.total, s) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    AdmmCtl* hs = sv->slot();
+    cudaEvent_t ev = nullptr;
+    if (!hs || cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        if (hs) sv->free_slots.push_back(hs);
+        cudaFreeAsync(mem, s);
+        return false;
+    }
+    char* c = static_cast<char*>(mem);
+    const size_t N = (size_t)j.sh.n1 * j.sh.n2 * j.sh.n3, bytes = N * elem;
+    j.mem = mem;
+    j.bytes = L.total;
+    j.lane = lane;
+    j.ev = ev;
+    j.h_ctl = hs;
+    j.aj.sh = j.sh;
+    j.aj.prec = j.prec;
+    j.aj.elem = elem;
+    j.aj.prm = j.prm;
+    j.aj.B = c + L.B;
+    j.aj.mask = reinterpret_cast<const uint8_t*>(c + L.mask);
+    j.aj.X = c + L.X;
+    j.aj.M = c + L.M;
+    j.aj.W = c + L.W;
+    j.aj.ctl = reinterpret_cast<AdmmCtl*>(c + L.ctl);
+    j.aj.partials = reinterpret_cast<double*>(c + L.partials);
+    j.aj.stats = reinterpret_cast<SliceStats*>(c + L.stats);
+    j.aj.jwork = jp.work_bytes ? c + L.jwork : nullptr;
+    j.aj.jp = jp;
+    bool ok = cudaMemcpyAsync(c + L.B, j.B_user, bytes, cudaMemcpyDefault, s) == cudaSuccess &&
+              cudaMemcpyAsync(c + L.mask, j.mask_user, N, cudaMemcpyDefault, s) == cudaSuccess;
+    if (ok) {
+        ok = (elem == 8 ? launch_admm_init<double>((const double*)j.aj.B, j.aj.mask, (double*)j.aj.X,
+                                                   (double*)j.aj.M, (int64_t)N, s)
+                        : launch_admm_init<float>((const float*)j.aj.B, j.aj.mask, (float*)j.aj.X, (float*)j.aj.M,
+                                                  (int64_t)N, s)) == cudaSuccess &&
+             launch_ctl_init(j.aj.ctl, j.prm.beta0, j.prm.rho, j.prm.beta_max, j.prm.tol, j.prm.max_iter, s) ==
+                 cudaSuccess &&
+             admm_prepare_job(sv->ctx, j.aj, s) == TNN_OK;
+    }
+    sv->bytes += L.total;
+    if (sv->bytes > sv->peak) sv->peak = sv->bytes;
+    sv->lane_load[lane] += 1;
+    sv->running += 1;
+    j.state = 1;
+    j.t_admit = sv->now();
+    if (!ok) {
+        cudaGetLastError();
+        j.state = 3;
+        j.result = TNN_ECUDA;
+        j.t_finish = j.t_admit;
+        sv->running -= 1;
+        sv->lane_load[lane] -= 1;
+    }
+    return true;
+}
+
+// Bytes a job would hold on the device.
+size_t footprint(const tnn_shape& sh, tnn_precision prec)
+{
+    const int elem = prec == TNN_FP64 ? 8 : 4;
+    JacobiPlan jp;
+    if (!jacobi_plan(sh.n1, sh.n2, sh.n3, elem, &jp)) return 0;
+    return layout_of(sh, elem, jp).total;
+}
+
+void release(tnn_server* sv, SJob& j)
+{
+    if (j.mem) {
+        cudaFreeAsync(j.mem, sv->lanes[j.lane]);
+        sv->bytes -= j.bytes;
+        j.mem = nullptr;
+    }
+    if (j.ev) {
+        cudaEventDestroy(j.ev);
+        j.ev = nullptr;
+    }
+    if (j.h_ctl) {
+        sv->free_slots.push_back(j.h_ctl);
+        j.h_ctl = nullptr;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+tnn_status tnn_server_create(const tnn_server_params* p, tnn_server** out)
+{
+    if (!out) return TNN_EINVAL;
+    *out = nullptr;
+    tnn_server_params q{};
+    if (p) q = *p;
+    if (q.max_active < 0 || q.streams < 0 || q.chunk < 0) return TNN_EINVAL;
+    if (q.hbm_cap_bytes == 0) q.hbm_cap_bytes = 150ull * 1000 * 1000 * 1000;
+    if (q.streams == 0) q.streams = 8;
+    if (q.chunk == 0) q.chunk = 8;
+    std::unique_ptr<tnn_server> sv(new tnn_server);
+    sv->p = q;
+    tnn_status st = tnn_create(&sv->ctx, q.device);
+    if (st != TNN_OK) return st;
+    // keep freed job memory in the stream-ordered pool for the next jobs
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, q.device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+    for (int i = 0; i < q.streams; ++i) {
+        cudaStream_t s = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            for (auto x : sv->lanes) cudaStreamDestroy(x);
+            tnn_destroy(sv->ctx);
+            return TNN_ECUDA;
+        }
+        sv->lanes.push_back(s);
+        sv->lane_load.push_back(0);
+    }
+    sv->t0 = std::chrono::steady_clock::now();
+    *out = sv.release();
+    return TNN_OK;
+}
+
+tnn_status tnn_server_submit(tnn_server* sv, const void* B, const uint8_t* mask, tnn_shape sh,
+                             const tnn_admm_params* prm, tnn_precision prec, int64_t* job_id)
+{
+    if (!sv || !B || !mask || !prm || !job_id) return TNN_EINVAL;
+    if (sh.n1 <= 0 || sh.n2 <= 0 || sh.n3 <= 0) return TNN_EINVAL;
+    if (!(prec == TNN_FP64 || prec == TNN_FP32 || prec == TNN_FP32_TF32X3 || prec == TNN_FP32_BF16SPLIT))
+        return TNN_EINVAL;
+    if (!(prm->beta0 > 0.0) || !(prm->rho > 0.0) || !(prm->beta_max > 0.0) || prm->tol != prm->tol ||
+        prm->max_iter < 0 || prm->jacobi_max_sweeps < 0)
+        return TNN_EINVAL;
+    const size_t fp = footprint(sh, prec);
+    if (fp == 0 || fp > sv->p.hbm_cap_bytes) return TNN_EINVAL;  // slice too large, or never fits the cap
+    std::unique_ptr<SJob> j(new SJob);
+    j->id = sv->next_id++;
+    j->sh = sh;
+    j->prec = prec;
+    j->prm = *prm;
+    j->B_user = B;
+    j->mask_user = mask;
+    j->bytes = fp;
+    j->t_submit = sv->now();
+    *job_id = j->id;
+    sv->queue.push_back(j->id);
+    sv->jobs[j->id] = std::move(j);
+    return TNN_OK;
+}
+
+tnn_status tnn_server_step(tnn_server* sv, int32_t* finished)
+{
+    if (!sv) return TNN_EINVAL;
+    if (cudaSetDevice(sv->p.device) != cudaSuccess) {
+        cudaGetLastError();
+        return TNN_ECUDA;
+    }
+    int nfin = 0;
+    // retire: running jobs whose last chunk has landed and that stopped
+    for (auto& kv : sv->jobs) {
+        SJob& j = *kv.second;
+        if (j.state != 1 || !j.in_flight) continue;
+        const cudaError_t q = cudaEventQuery(j.ev);
+        if (q == cudaErrorNotReady) continue;
+        j.in_flight = false;
+        if (q != cudaSuccess) {
+            cudaGetLastError();
+            j.state = 3;
+            j.result = TNN_ECUDA;
+        } else {
+            j.last = *j.h_ctl;
+            if (!(j.last.done || j.queued >= j.prm.max_iter)) continue;
+            j.state = 2;
+            j.result = j.last.nonfinite ? TNN_ENONFINITE : (j.last.converged ? TNN_OK : TNN_ENOCONV);
+        }
+        j.t_finish = sv->now();
+        sv->running -= 1;
+        sv->lane_load[j.lane] -= 1;
+        sv->completed += 1;
+        ++nfin;
+    }
+    // admit in submission order while the footprint fits
+    while (!sv->queue.empty()) {
+        SJob& j = *sv->jobs[sv->queue.front()];
+        if (sv->p.max_active > 0 && sv->running >= sv->p.max_active) break;
+        if (sv->bytes + j.bytes > sv->p.hbm_cap_bytes) break;
+        if (!admit(sv, j)) {
+            if (sv->running > 0) break;  // retry when running jobs have released memory
+            j.state = 3;                 // nothing left to wait for
+            j.result = TNN_ENOMEM;
+            j.t_finish = sv->now();
+            sv->queue.pop_front();
+            sv->completed += 1;
+            ++nfin;
+            continue;
+        }
+        sv->queue.pop_front();
+        if (j.state == 3) {
+            sv->completed += 1;
+            ++nfin;
+        }
+    }
+    // queue the next chunk of every running job that is not in flight
+    for (auto& kv : sv->jobs) {
+        SJob& j = *kv.second;
+        if (j.state != 1 || j.in_flight) continue;
+        cudaStream_t s = sv->lanes[j.lane];
+        int n = j.prm.max_iter - j.queued;
+        if (n > sv->p.chunk) n = sv->p.chunk;
+        if (n > 0 && admm_enqueue_iters(sv->ctx, j.aj, n, s) != TNN_OK) {
+            j.state = 3;
+            j.result = TNN_ECUDA;
+            j.t_finish = sv->now();
+            sv->running -= 1;
+            sv->lane_load[j.lane] -= 1;
+            sv->completed += 1;
+            ++nfin;
+            continue;
+        }
+        j.queued += n;
+        if (cudaMemcpyAsync(j.h_ctl, j.aj.ctl, sizeof(AdmmCtl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaEventRecord(j.ev, s) != cudaSuccess) {
+            cudaGetLastError();
+            j.state = 3;
+            j.result = TNN_ECUDA;
+            j.t_finish = sv->now();
+            sv->running -= 1;
+            sv->lane_load[j.lane] -= 1;
+            sv->completed += 1;
+            ++nfin;
+            continue;
+        }
+        j.in_flight = true;
+    }
+    if (finished) *finished = nfin;
+    return TNN_OK;
+}
+
+tnn_status tnn_server_job_state(tnn_server* sv, int64_t id, int32_t* state)
+{
+    if (!sv || !state) return TNN_EINVAL;
+    auto it = sv->jobs.find(id);
+    if (it == sv->jobs.end()) return TNN_EINVAL;
+    *state = it->second->state;
+    return TNN_OK;
+}
+
+tnn_status tnn_server_take(tnn_server* sv, int64_t id, void* X_out, tnn_admm_report* rep, double times[3])
+{
+    if (!sv) return TNN_EINVAL;
+    auto it = sv->jobs.find(id);
+    if (it == sv->jobs.end()) return TNN_EINVAL;
+    SJob& j = *it->second;
+    if (j.state < 2) return TNN_EINVAL;  // not finished yet
+    tnn_status res = j.result;
+    if (j.state == 2 && X_out) {
+        const size_t bytes = (size_t)j.sh.n1 * j.sh.n2 * j.sh.n3 * (j.prec == TNN_FP64 ? 8 : 4);
+        cudaStream_t s = sv->lanes[j.lane];
+        if (cudaMemcpyAsync(X_out, j.aj.X, bytes, cudaMemcpyDefault, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            cudaGetLastError();
+            res = TNN_ECUDA;
+        } else if (ctx_check_tc(sv->ctx) != TNN_OK) {
+            res = TNN_ECUDA;
+        }
+    }
+    if (rep) {
+        rep->iters = j.last.iter;
+        rep->converged = j.last.converged;
+        rep->rel_change = j.last.rel_change;
+        rep->primal_res = j.last.primal_res;
+        rep->beta_final = j.last.beta;
+        rep->jacobi_sweeps_max = j.last.sweeps_max;
+        rep->jacobi_unconverged = j.last.unconverged;
+    }
+    if (times) {
+        times[0] = j.t_submit;
+        times[1] = j.t_admit;
+        times[2] = j.t_finish;
+    }
+    if (j.lane >= 0) release(sv, j);
+    sv->jobs.erase(it);
+    return res;
+}
+
+tnn_status tnn_server_stats(const tnn_server* sv, int64_t out[6])
+{
+    if (!sv || !out) return TNN_EINVAL;
+    int64_t fin = 0;
+    for (auto& kv : sv->jobs) fin += kv.second->state >= 2 ? 1 : 0;
+    out[0] = (int64_t)sv->queue.size();
+    out[1] = sv->running;
+    out[2] = fin;
+    out[3] = (int64_t)sv->bytes;
+    out[4] = (int64_t)sv->peak;
+    out[5] = sv->completed;
+    return TNN_OK;
+}
+
+void tnn_server_destroy(tnn_server* sv)
+{
+    if (!sv) return;
+    cudaSetDevice(sv->p.device);
+    for (auto s : sv->lanes) cudaStreamSynchronize(s);
+    for (auto& kv : sv->jobs)
+        if (kv.second->lane >= 0) release(sv, *kv.second);
+    for (auto s : sv->lanes) cudaStreamSynchronize(s);
+    for (auto s : sv->lanes) cudaStreamDestroy(s);
+    for (auto b : sv->pinned_blocks) cudaFreeHost(b);
+    tnn_destroy(sv->ctx);
+    delete sv;
+}
+
+}  // extern "C"

@@ -171,8 +171,42 @@ template <typename T>
 cudaError_t launch_tube_batched(const TubeItem* items, int count, cudaStream_t s);
 int tube_batched_tile();
 
+// ---- one completion job's device state (api.cu) ---------------------------------
+// One tube transform direction: CUDA-core operator or tensor-core images.
+struct TubeOp {
+    const void* op = nullptr;    // CUDA-core operator (n3 x n3)
+    const float* img = nullptr;  // tensor-core images
+    bool tc = false;
+    bool bf = false;             // BF16 hi/lo split (else 3xTF32)
+};
+
+// Everything an ADMM run (Algorithm 1) touches on the device.
+struct AdmmJob {
+    tnn_shape sh;
+    tnn_precision prec;
+    int elem;
+    tnn_admm_params prm;
+    const void* B;
+    const uint8_t* mask;
+    void* X;
+    void* M;
+    void* W;               // transformed tensor (N elements)
+    AdmmCtl* ctl;          // device control block
+    double* partials;      // tube_partials_count(P, n3) x 4
+    SliceStats* stats;     // n3
+    void* jwork;           // plan.work_bytes
+    JacobiPlan jp;
+    TubeOp opf, opi;       // filled by admm_prepare_job
+};
+
+// The job's transform operators, from the context's caches (built on first use).
+tnn_status admm_prepare_job(tnn_ctx* ctx, AdmmJob& j, cudaStream_t s);
+// Queue `iters` iterations on stream s; each exits at once if the job is done.
+tnn_status admm_enqueue_iters(tnn_ctx* ctx, const AdmmJob& j, int iters, cudaStream_t s);
+
 // ---- context hooks for entry points outside api.cu ------------------------------
 tnn_status ctx_fail(tnn_ctx* ctx, tnn_status s, const char* msg);
+tnn_status ctx_check_tc(tnn_ctx* ctx);  // after a synchronisation: a tensor-core wait that timed out
 int ctx_device(const tnn_ctx* ctx);
 bool is_device_pointer(const void* p);
 

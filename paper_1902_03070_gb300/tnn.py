@@ -106,6 +106,27 @@ _lib.tnn_tsvt_batch_stats.argtypes = [_vp, _vp, _ct.POINTER(_ct.c_int64)]
 _lib.tnn_tsvt_batch_stats.restype = _st
 _lib.tnn_tsvt_batch_destroy.argtypes = [_vp]
 _lib.tnn_tsvt_batch_destroy.restype = None
+
+
+class ServerParams(_ct.Structure):
+    _fields_ = [("hbm_cap_bytes", _ct.c_uint64), ("max_active", _ct.c_int32), ("streams", _ct.c_int32),
+                ("chunk", _ct.c_int32), ("device", _ct.c_int32)]
+
+
+_lib.tnn_server_create.argtypes = [_ct.POINTER(ServerParams), _ct.POINTER(_vp)]
+_lib.tnn_server_create.restype = _st
+_lib.tnn_server_submit.argtypes = [_vp, _vp, _vp, Shape, _ct.POINTER(AdmmParams), _ct.c_int, _ct.POINTER(_ct.c_int64)]
+_lib.tnn_server_submit.restype = _st
+_lib.tnn_server_step.argtypes = [_vp, _ct.POINTER(_ct.c_int32)]
+_lib.tnn_server_step.restype = _st
+_lib.tnn_server_job_state.argtypes = [_vp, _ct.c_int64, _ct.POINTER(_ct.c_int32)]
+_lib.tnn_server_job_state.restype = _st
+_lib.tnn_server_take.argtypes = [_vp, _ct.c_int64, _vp, _ct.POINTER(AdmmReport), _ct.POINTER(_ct.c_double)]
+_lib.tnn_server_take.restype = _st
+_lib.tnn_server_stats.argtypes = [_vp, _ct.POINTER(_ct.c_int64)]
+_lib.tnn_server_stats.restype = _st
+_lib.tnn_server_destroy.argtypes = [_vp]
+_lib.tnn_server_destroy.restype = None
 BATCH_GRAPH = 1
 BATCH_AUTOTUNE = 2
 NKERNELS = 9
@@ -116,7 +137,9 @@ EXPORTS = ["tnn_create", "tnn_destroy", "tnn_status_string", "tnn_last_error", "
            "tdct3", "tsvt_dct", "tsvd_dct_forward", "tsvd_dct_inverse", "tprod_dct", "tnn_complete",
            "tnn_admm_iterate", "tnn_last_jacobi_stats", "tnn_profile", "tnn_profile_read", "tsvt_dct_static",
            "tnn_tsvt_batch_create", "tnn_tsvt_batch_run", "tnn_tsvt_batch_info", "tnn_tsvt_batch_group",
-           "tnn_tsvt_batch_profile", "tnn_tsvt_batch_stats", "tnn_tsvt_batch_destroy"]
+           "tnn_tsvt_batch_profile", "tnn_tsvt_batch_stats", "tnn_tsvt_batch_destroy",
+           "tnn_server_create", "tnn_server_submit", "tnn_server_step", "tnn_server_job_state", "tnn_server_take",
+           "tnn_server_stats", "tnn_server_destroy"]
 
 
 class TnnError(RuntimeError):
@@ -420,6 +443,91 @@ class TsvtBatch:
         if self._h:
             _lib.tnn_tsvt_batch_destroy(self._h)
             self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Completion server (tnn_server_*): continuous batching of completion
+    jobs with device-resident state and HBM-footprint admission."""
+
+    QUEUED, RUNNING, FINISHED, FAILED = range(4)
+
+    def __init__(self, hbm_cap_bytes=0, max_active=0, streams=0, chunk=0, device=0):
+        p = ServerParams(int(hbm_cap_bytes), int(max_active), int(streams), int(chunk), int(device))
+        h = _vp()
+        st = _lib.tnn_server_create(_ct.byref(p), _ct.byref(h))
+        if st != OK:
+            raise TnnError(st, "tnn_server_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, B, mask, params, prec="fp32"):
+        """Queue a completion job (B and mask are kept referenced until the
+        result is taken).  Returns the job id."""
+        _check_layout(B, B.shape)
+        _check_layout(mask, B.shape)
+        _dtype_ok(B, prec)
+        jid = _ct.c_int64(0)
+        st = _lib.tnn_server_submit(self._h, _ptr(B)[0], _ptr(mask)[0], Shape(*B.shape), _ct.byref(params),
+                                    PRECISIONS[prec], _ct.byref(jid))
+        if st != OK:
+            raise TnnError(st, "tnn_server_submit")
+        self._keep[jid.value] = (B, mask, tuple(B.shape), prec)
+        return jid.value
+
+    def step(self):
+        """One scheduling pass; returns how many jobs finished in it."""
+        fin = _ct.c_int32(0)
+        st = _lib.tnn_server_step(self._h, _ct.byref(fin))
+        if st != OK:
+            raise TnnError(st, "tnn_server_step")
+        return fin.value
+
+    def state(self, jid):
+        out = _ct.c_int32(0)
+        st = _lib.tnn_server_job_state(self._h, int(jid), _ct.byref(out))
+        if st != OK:
+            raise TnnError(st, "tnn_server_job_state")
+        return out.value
+
+    def take(self, jid, X_out=None):
+        """(status, X, report, (t_submit, t_admit, t_finish)) of a finished
+        job; X is X_out, or a new host array when X_out is None."""
+        import numpy as np
+        B, mask, shape, prec = self._keep[jid]
+        if X_out is None:
+            X_out = np.empty(shape, dtype=np.float64 if prec == "fp64" else np.float32, order="F")
+        rep = AdmmReport()
+        t = (_ct.c_double * 3)()
+        st = _lib.tnn_server_take(self._h, int(jid), _ptr(X_out)[0], _ct.byref(rep), t)
+        if st == EINVAL and self.state(jid) < 2:
+            raise TnnError(st, "tnn_server_take: job %d not finished" % jid)
+        del self._keep[jid]
+        return st, X_out, rep.as_dict(), (t[0], t[1], t[2])
+
+    def stats(self):
+        out = (_ct.c_int64 * 6)()
+        st = _lib.tnn_server_stats(self._h, out)
+        if st != OK:
+            raise TnnError(st, "tnn_server_stats")
+        return dict(zip(["queued", "running", "finished", "bytes", "peak_bytes", "completed"], list(out)))
+
+    def close(self):
+        if self._h:
+            _lib.tnn_server_destroy(self._h)
+            self._h = None
+            self._keep = {}
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
     def __del__(self):
         try:

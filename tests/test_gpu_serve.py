@@ -1,0 +1,144 @@
+"""GPU tests of the completion server (tnn_server_*): a job's result is the
+same, bit for bit, whether it runs alone through tnn_complete or in a mix of
+concurrent jobs of other shapes and precisions; admission keeps the device
+footprint under the cap; invalid jobs are refused at submission."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_common import dtype_of, torch_cuda
+from paper_1902_03070_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+# (shape, precision, observed fraction, iteration cap): the 48 x 48 x 16
+# FP64 workload, small FP32 / 3xTF32 / BF16-split tensors, and slices large
+# enough for the cluster Jacobi kernel
+MIX = [((48, 48, 16), "fp64", 0.4, 60), ((64, 80, 12), "fp32", 0.3, 40), ((40, 50, 20), "tf32x3", 0.25, 50),
+       ((64, 64, 31), "bf16split", 0.2, 30), ((300, 280, 3), "fp32", 0.3, 8), ((33, 17, 5), "fp64", 0.5, 70)]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    torch_cuda()
+    from paper_1902_03070_gb300 import tnn
+    with tnn.Context(0) as c:
+        yield c
+
+
+def _jobs(seed=5):
+    rng = np.random.default_rng(seed)
+    out = []
+    for shape, prec, frac, iters in MIX:
+        n1, n2, n3 = shape
+        A, F = inputs.lowrank_factors(n1, n2, n3, 3, rng)
+        T = O.tprod(A, F)
+        mask = inputs.uniform_mask(shape, frac, rng)
+        B = inputs.fortran(T * mask)
+        out.append(dict(shape=shape, prec=prec, B=B, mask=mask,
+                        prm=dict(beta0=1e-4, rho=1.1, beta_max=1e10, tol=1e-8, max_iter=iters)))
+    return out
+
+
+def _alone(ctx, job):
+    from paper_1902_03070_gb300 import tnn
+    dt = dtype_of(job["prec"])
+    Xd = tnn.fortran_empty(job["shape"], dt)
+    st, rep = ctx.complete(tnn.to_fortran(job["B"], dtype=dt), tnn.to_fortran(job["mask"]), Xd,
+                           ctx.params(**job["prm"]), prec=job["prec"])
+    return tnn.to_numpy(Xd), rep
+
+
+def _run_server(server, jobs, device_inputs, stagger=0.0):
+    from paper_1902_03070_gb300 import tnn
+    ids = []
+    for i, job in enumerate(jobs):
+        dt = dtype_of(job["prec"])
+        if device_inputs and i % 2 == 0:
+            B, mask = tnn.to_fortran(job["B"], dtype=dt), tnn.to_fortran(job["mask"])
+        else:
+            B = np.asfortranarray(job["B"].astype(np.float64 if job["prec"] == "fp64" else np.float32))
+            mask = np.asfortranarray(job["mask"])
+        ids.append(server.submit(B, mask, tnn.Context.params(**job["prm"]), prec=job["prec"]))
+        server.step()
+        if stagger:
+            time.sleep(stagger)
+    results = {}
+    t_end = time.time() + 120
+    while len(results) < len(ids):
+        server.step()
+        for jid in ids:
+            if jid not in results and server.state(jid) >= 2:
+                results[jid] = server.take(jid)
+        assert time.time() < t_end, server.stats()
+    return [results[j] for j in ids]
+
+
+def test_alone_equals_in_mix(ctx):
+    from paper_1902_03070_gb300 import tnn
+    jobs = _jobs()
+    alone = [_alone(ctx, j) for j in jobs]
+    with tnn.Server(streams=4, chunk=3) as sv:
+        mixed = _run_server(sv, jobs, device_inputs=True, stagger=0.002)
+        st = sv.stats()
+    assert st["queued"] == 0 and st["running"] == 0
+    for job, (Xa, ra), (status, Xm, rm, times) in zip(jobs, alone, mixed):
+        assert status in (tnn.OK, tnn.ENOCONV), (job["shape"], status)
+        assert rm["iters"] == ra["iters"], (job["shape"], rm, ra)
+        assert np.array_equal(Xa, Xm), job["shape"]
+        assert times[0] <= times[1] <= times[2]
+
+
+def test_admission_respects_the_footprint_cap(ctx):
+    from paper_1902_03070_gb300 import tnn
+    jobs = _jobs(seed=6)[:4]
+    alone = [_alone(ctx, j) for j in jobs]
+    # room for about two of these jobs at a time
+    sizes = []
+    for j in jobs:
+        n = int(np.prod(j["shape"]))
+        e = 8 if j["prec"] == "fp64" else 4
+        sizes.append(5 * n * e + n)
+    cap = int(sorted(sizes)[-1] + sorted(sizes)[-2] + (8 << 20))
+    with tnn.Server(hbm_cap_bytes=cap, streams=2, chunk=4) as sv:
+        mixed = _run_server(sv, jobs, device_inputs=False)
+        st = sv.stats()
+    assert 0 < st["peak_bytes"] <= cap
+    assert st["completed"] == len(jobs)
+    for (Xa, ra), (status, Xm, rm, times) in zip(alone, mixed):
+        assert np.array_equal(Xa, Xm)
+
+
+def test_max_active_serialises_jobs(ctx):
+    from paper_1902_03070_gb300 import tnn
+    jobs = _jobs(seed=7)[:3]
+    with tnn.Server(max_active=1, streams=2, chunk=8) as sv:
+        res = _run_server(sv, jobs, device_inputs=False)
+    spans = sorted((r[3][1], r[3][2]) for r in res)
+    for (a0, a1), (b0, b1) in zip(spans, spans[1:]):
+        assert b0 >= a1 - 1e-9  # the next job is admitted only after the previous one finished
+
+
+def test_server_rejects_invalid_jobs(ctx):
+    torch = torch_cuda()
+    from paper_1902_03070_gb300 import tnn
+    with tnn.Server(hbm_cap_bytes=1 << 20) as sv:
+        B = np.asfortranarray(np.zeros((200, 200, 4), dtype=np.float32))
+        mask = np.asfortranarray(np.ones((200, 200, 4), dtype=np.uint8))
+        with pytest.raises(tnn.TnnError):
+            sv.submit(B, mask, tnn.Context.params(), prec="fp32")  # never fits 1 MiB
+        Bs = np.asfortranarray(np.zeros((8, 8, 2), dtype=np.float32))
+        ms = np.asfortranarray(np.ones((8, 8, 2), dtype=np.uint8))
+        bad = tnn.Context.params()
+        bad.beta0 = -1.0
+        with pytest.raises(tnn.TnnError):
+            sv.submit(Bs, ms, bad, prec="fp32")
+        jid = sv.submit(Bs, ms, tnn.Context.params(max_iter=5), prec="fp32")
+        while sv.state(jid) < 2:
+            sv.step()
+        status, X, rep, t = sv.take(jid)
+        assert rep["iters"] <= 5
+        with pytest.raises(KeyError):
+            sv.take(jid)  # already taken

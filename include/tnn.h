@@ -266,7 +266,7 @@ void tnn_tsvt_batch_destroy(tnn_tsvt_batch* plan);
  * Algorithm 1).  A job is a completion problem with tnn_complete's
  * arguments.  Queued jobs are admitted in submission order while the device
  * footprint of the admitted ones stays within hbm_cap_bytes (and at most
- * max_active run); an admitted job keeps B, the mask, X, M, the transformed
+ * max_active run), or least estimated work first; an admitted job keeps B, the mask, X, M, the transformed
  * tensor and its control block (beta, iteration, stop test) resident on the
  * device until its result is taken.  Each tnn_server_step retires the jobs
  * that stopped (stop test or max_iter), admits what now fits, and queues the
@@ -275,18 +275,23 @@ void tnn_tsvt_batch_destroy(tnn_tsvt_batch* plan);
  * the GPU.  A job runs exactly tnn_complete's kernels on its own buffers, so
  * its result does not depend on what else is running.  Not thread-safe: one
  * host thread drives a server. */
+#define TNN_SERVER_FIFO 0           /* admit in submission order */
+#define TNN_SERVER_SHORTEST_FIRST 1 /* admit the least estimated work first (iterations x n3 x m n^2) */
 typedef struct {
     uint64_t hbm_cap_bytes; /* 0: 150e9 */
     int32_t max_active;     /* 0: no limit beyond the footprint cap */
     int32_t streams;        /* 0: 8 */
     int32_t chunk;          /* iterations queued per job per step; 0: 8 */
     int32_t device;
+    int32_t policy;         /* TNN_SERVER_FIFO or TNN_SERVER_SHORTEST_FIRST */
 } tnn_server_params;
 typedef struct tnn_server tnn_server;
 tnn_status tnn_server_create(const tnn_server_params* params, tnn_server** server);
-/* B (FP64 for TNN_FP64, else FP32) and mask (uint8, 1 = observed), host or
- * device, must stay valid and unchanged until the job is admitted (state 1).
- * TNN_EINVAL if the job could never fit the cap or its slices are too large. */
+/* B (FP64 for TNN_FP64, else FP32) and mask (uint8, 1 = observed): pageable
+ * host memory is copied at submission (into pinned memory the job owns);
+ * pinned host or device memory is read at admission and must stay valid and
+ * unchanged until then (state 1).  TNN_EINVAL if the job could never fit
+ * the cap or its slices are too large. */
 tnn_status tnn_server_submit(tnn_server* server, const void* B, const uint8_t* mask, tnn_shape shape,
                              const tnn_admm_params* params, tnn_precision prec, int64_t* job_id);
 /* *finished = jobs that finished (or failed) in this pass (may be NULL). */

@@ -15,6 +15,8 @@
 // its result is the same bit for bit whatever else is running.
 #include <cuda_runtime.h>
 
+#include <string.h>
+
 #include <chrono>
 #include <deque>
 #include <map>
@@ -48,7 +50,22 @@ struct SJob {
     AdmmCtl* h_ctl = nullptr;  // pinned slot
     AdmmCtl last{};
     double t_submit = 0, t_admit = -1, t_finish = -1;
+    double work = 0;  // estimated: iterations x slices x m n^2 (one-sided Jacobi sweep cost)
+    void* stage = nullptr;  // pinned copy of pageable host inputs (from the server's pool)
+    size_t stage_size = 0;
 };
+
+// True for pageable host memory (a copy from it would block the host until
+// the stream reaches it).
+bool pageable(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;
+    }
+    return a.type == cudaMemoryTypeUnregistered;
+}
 
 // Device layout of one job (offsets into its allocation).
 struct Layout {
@@ -93,6 +110,32 @@ struct tnn_server {
     int64_t completed = 0;
     std::vector<AdmmCtl*> pinned_blocks;  // 64 control-block slots each
     std::vector<AdmmCtl*> free_slots;
+    // pinned staging buffers, kept for reuse (freeing pinned memory can
+    // synchronise the device): size -> buffer
+    std::multimap<size_t, void*> stage_free;
+    std::vector<void*> stage_all;
+
+    void* stage_get(size_t bytes, size_t* got)
+    {
+        auto it = stage_free.lower_bound(bytes);
+        if (it != stage_free.end()) {
+            void* p = it->second;
+            *got = it->first;
+            stage_free.erase(it);
+            return p;
+        }
+        size_t sz = 1 << 20;
+        while (sz < bytes) sz <<= 1;
+        void* p = nullptr;
+        if (cudaHostAlloc(&p, sz, cudaHostAllocDefault) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        stage_all.push_back(p);
+        *got = sz;
+        return p;
+    }
+    void stage_put(void* p, size_t sz) { stage_free.emplace(sz, p); }
     std::chrono::steady_clock::time_point t0;
 
     double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
@@ -213,6 +256,12 @@ void release(tnn_server* sv, SJob& j)
         sv->free_slots.push_back(j.h_ctl);
         j.h_ctl = nullptr;
     }
+    if (j.stage) {
+        // a job that failed at admission may still have its copies in flight
+        if (j.state == 3) cudaStreamSynchronize(sv->lanes[j.lane]);
+        sv->stage_put(j.stage, j.stage_size);
+        j.stage = nullptr;
+    }
 }
 
 }  // namespace
@@ -226,6 +275,7 @@ tnn_status tnn_server_create(const tnn_server_params* p, tnn_server** out)
     tnn_server_params q{};
     if (p) q = *p;
     if (q.max_active < 0 || q.streams < 0 || q.chunk < 0) return TNN_EINVAL;
+    if (q.policy != TNN_SERVER_FIFO && q.policy != TNN_SERVER_SHORTEST_FIRST) return TNN_EINVAL;
     if (q.hbm_cap_bytes == 0) q.hbm_cap_bytes = 150ull * 1000 * 1000 * 1000;
     if (q.streams == 0) q.streams = 8;
     if (q.chunk == 0) q.chunk = 8;
@@ -276,6 +326,29 @@ tnn_status tnn_server_submit(tnn_server* sv, const void* B, const uint8_t* mask,
     j->B_user = B;
     j->mask_user = mask;
     j->bytes = fp;
+    {
+        const double m = (double)(sh.n1 > sh.n2 ? sh.n1 : sh.n2), n = (double)(sh.n1 > sh.n2 ? sh.n2 : sh.n1);
+        j->work = (double)prm->max_iter * (double)sh.n3 * m * n * n;
+    }
+    // pageable host inputs are copied now into pinned memory, so that the
+    // admission copies never block the scheduling pass
+    const size_t N = (size_t)sh.n1 * sh.n2 * sh.n3, bytes = N * (prec == TNN_FP64 ? 8 : 4);
+    const bool pb = pageable(B), pm = pageable(mask);
+    if (pb || pm) {
+        const size_t sz = (pb ? (bytes + 255) / 256 * 256 : 0) + (pm ? N : 0);
+        j->stage = sv->stage_get(sz, &j->stage_size);
+        if (!j->stage) return TNN_ENOMEM;
+        char* c = static_cast<char*>(j->stage);
+        if (pb) {
+            memcpy(c, B, bytes);
+            j->B_user = c;
+            c += (bytes + 255) / 256 * 256;
+        }
+        if (pm) {
+            memcpy(c, mask, N);
+            j->mask_user = reinterpret_cast<const uint8_t*>(c);
+        }
+    }
     j->t_submit = sv->now();
     *job_id = j->id;
     sv->queue.push_back(j->id);
@@ -303,6 +376,10 @@ tnn_status tnn_server_step(tnn_server* sv, int32_t* finished)
             j.state = 3;
             j.result = TNN_ECUDA;
         } else {
+            if (j.stage) {  // the admission copies came before this chunk
+                sv->stage_put(j.stage, j.stage_size);
+                j.stage = nullptr;
+            }
             j.last = *j.h_ctl;
             if (!(j.last.done || j.queued >= j.prm.max_iter)) continue;
             j.state = 2;
@@ -314,8 +391,17 @@ tnn_status tnn_server_step(tnn_server* sv, int32_t* finished)
         sv->completed += 1;
         ++nfin;
     }
-    // admit in submission order while the footprint fits
+    // admit while the footprint fits: in submission order, or the queued job
+    // with the least estimated work first
     while (!sv->queue.empty()) {
+        if (sv->p.policy == TNN_SERVER_SHORTEST_FIRST) {
+            auto best = sv->queue.begin();
+            for (auto it = sv->queue.begin(); it != sv->queue.end(); ++it)
+                if (sv->jobs[*it]->work < sv->jobs[*best]->work) best = it;
+            const int64_t id = *best;
+            sv->queue.erase(best);
+            sv->queue.push_front(id);
+        }
         SJob& j = *sv->jobs[sv->queue.front()];
         if (sv->p.max_active > 0 && sv->running >= sv->p.max_active) break;
         if (sv->bytes + j.bytes > sv->p.hbm_cap_bytes) break;
@@ -414,6 +500,10 @@ tnn_status tnn_server_take(tnn_server* sv, int64_t id, void* X_out, tnn_admm_rep
         times[2] = j.t_finish;
     }
     if (j.lane >= 0) release(sv, j);
+    if (j.stage) {
+        sv->stage_put(j.stage, j.stage_size);
+        j.stage = nullptr;
+    }
     sv->jobs.erase(it);
     return res;
 }
@@ -442,6 +532,7 @@ void tnn_server_destroy(tnn_server* sv)
     for (auto s : sv->lanes) cudaStreamSynchronize(s);
     for (auto s : sv->lanes) cudaStreamDestroy(s);
     for (auto b : sv->pinned_blocks) cudaFreeHost(b);
+    for (auto b : sv->stage_all) cudaFreeHost(b);
     tnn_destroy(sv->ctx);
     delete sv;
 }

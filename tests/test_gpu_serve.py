@@ -142,3 +142,25 @@ def test_server_rejects_invalid_jobs(ctx):
         assert rep["iters"] <= 5
         with pytest.raises(KeyError):
             sv.take(jid)  # already taken
+
+
+def test_shortest_first_admission_order(ctx):
+    from paper_1902_03070_gb300 import tnn
+    jobs = _jobs(seed=8)[:4]
+    work = [j["prm"]["max_iter"] * j["shape"][2] * max(j["shape"][:2]) * min(j["shape"][:2]) ** 2 for j in jobs]
+    with tnn.Server(max_active=1, streams=1, chunk=16, policy=tnn.Server.SHORTEST_FIRST) as sv:
+        ids = []
+        for j in jobs:  # all queued before the first scheduling pass
+            dt = np.float64 if j["prec"] == "fp64" else np.float32
+            ids.append(sv.submit(np.asfortranarray(j["B"].astype(dt)), np.asfortranarray(j["mask"]),
+                                 tnn.Context.params(**j["prm"]), prec=j["prec"]))
+        t_end = time.time() + 120
+        admitted = {}
+        while len(admitted) < len(ids):
+            sv.step()
+            for jid in ids:
+                if jid not in admitted and sv.state(jid) >= 2:
+                    admitted[jid] = sv.take(jid)[3][1]
+            assert time.time() < t_end
+    order = sorted(range(len(ids)), key=lambda i: admitted[ids[i]])
+    assert order == sorted(range(len(ids)), key=lambda i: work[i])

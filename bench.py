@@ -41,6 +41,10 @@ METRIC = "t-SVT slices/s (one ADMM iteration = 100 slices)"
 PREC = "tf32x3"   # FP32 data; tube DCT on tcgen05 with a 3xTF32 split; FP32 Jacobi
 FP32_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# DRAM bytes (read + write) of one Jacobi SVT launch on this workload, from
+# an ncu capture of the current kernel (dram__bytes.sum.per_second x
+# gpu__time_duration); the slices stay in L2 between the transforms.
+JACOBI_TRAFFIC_BYTES = 10.25e6
 
 
 def parse():
@@ -52,6 +56,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--no-next", action="store_true", help="skip the batched, multispectral and serving legs")
+    p.add_argument("--serve-jobs", type=int, default=24)
     return p.parse_args()
 
 
@@ -275,6 +281,12 @@ def run_ours(args):
                "rel_err_vs_ground_truth": float(np.linalg.norm(hx.numpy().transpose(2, 1, 0) - T) /
                                                 np.linalg.norm(T))}
 
+    # ---- the other workloads (rank 0, one GPU): uneven batch, multispectral
+    # t-SVT, serving stream
+    nxt = None
+    if rank == 0 and ws == 1 and not args.no_next:
+        nxt = next_legs(ctx, torch, dev, flush, args.serve_jobs)
+
     # ---- CPU oracle on the host cores: bounded sample (t-SVT of the full tensor)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -287,7 +299,9 @@ def run_ours(args):
         pass
     sm_mhz = clk.get("sm_mhz")
     roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": (achieved / FP32_PEAK_TFLOPS) if achieved else None, "traffic": None,
+            "frac": (achieved / FP32_PEAK_TFLOPS) if achieved else None, "traffic": JACOBI_TRAFFIC_BYTES,
+            "traffic_basis": "ncu dram__bytes of one launch of this kernel on this workload "
+                             "(profiles/jacobi_svt_fp32_144x176x100.md)",
             "kernel": "jacobi_svt (FP32 CUDA cores)", "peak_basis": FP32_PEAK_NOTE + " (derived, not measured)",
             "launches": jac_n, "avg_launch_ms": jac_ms / max(jac_n, 1),
             "share_of_step": jac_ms / total_ms if total_ms > 0 else None}
@@ -301,7 +315,7 @@ def run_ours(args):
         "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
         "roofline": roof, "kernels_ms": {k: v[0] for k, v in prof.items()},
         "gpu_launches": launches, "clocks": clk, "e2e": e2e, "fp64_plain": fp64, "accuracy": acc,
-        "cpu_baseline": cpu,
+        "cpu_baseline": cpu, "other_workloads": nxt,
         "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained")},
     }
     if rank == 0:
@@ -309,6 +323,82 @@ def run_ours(args):
     ctx.close()
     if ws > 1:
         dist.destroy_process_group()
+
+
+def timed(fn, reps, flush, stream, torch):
+    """Per-call device milliseconds of fn (CUDA events on `stream`, L2
+    flushed before each call, one untimed call first)."""
+    fn()
+    ms = []
+    for _ in range(reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return ms
+
+
+def next_legs(ctx, torch, dev, flush, serve_jobs):
+    """Batched uneven t-SVT (64 tensors, n1, n2 in [32, 256], n3 in [8, 64],
+    FP32, one graph launch, autotuned) against the per-tensor loop; the
+    512 x 512 x 31 multispectral-shaped t-SVT (BF16-split transforms, slices
+    on thread-block clusters) and its FP64 plain path; and a seeded serving
+    stream of completion jobs."""
+    from paper_1902_03070_gb300 import inputs, serve, tnn
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    # ---- uneven batch
+    tp = serve.library_tprod(ctx)
+    Zs = inputs.config4(tp)
+    taus = [inputs.config4_tau(Z.shape[0], Z.shape[1]) for Z in Zs]
+    Zd = [tnn.to_fortran(Z, device=dev, dtype=torch.float32) for Z in Zs]
+    Yd = [tnn.fortran_empty(Z.shape, torch.float32, device=dev) for Z in Zs]
+    slices = sum(Z.shape[2] for Z in Zs)
+    plan = ctx.tsvt_batch(Zd, taus, Yd, prec="fp32", graph=True, autotune=True)
+    ms_b = timed(plan.run, 10, flush, stream, torch)
+    ms_l = timed(lambda: [ctx.tsvt(z, t, Y=y, prec="fp32") for z, t, y in zip(Zd, taus, Yd)], 3, flush, stream, torch)
+    prof = plan.profile()
+    out["batched_tsvt"] = {
+        "workload": "64 FP32 tensors, n1, n2 in [32, 256], n3 in [8, 64], tubal rank 2-12 + N(0, 1e-3) noise, "
+                    "tau = 2e-3 (sqrt(n1) + sqrt(n2)); %d slices" % slices,
+        "value": slices / (float(np.median(ms_b)) / 1e3), "unit": "slices/s",
+        "ms_per_batch": float(np.median(ms_b)), "launches_per_batch": plan.info()["launches"],
+        "per_tensor_loop_ms": float(np.median(ms_l)), "speedup_vs_loop": float(np.median(ms_l) / np.median(ms_b)),
+        "groups": [dict(g, ms=t) for g, t in zip(plan.groups(), prof["groups"])],
+        "transform_ms": prof["forward"] + prof["inverse"]}
+    plan.close()
+    del Zd, Yd
+    # ---- multispectral-shaped t-SVT
+    d = inputs.config3()
+    Z = d["T"]
+    tau = 1e-3 * float(np.linalg.norm(Z)) / np.sqrt(Z.shape[2])
+    Z32 = tnn.to_fortran(Z, device=dev, dtype=torch.float32)
+    Y32 = tnn.fortran_empty(Z.shape, torch.float32, device=dev)
+    ms_m = timed(lambda: ctx.tsvt(Z32, tau, Y=Y32, prec="bf16split"), 5, flush, stream, torch)
+    st = ctx.last_jacobi_stats()
+    Z64 = tnn.to_fortran(Z, device=dev, dtype=torch.float64)
+    Y64 = tnn.fortran_empty(Z.shape, torch.float64, device=dev)
+    ms_64 = timed(lambda: ctx.tsvt(Z64, tau, Y=Y64, prec="fp64"), 1, flush, stream, torch)
+    y32, y64 = tnn.to_numpy(Y32).astype(np.float64), tnn.to_numpy(Y64)
+    out["msi_tsvt"] = {
+        "workload": "512x512x31 multispectral-shaped tensor (5 smooth spectral signatures x smoothed abundance "
+                    "maps), one t-SVT, tau = 1e-3 ||Z|| / sqrt(31)",
+        "value": Z.shape[2] / (float(np.median(ms_m)) / 1e3), "unit": "slices/s", "prec": "bf16split",
+        "ms_per_tsvt": float(np.median(ms_m)), "jacobi": st,
+        "fp64_plain_ms_per_tsvt": float(np.median(ms_64)),
+        "rel_err_vs_fp64": float(np.linalg.norm(y32 - y64) / np.linalg.norm(y64))}
+    del Z32, Y32, Z64, Y64
+    # ---- serving stream
+    jobs = serve.make_stream(serve_jobs, 200.0, tprod=tp)
+    _, summ = serve.run(jobs, streams=8, chunk=8, max_active=8, policy=1)
+    summ.update({"rate_jobs_per_s": 200.0, "policy": "shortest estimated work first, at most 8 running",
+                 "note": "the stream's offered load is far above what one GPU completes: latency is queueing"})
+    out["serving"] = summ
+    return out
 
 
 def oracle_baseline(B, mask, budget_s=12.0):

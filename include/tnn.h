@@ -213,6 +213,24 @@ tnn_status tnn_last_jacobi_stats(tnn_ctx* ctx, int64_t out[6]);
 #define TNN_STATIC_SCRATCH_BYTES ((size_t)16 << 20)
 tnn_status tsvt_dct_static(const void* Z, tnn_shape shape, double tau, tnn_precision prec, void* Y, void* stream);
 
+/* The DFT comparison path (Section 2: the t-SVD of Kilmer and Martin that
+ * the paper compares against).  tsvt_dft is the proximal operator of
+ * tau * TNN-F (Definition 6): Y = ifft(SVT_tau(fft(Z))) along the tubes,
+ * each DFT slice shrunk by tau; for real Z only the slices
+ * k = 0..floor(n3/2) are computed (the others are their conjugates) and Y is
+ * real.  *tnn_out (may be NULL) receives TNN-F(Y).  tsvt_dct_plain is the
+ * DCT t-SVT of tsvt_dct computed with the same plain per-slice Jacobi kernel
+ * as tsvt_dft (one warp per column pair), so that the two differ only in the
+ * transform and the arithmetic it implies (real against complex slices):
+ * the pair measures the paper's DCT-against-DFT cost comparison (Table 2).
+ * Device pointers only (TNN_EINVAL otherwise); Y may alias Z; slices up to
+ * 512 x 512; TNN_FP64 runs in FP64, every other precision in plain FP32.
+ * Synchronises the stream only when tnn_out is requested. */
+tnn_status tsvt_dft(tnn_ctx* ctx, const void* Z, tnn_shape shape, double tau, tnn_precision prec, void* Y,
+                    double* tnn_out, void* stream);
+tnn_status tsvt_dct_plain(tnn_ctx* ctx, const void* Z, tnn_shape shape, double tau, tnn_precision prec, void* Y,
+                          double* tnn_out, void* stream);
+
 /* Batched t-SVT: one t-SVT (as tsvt_dct) for each of `count` tensors of
  * different shapes, with the slices of all tensors in the same launches.
  * A plan is built once for fixed device buffers (items[i].Z in, items[i].Y
@@ -318,8 +336,9 @@ void tnn_server_destroy(tnn_server* server);
  *   2 Jacobi SVT                3 inverse transform + ADMM epilogue
  *   4 ADMM iteration finalize   5 ADMM control init
  *   6 ADMM state init           7 Jacobi SVD
- *   8 facewise product */
-#define TNN_NKERNELS 9
+ *   8 facewise product          9 DFT / rectangular tube transform
+ *  10 plain Jacobi SVT (comparison path) */
+#define TNN_NKERNELS 11
 tnn_status tnn_profile(tnn_ctx* ctx, int enable);
 tnn_status tnn_profile_read(tnn_ctx* ctx, double ms[TNN_NKERNELS], int64_t launches[TNN_NKERNELS]);
 

@@ -137,7 +137,7 @@ struct Trace {
 
 // Kernel kinds reported by tnn_profile_read (array index, listed in tnn.h).
 enum { K_TUBE = 0, K_TUBE_FWD_ADMM, K_JACOBI_SVT, K_TUBE_INV_ADMM, K_FINALIZE, K_CTL_INIT, K_ADMM_INIT,
-       K_JACOBI_SVD, K_FACEWISE, K_NKINDS };
+       K_JACOBI_SVD, K_FACEWISE, K_DFT, K_JACOBI_PLAIN, K_NKINDS };
 #define TRACE_CAT2(a, b) a##b
 #define TRACE_CAT(a, b) TRACE_CAT2(a, b)
 #define TRACE(kind) Trace TRACE_CAT(trace_, __LINE__)(ctx, kind, s)
@@ -860,6 +860,121 @@ tnn_status tnn_admm_iterate(tnn_ctx* ctx, const void* B, const uint8_t* mask, tn
     fill_report(rep, res);
     if (res.nonfinite) return fail(ctx, TNN_ENONFINITE, "non-finite value met in iteration %d", res.iter);
     return TNN_OK;
+}
+
+// The DFT comparison path and its like-for-like DCT counterpart: transform,
+// plain per-slice Jacobi SVT, inverse transform.
+static tnn_status tsvt_plain_run(tnn_ctx* ctx, const void* Z, tnn_shape sh, double tau, tnn_precision prec, void* Y,
+                                 double* tnn_out, void* stream, bool dft)
+{
+    if (!ctx) return TNN_EINVAL;
+    if (!Z || !Y || !shape_ok(sh) || !prec_ok(prec) || !(tau >= 0.0) || !(tau < 1e300))
+        return fail(ctx, TNN_EINVAL, "invalid argument");
+    if (sh.n1 > 512 || sh.n2 > 512 || sh.n3 > (1 << 20)) return fail(ctx, TNN_EINVAL, "slice too large");
+    tnn_status st = set_device(ctx);
+    if (st) return st;
+    if (!is_device_ptr(Z) || !is_device_ptr(Y)) return fail(ctx, TNN_EINVAL, "device pointers required");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int elem = elem_of(prec);
+    const int64_t P = sh.n1 * sh.n2, n3 = sh.n3, nh = n3 / 2 + 1;
+    const int64_t planes = dft ? 2 * nh : n3;
+    const int64_t nsl = dft ? nh : n3;
+    bool smem_copy = true;
+    const size_t wbytes = jacobi_plain_work_bytes(sh.n1, sh.n2, nsl, elem, dft, &smem_copy);
+    Carve cv;
+    const size_t oW = cv.add((size_t)planes * P * elem), oS = cv.add(sizeof(SliceStats) * nsl);
+    const size_t oF = dft ? cv.add((size_t)n3 * 2 * nh * elem) : 0, oI = dft ? cv.add((size_t)n3 * 2 * nh * elem) : 0;
+    const size_t oJ = cv.add(wbytes);
+    if ((st = ensure_ws(ctx, cv.total))) return st;
+    void* W = at(ctx, oW);
+    SliceStats* stats = (SliceStats*)at(ctx, oS);
+    if (dft) {
+        {
+            TRACE(K_DFT);
+            if (elem == 8) {
+                CK(launch_build_dft_ops<double>((double*)at(ctx, oF), (double*)at(ctx, oI), (int)n3, s));
+                CK(launch_tube_rect<double>((const double*)Z, (double*)W, (const double*)at(ctx, oF), P, (int)n3,
+                                            (int)(2 * nh), s));
+            } else {
+                CK(launch_build_dft_ops<float>((float*)at(ctx, oF), (float*)at(ctx, oI), (int)n3, s));
+                CK(launch_tube_rect<float>((const float*)Z, (float*)W, (const float*)at(ctx, oF), P, (int)n3,
+                                           (int)(2 * nh), s));
+            }
+        }
+        {
+            TRACE(K_JACOBI_PLAIN);
+            if (elem == 8)
+                CK(launch_jacobi_plain<double>((double*)W, 2 * P, P, (int)nh, (int)sh.n1, (int)sh.n2, tau, true,
+                                               (double*)at(ctx, oJ), smem_copy, stats, s));
+            else
+                CK(launch_jacobi_plain<float>((float*)W, 2 * P, P, (int)nh, (int)sh.n1, (int)sh.n2, tau, true,
+                                              (float*)at(ctx, oJ), smem_copy, stats, s));
+        }
+        {
+            TRACE(K_DFT);
+            if (elem == 8)
+                CK(launch_tube_rect<double>((const double*)W, (double*)Y, (const double*)at(ctx, oI), P, (int)(2 * nh),
+                                            (int)n3, s));
+            else
+                CK(launch_tube_rect<float>((const float*)W, (float*)Y, (const float*)at(ctx, oI), P, (int)(2 * nh),
+                                           (int)n3, s));
+        }
+    } else {
+        const void *opf = nullptr, *opi = nullptr;
+        if ((st = get_op(ctx, n3, elem, 0, 0, s, &opf))) return st;
+        if ((st = get_op(ctx, n3, elem, 1, 0, s, &opi))) return st;
+        {
+            TRACE(K_TUBE);
+            CK(elem == 8 ? launch_tube_op<double>((const double*)Z, (double*)W, (const double*)opf, P, n3, s)
+                         : launch_tube_op<float>((const float*)Z, (float*)W, (const float*)opf, P, n3, s));
+        }
+        {
+            TRACE(K_JACOBI_PLAIN);
+            if (elem == 8)
+                CK(launch_jacobi_plain<double>((double*)W, P, 0, (int)n3, (int)sh.n1, (int)sh.n2, tau, false,
+                                               (double*)at(ctx, oJ), smem_copy, stats, s));
+            else
+                CK(launch_jacobi_plain<float>((float*)W, P, 0, (int)n3, (int)sh.n1, (int)sh.n2, tau, false,
+                                              (float*)at(ctx, oJ), smem_copy, stats, s));
+        }
+        {
+            TRACE(K_TUBE);
+            CK(elem == 8 ? launch_tube_op<double>((const double*)W, (double*)Y, (const double*)opi, P, n3, s)
+                         : launch_tube_op<float>((const float*)W, (float*)Y, (const float*)opi, P, n3, s));
+        }
+    }
+    ctx->last_stats = stats;
+    ctx->last_n3 = nsl;
+    ctx->last_stream = s;
+    if (!tnn_out) return TNN_OK;
+    std::vector<SliceStats> h((size_t)nsl);
+    CK(cudaMemcpyAsync(h.data(), stats, sizeof(SliceStats) * nsl, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    double nuc = 0.0;
+    bool unconv = false, nonfin = false;
+    for (int64_t k = 0; k < nsl; ++k) {
+        // TNN-F sums all n3 DFT slices: slice k and its conjugate n3 - k count twice
+        const double w = !dft ? 1.0 : ((k == 0 || 2 * k == n3) ? 1.0 : 2.0);
+        nuc += w * h[k].nuc;
+        unconv |= !h[k].converged;
+        nonfin |= h[k].nonfinite != 0;
+    }
+    *tnn_out = dft ? nuc / (double)n3 : nuc;
+    if (nonfin) return fail(ctx, TNN_ENONFINITE, "non-finite singular value met");
+    if (unconv) return fail(ctx, TNN_ENOCONV, "a Jacobi SVD reached its sweep cap");
+    return TNN_OK;
+}
+
+tnn_status tsvt_dft(tnn_ctx* ctx, const void* Z, tnn_shape sh, double tau, tnn_precision prec, void* Y,
+                    double* tnn_out, void* stream)
+{
+    return tsvt_plain_run(ctx, Z, sh, tau, prec, Y, tnn_out, stream, true);
+}
+
+tnn_status tsvt_dct_plain(tnn_ctx* ctx, const void* Z, tnn_shape sh, double tau, tnn_precision prec, void* Y,
+                          double* tnn_out, void* stream)
+{
+    return tsvt_plain_run(ctx, Z, sh, tau, prec, Y, tnn_out, stream, false);
 }
 
 tnn_status tnn_last_jacobi_stats(tnn_ctx* ctx, int64_t out[6])

@@ -171,6 +171,23 @@ template <typename T>
 cudaError_t launch_tube_batched(const TubeItem* items, int count, cudaStream_t s);
 int tube_batched_tile();
 
+// ---- DFT comparison path (dft.cu) ------------------------------------------------
+// out(p, q) = sum_j in(p, j) op(j, q), q < nout; op nin x nout column-major.
+template <typename T>
+cudaError_t launch_tube_rect(const T* in, T* out, const T* op, int64_t P, int nin, int nout, cudaStream_t s);
+// Forward (n3 x 2nh) and inverse (2nh x n3) real DFT operators, nh = n3/2 + 1:
+// slice k of the half spectrum as planes 2k (real part) and 2k + 1 (imaginary).
+template <typename T>
+cudaError_t launch_build_dft_ops(T* fwd, T* inv, int n3, cudaStream_t s);
+// Plain one-sided Jacobi SVT of n3s slices (n1 x n2, slice s at data + s *
+// stride; complex slices keep their imaginary plane im_off elements after the
+// real one), threshold tau, in place.  Scratch bytes when the working copy
+// does not fit in shared memory (smem_copy = false).
+size_t jacobi_plain_work_bytes(int64_t n1, int64_t n2, int64_t n3s, int elem, bool cplx, bool* smem_copy);
+template <typename T>
+cudaError_t launch_jacobi_plain(T* data, int64_t stride, int64_t im_off, int n3s, int n1, int n2, double tau,
+                                bool cplx, T* work, bool smem_copy, SliceStats* stats, cudaStream_t s);
+
 // ---- one completion job's device state (api.cu) ---------------------------------
 // One tube transform direction: CUDA-core operator or tensor-core images.
 struct TubeOp {

@@ -129,9 +129,13 @@ _lib.tnn_server_destroy.argtypes = [_vp]
 _lib.tnn_server_destroy.restype = None
 BATCH_GRAPH = 1
 BATCH_AUTOTUNE = 2
-NKERNELS = 9
+NKERNELS = 11
 KERNEL_KINDS = ["tube", "tube_fwd_admm", "jacobi_svt", "tube_inv_admm", "admm_finalize", "ctl_init", "admm_init",
-                "jacobi_svd", "facewise"]
+                "jacobi_svd", "facewise", "dft", "jacobi_plain"]
+_lib.tsvt_dft.argtypes = [_vp, _vp, Shape, _ct.c_double, _ct.c_int, _vp, _ct.POINTER(_ct.c_double), _vp]
+_lib.tsvt_dft.restype = _st
+_lib.tsvt_dct_plain.argtypes = [_vp, _vp, Shape, _ct.c_double, _ct.c_int, _vp, _ct.POINTER(_ct.c_double), _vp]
+_lib.tsvt_dct_plain.restype = _st
 
 EXPORTS = ["tnn_create", "tnn_destroy", "tnn_status_string", "tnn_last_error", "tnn_reserve", "tnn_workspace_size",
            "tdct3", "tsvt_dct", "tsvd_dct_forward", "tsvd_dct_inverse", "tprod_dct", "tnn_complete",
@@ -139,7 +143,7 @@ EXPORTS = ["tnn_create", "tnn_destroy", "tnn_status_string", "tnn_last_error", "
            "tnn_tsvt_batch_create", "tnn_tsvt_batch_run", "tnn_tsvt_batch_info", "tnn_tsvt_batch_group",
            "tnn_tsvt_batch_profile", "tnn_tsvt_batch_stats", "tnn_tsvt_batch_destroy",
            "tnn_server_create", "tnn_server_submit", "tnn_server_step", "tnn_server_job_state", "tnn_server_take",
-           "tnn_server_stats", "tnn_server_destroy"]
+           "tnn_server_stats", "tnn_server_destroy", "tsvt_dft", "tsvt_dct_plain"]
 
 
 class TnnError(RuntimeError):
@@ -284,6 +288,28 @@ class Context:
                            _ct.byref(out) if want_tnn else None, _stream([Z, Y]))
         self._chk(st, "tsvt_dct", allow=(ENOCONV,) if allow_noconv else ())
         return (Y, out.value) if want_tnn else Y
+
+    def _tsvt_plain(self, fn, name, Z, tau, Y, prec, want_tnn, allow_noconv):
+        _check_layout(Z, Z.shape)
+        _dtype_ok(Z, prec)
+        if Y is None:
+            Y = Z
+        _check_layout(Y, Z.shape)
+        out = _ct.c_double(0.0)
+        st = fn(self._h, _ptr(Z)[0], Shape(*Z.shape), float(tau), PRECISIONS[prec], _ptr(Y)[0],
+                _ct.byref(out) if want_tnn else None, _stream([Z, Y]))
+        self._chk(st, name, allow=(ENOCONV,) if allow_noconv else ())
+        return (Y, out.value) if want_tnn else Y
+
+    def tsvt_dft(self, Z, tau, Y=None, prec="fp32", want_tnn=False, allow_noconv=False):
+        """Y = ifft(SVT_tau(fft(Z))) along the tubes: the proximal operator of
+        tau * TNN-F (the DFT comparison path).  With want_tnn: (Y, TNN-F(Y))."""
+        return self._tsvt_plain(_lib.tsvt_dft, "tsvt_dft", Z, tau, Y, prec, want_tnn, allow_noconv)
+
+    def tsvt_dct_plain(self, Z, tau, Y=None, prec="fp32", want_tnn=False, allow_noconv=False):
+        """The DCT t-SVT with the DFT path's plain Jacobi kernel (like-for-like
+        comparison)."""
+        return self._tsvt_plain(_lib.tsvt_dct_plain, "tsvt_dct_plain", Z, tau, Y, prec, want_tnn, allow_noconv)
 
     def tsvd(self, X, U, S, V, prec="fp32"):
         n1, n2, n3 = X.shape

@@ -346,8 +346,9 @@ def next_legs(ctx, torch, dev, flush, serve_jobs):
     """Batched uneven t-SVT (64 tensors, n1, n2 in [32, 256], n3 in [8, 64],
     FP32, one graph launch, autotuned) against the per-tensor loop; the
     512 x 512 x 31 multispectral-shaped t-SVT (BF16-split transforms, slices
-    on thread-block clusters) and its FP64 plain path; and a seeded serving
-    stream of completion jobs."""
+    on thread-block clusters) and its FP64 plain path; the DCT against the
+    DFT t-SVT at the paper's Table 2 sizes; and a seeded serving stream of
+    completion jobs."""
     from paper_1902_03070_gb300 import inputs, serve, tnn
     stream = torch.cuda.current_stream(dev)
     out = {}
@@ -392,6 +393,24 @@ def next_legs(ctx, torch, dev, flush, serve_jobs):
         "fp64_plain_ms_per_tsvt": float(np.median(ms_64)),
         "rel_err_vs_fp64": float(np.linalg.norm(y32 - y64) / np.linalg.norm(y64))}
     del Z32, Y32, Z64, Y64
+    # ---- DCT against DFT (the paper's Table 2 sizes, U[0,1) tensors, one
+    # t-SVT each, tau = 1): both on the same plain Jacobi kernel, and the
+    # tuned DCT path beside them
+    cmp = []
+    for shp in [(100, 100, 100), (100, 100, 400), (200, 200, 100), (400, 400, 100)]:
+        Zc = inputs.random_tensor(shp, np.random.default_rng(sum(shp)), "uniform")
+        Zd = tnn.to_fortran(Zc, device=dev, dtype=torch.float32)
+        Yd = tnn.fortran_empty(shp, torch.float32, device=dev)
+        row = {"shape": list(shp)}
+        for name, fn in (("dft_plain_ms", ctx.tsvt_dft), ("dct_plain_ms", ctx.tsvt_dct_plain),
+                         ("dct_tuned_ms", ctx.tsvt)):
+            row[name] = float(np.median(timed(lambda: fn(Zd, 1.0, Y=Yd, prec="fp32"), 2, flush, stream, torch)))
+        row["dft_over_dct_same_kernel"] = row["dft_plain_ms"] / row["dct_plain_ms"]
+        cmp.append(row)
+        del Zd, Yd
+    out["dct_vs_dft"] = {"note": "one FP32 t-SVT per tensor; dft/dct_plain share one plain Jacobi kernel (complex "
+                                 "vs real slices, n3/2+1 vs n3 of them); dct_tuned is tsvt_dct",
+                         "rows": cmp}
     # ---- serving stream
     jobs = serve.make_stream(serve_jobs, 200.0, tprod=tp)
     _, summ = serve.run(jobs, streams=8, chunk=8, max_active=8, policy=1)

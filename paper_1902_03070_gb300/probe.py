@@ -6,6 +6,7 @@ and for profilers (ncu) that capture a launch of it.
 
 Prints the per-kernel device time of the repetitions (library trace events;
 one untimed call runs first) and the Jacobi statistics of the last call.
+--op batch runs the 64-tensor uneven batched t-SVT plan instead.
 """
 import argparse
 import json
@@ -15,7 +16,7 @@ import numpy as np
 
 def main():
     p = argparse.ArgumentParser()
-    p.add_argument("--op", default="tsvt", choices=["tsvt", "tdct3", "tsvd"])
+    p.add_argument("--op", default="tsvt", choices=["tsvt", "tdct3", "tsvd", "tsvt_dft", "tsvt_dct_plain", "batch"])
     p.add_argument("--shape", default="144,176,100")
     p.add_argument("--prec", default="fp32")
     p.add_argument("--reps", type=int, default=3)
@@ -27,6 +28,8 @@ def main():
     from paper_1902_03070_gb300 import inputs, tnn
     shape = tuple(int(x) for x in a.shape.split(","))
     dt = torch.float64 if a.prec == "fp64" else torch.float32
+    if a.op == "batch":
+        return batch(a, torch, inputs, tnn)
     Z = inputs.random_tensor(shape, np.random.default_rng(a.seed), "uniform")
     with tnn.Context(0) as ctx:
         Zd = tnn.to_fortran(Z, dtype=dt)
@@ -37,6 +40,8 @@ def main():
                 ctx.profile(True)
             if a.op == "tsvt":
                 ctx.tsvt(Zd, a.tau, Y=Yd, prec=a.prec)
+            elif a.op in ("tsvt_dft", "tsvt_dct_plain"):
+                getattr(ctx, a.op)(Zd, a.tau, Y=Yd, prec=a.prec, allow_noconv=True)
             elif a.op == "tdct3":
                 ctx.tdct3(Zd, Yd, prec=a.prec)
             else:
@@ -50,9 +55,27 @@ def main():
         out = {"op": a.op, "shape": shape, "prec": a.prec, "reps": a.reps,
                "kernels": {k: {"ms_total": v[0], "launches": v[1], "ms_per_launch": v[0] / max(v[1], 1)}
                            for k, v in prof.items()}}
-        if a.op in ("tsvt", "tsvd"):
+        if a.op in ("tsvt", "tsvd", "tsvt_dft", "tsvt_dct_plain"):
             out["jacobi"] = ctx.last_jacobi_stats()
         print(json.dumps(out))
+
+
+def batch(a, torch, inputs, tnn):
+    """The 64-tensor uneven batch (shape argument ignored), one graph replay
+    per repetition; prints per-launch times of one serial profiled run."""
+    from .serve import library_tprod
+    with tnn.Context(0) as ctx:
+        Zs = inputs.config4(library_tprod(ctx))
+        taus = [inputs.config4_tau(Z.shape[0], Z.shape[1]) for Z in Zs]
+        Zd = [tnn.to_fortran(Z, dtype=torch.float32) for Z in Zs]
+        Yd = [tnn.fortran_empty(Z.shape, torch.float32) for Z in Zs]
+        plan = ctx.tsvt_batch(Zd, taus, Yd, prec="fp32", graph=True, autotune=False)
+        for _ in range(a.reps + 1):
+            plan.run()
+        torch.cuda.synchronize()
+        print(json.dumps({"op": "batch", "tensors": len(Zs), "info": plan.info(), "groups": plan.groups(),
+                          "profile_ms": plan.profile()}))
+        plan.close()
 
 
 if __name__ == "__main__":

@@ -61,6 +61,22 @@ def parse():
     return p.parse_args()
 
 
+def max_over_ranks(value, ws, dist, device):
+    """The largest `value` over all ranks (timed regions are reported as the
+    slowest rank's); `value` itself on one rank."""
+    if ws <= 1:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(ws, units_per_step, steps, total_ms):
+    """Whole-job rate: the units all ranks processed over the slowest rank's time."""
+    return ws * units_per_step * steps / (total_ms / 1e3)
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rk = int(os.environ.get("RANK", "0"))
@@ -208,13 +224,9 @@ def run_ours(args):
     if ws > 1:
         dist.barrier()
     clk = clocks.stop()
-    total_ms = float(np.sum(step_ms))
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(np.sum(step_ms)), ws, dist, dev)
     K = args.steps
-    value = ws * N3 * K / (total_ms / 1e3)
+    value = job_rate(ws, N3, K, total_ms)
     jac_ms, jac_n = prof.get("jacobi_svt", (0.0, 0))
     launches = sum(c for _, c in prof.values())
     achieved = flops / (jac_ms / 1e3) / 1e12 if jac_ms > 0 else None

@@ -649,7 +649,7 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
     int* rank = kidx + npad;
     T* gbuf = reinterpret_cast<T*>(rank + npad);
     __shared__ int s_rot, s_keep, s_nonfinite;
-    __shared__ double s_nuc;
+    __shared__ double s_nuc, s_fro;
     __shared__ unsigned long long s_pairs, s_rots;
 
     T* src = item ? static_cast<T*>(item->data) : a.data + (size_t)slice * n1 * n2;
@@ -663,23 +663,39 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
         }
     __syncthreads();
     const int64_t S = n1 * n2;
+    T fro = T(0);  // this thread's share of ||A||_F^2
     for (int64_t e = tid; e < S; e += nthr) {
         int i = (int)(e % n1), j = (int)(e / n1);
         // oriented (row, col): (i, j) if n1 >= n2 else (j, i)
         int r = tr ? j : i, c = tr ? i : j;
-        Aw[(size_t)c * ldA + r] = src[e];
+        const T v = src[e];
+        Aw[(size_t)c * ldA + r] = v;
+        fro = fma(v, v, fro);
     }
     for (int c = tid; c < npad; c += nthr) dsc[c] = T(1);
-    if (tid == 0) { s_pairs = 0; s_rots = 0; s_nonfinite = 0; s_nuc = 0.0; s_keep = 0; }
+    if (tid == 0) { s_pairs = 0; s_rots = 0; s_nonfinite = 0; s_nuc = 0.0; s_keep = 0; s_fro = 0.0; }
     __syncthreads();
+    fro = group_sum<32>(fro);
+    if (lane == 0) atomicAdd(&s_fro, (double)fro);
+    __syncthreads();
+
+    // SVT of a slice whose Frobenius norm is below the threshold: every
+    // singular value is at most ||A||_F <= tau, so Y = 0 and the sweeps can
+    // be skipped (the rebuild below then keeps nothing and writes zeros, as
+    // the full computation would).  The margin covers the rounding of the sum.
+    bool skip = false;
+    if (!WITHV) {
+        const double tau0 = a.ctl ? 1.0 / a.ctl->beta : (item ? item->tau : a.tau);
+        skip = s_fro * (1.0 + 1e-3) < tau0 * tau0;
+    }
 
     // ---- sweeps
     const T tol = sqrt((T)m) * Num<T>::unit();
     Counters cnt{0, 0, 0};
-    int sweeps = 0, converged = 0;
+    int sweeps = 0, converged = skip ? 1 : 0;
     const int max_sweeps = a.max_sweeps > 0 ? a.max_sweeps : 30;
     const int npairs = nb / 2;
-    while (sweeps < max_sweeps) {
+    while (!skip && sweeps < max_sweeps) {
         if (tid == 0) s_rot = 0;
         __syncthreads();
         const int big0 = cnt.big;

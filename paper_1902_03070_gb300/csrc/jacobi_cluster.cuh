@@ -180,10 +180,11 @@ __global__ void __launch_bounds__(ClusterBound<T, K, R>::value) jacobi_cluster_k
     __shared__ T* s_sig[kMaxCluster];
     __shared__ T* s_nrm[kMaxCluster];
     __shared__ int s_rotv[2], s_keep, s_nonfinite;
-    __shared__ double s_nuc;
+    __shared__ double s_nuc, s_fro;
     __shared__ unsigned long long s_pairs, s_rots;
 
     if (tid == 0) {
+        s_fro = 0.0;
         s_rotv[0] = 0;
         s_rotv[1] = 0;
         s_pairs = 0;
@@ -202,6 +203,7 @@ __global__ void __launch_bounds__(ClusterBound<T, K, R>::value) jacobi_cluster_k
         buf(0)[(size_t)ldA * sK + c] = T(1);
         buf(1)[(size_t)ldA * sK + c] = T(1);
     }
+    T fro = T(0);  // this thread's share of ||A||_F^2
     for (int h = 0; h < 2; ++h) {
         const int c0 = (h == 0 ? rank : 2 * C - 1 - rank) * sK;
         const int nloc = n - c0 < sK ? (n - c0 > 0 ? n - c0 : 0) : sK;
@@ -211,19 +213,31 @@ __global__ void __launch_bounds__(ClusterBound<T, K, R>::value) jacobi_cluster_k
             int r, c;
             if (tr) { r = (int)(e / nloc); c = (int)(e % nloc); }  // source row c0 + c, column r
             else { c = (int)(e / m); r = (int)(e % m); }
-            A[(size_t)c * ldA + r] = tr ? src[(size_t)(c0 + c) + (size_t)n1 * r] : src[(size_t)r + (size_t)n1 * (c0 + c)];
+            const T v = tr ? src[(size_t)(c0 + c) + (size_t)n1 * r] : src[(size_t)r + (size_t)n1 * (c0 + c)];
+            A[(size_t)c * ldA + r] = v;
+            fro = fma(v, v, fro);
         }
     }
+    fro = group_sum<32>(fro);
+    if (lane == 0) atomicAdd(&s_fro, (double)fro);
     cl.sync();
+    // ||A||_F^2 of the whole slice, summed over the cluster in rank order (the
+    // same value, hence the same decision, in every CTA): a slice whose
+    // Frobenius norm is below the threshold has every singular value below
+    // it, so Y = 0 and the sweeps are skipped (the rebuild keeps nothing)
+    const T tau = a.ctl ? (T)(1.0 / a.ctl->beta) : (T)(item ? item->tau : a.tau);
+    double fro_all = 0.0;
+    for (int r = 0; r < C; ++r) fro_all += *cl.map_shared_rank(&s_fro, r);
+    const bool skip = fro_all * (1.0 + 1e-3) < (double)tau * (double)tau;
 
     // ---- sweeps
     const T tol = sqrt((T)m) * Num<T>::unit();
     Counters cnt{0, 0, 0};
-    int sweeps = 0, converged = 0;
+    int sweeps = 0, converged = skip ? 1 : 0;
     const int max_sweeps = a.max_sweeps > 0 ? a.max_sweeps : 30;
     const int nss = 2 * C - 1;
     int k = 0;  // super-block moves so far
-    while (sweeps < max_sweeps) {
+    while (!skip && sweeps < max_sweeps) {
         const int par = sweeps & 1;
         const int big0 = cnt.big;
         for (int ss = 0; ss < nss; ++ss, ++k) {
@@ -307,7 +321,6 @@ __global__ void __launch_bounds__(ClusterBound<T, K, R>::value) jacobi_cluster_k
     }
     cl.sync();
 
-    const T tau = a.ctl ? (T)(1.0 / a.ctl->beta) : (T)(item ? item->tau : a.tau);
     // ---- kept columns (sigma > tau) in ascending order, the same list in every CTA
     if (warp == 0) {
         int kk = 0;

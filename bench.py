@@ -373,6 +373,12 @@ def next_legs(ctx, torch, dev, flush, serve_jobs):
     slices = sum(Z.shape[2] for Z in Zs)
     plan = ctx.tsvt_batch(Zd, taus, Yd, prec="fp32", graph=True, autotune=True)
     ms_b = timed(plan.run, 10, flush, stream, torch)
+    Zd64 = [tnn.to_fortran(Z, device=dev, dtype=torch.float64) for Z in Zs]
+    Yd64 = [tnn.fortran_empty(Z.shape, torch.float64, device=dev) for Z in Zs]
+    plan64 = ctx.tsvt_batch(Zd64, taus, Yd64, prec="fp64", graph=True)
+    ms_b64 = timed(plan64.run, 2, flush, stream, torch)
+    plan64.close()
+    del Zd64, Yd64
     ms_l = timed(lambda: [ctx.tsvt(z, t, Y=y, prec="fp32") for z, t, y in zip(Zd, taus, Yd)], 3, flush, stream, torch)
     prof = plan.profile()
     out["batched_tsvt"] = {
@@ -381,6 +387,7 @@ def next_legs(ctx, torch, dev, flush, serve_jobs):
         "value": slices / (float(np.median(ms_b)) / 1e3), "unit": "slices/s",
         "ms_per_batch": float(np.median(ms_b)), "launches_per_batch": plan.info()["launches"],
         "per_tensor_loop_ms": float(np.median(ms_l)), "speedup_vs_loop": float(np.median(ms_l) / np.median(ms_b)),
+        "fp64_plain_ms_per_batch": float(np.median(ms_b64)),
         "groups": [dict(g, ms=t) for g, t in zip(plan.groups(), prof["groups"])],
         "transform_ms": prof["forward"] + prof["inverse"]}
     plan.close()
@@ -418,10 +425,19 @@ def next_legs(ctx, torch, dev, flush, serve_jobs):
                          ("dct_tuned_ms", ctx.tsvt)):
             row[name] = float(np.median(timed(lambda: fn(Zd, 1.0, Y=Yd, prec="fp32"), 2, flush, stream, torch)))
         row["dft_over_dct_same_kernel"] = row["dft_plain_ms"] / row["dct_plain_ms"]
+        # the full DCT t-SVD (U, S, V of Theorem 4; no shrink), as Table 2 times it
+        r = min(shp[0], shp[1])
+        U = tnn.fortran_empty((shp[0], r, shp[2]), torch.float32, device=dev)
+        Sd = tnn.fortran_empty((r, shp[2]), torch.float32, device=dev)
+        V = tnn.fortran_empty((shp[1], r, shp[2]), torch.float32, device=dev)
+        row["dct_tsvd_ms"] = float(np.median(timed(lambda: ctx.tsvd(Zd, U, Sd, V, prec="fp32"), 2, flush, stream,
+                                                   torch)))
+        del U, Sd, V
         cmp.append(row)
         del Zd, Yd
     out["dct_vs_dft"] = {"note": "one FP32 t-SVT per tensor; dft/dct_plain share one plain Jacobi kernel (complex "
-                                 "vs real slices, n3/2+1 vs n3 of them); dct_tuned is tsvt_dct",
+                                 "vs real slices, n3/2+1 vs n3 of them); dct_tuned is tsvt_dct; dct_tsvd is "
+                                 "tsvd_dct_forward (U, S, V)",
                          "rows": cmp}
     # ---- serving stream
     jobs = serve.make_stream(serve_jobs, 200.0, tprod=tp)
@@ -447,8 +463,15 @@ def oracle_baseline(B, mask, budget_s=12.0):
         el = time.perf_counter() - t0
         if el >= budget_s or reps >= 20:
             break
+    # the same t-SVT on one core (10 slices of the tensor, scaled to slices/s)
+    O.threads(1)
+    t1 = time.perf_counter()
+    O.tsvt(np.asfortranarray(Z[:, :, :10]), tau, nthreads=1)
+    single = 10 / (time.perf_counter() - t1)
+    O.threads(got)
     return {"value": N3 * reps / el, "unit": "slices/s", "cores": got, "kind": "oracle",
-            "sample": "%d oracle t-SVT(s) of the full 144x176x100 tensor (tau=1.0), %.1f s" % (reps, el)}
+            "sample": "%d oracle t-SVT(s) of the full 144x176x100 tensor (tau=1.0), %.1f s" % (reps, el),
+            "single_core_slices_per_s": single}
 
 
 def run_reference(args):

@@ -206,3 +206,24 @@ def test_batch_64_uneven_tensors_full_size(ctx):
         worst = max(worst, err)
         assert err <= 1e-5, (Z.shape, err)
     log_err("batch c4", worst=worst)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_edge_shapes(ctx, prec):
+    # single tensor; 1 x 1 x 1; one slice; one row / column; identical shapes
+    shapes = [(1, 1, 1), (1, 7, 3), (7, 1, 2), (5, 5, 1), (16, 16, 4), (16, 16, 4)]
+    rng = np.random.default_rng(31)
+    Zs = [inputs.random_tensor(s, rng) for s in shapes]
+    if prec != "fp64":
+        Zs = [Z.astype(np.float32).astype(np.float64) for Z in Zs]
+    taus = [0.1, 0.5, 0.5, 1.0, 2.0, 0.0]
+    for one in (False, True):
+        sel = [0] if one else list(range(len(Zs)))
+        Zd, Yd = _device([Zs[i] for i in sel], prec)
+        plan = ctx.tsvt_batch(Zd, [taus[i] for i in sel], Yd, prec=prec, graph=True)
+        plan.run()
+        for i, Y in zip(sel, _host(Yd)):
+            ref = O.tsvt(Zs[i], taus[i])
+            tol = 1e-12 if prec == "fp64" else 1e-5
+            assert np.linalg.norm(Y - ref) <= tol * max(np.linalg.norm(Zs[i]), 1e-300), shapes[i]
+        plan.close()

@@ -128,3 +128,14 @@ def test_tsvt_dft_special_cases(ctx, prec):
     assert rel_err(tnn.to_numpy(Zd), ref, Z) <= (1e-12 if prec == "fp64" else 1e-5)
     with pytest.raises(tnn.TnnError):
         ctx.tsvt_dft(np.asfortranarray(Z.astype(np.float64 if prec == "fp64" else np.float32)), 0.5, prec=prec)
+
+
+@pytest.mark.parametrize("n3", [1, 2, 3, 4])
+def test_tsvt_dft_short_tubes(ctx, n3):
+    # n3 = 1 is the matrix SVT; n3 = 2 has a real Nyquist slice
+    from paper_1902_03070_gb300 import tnn
+    rng = np.random.default_rng(40 + n3)
+    Z = inputs.random_tensor((9, 7, n3), rng)
+    Yd = tnn.fortran_empty(Z.shape, dtype_of("fp64"))
+    ctx.tsvt_dft(tnn.to_fortran(Z), 0.8, Y=Yd, prec="fp64")
+    assert rel_err(tnn.to_numpy(Yd), D.tsvt_dft(Z, 0.8), Z) <= 1e-12

@@ -164,3 +164,21 @@ def test_shortest_first_admission_order(ctx):
             assert time.time() < t_end
     order = sorted(range(len(ids)), key=lambda i: admitted[ids[i]])
     assert order == sorted(range(len(ids)), key=lambda i: work[i])
+
+
+def test_server_zero_iterations_and_full_observation(ctx):
+    from paper_1902_03070_gb300 import tnn
+    rng = np.random.default_rng(12)
+    T = inputs.random_tensor((10, 8, 3), rng)
+    full = np.asfortranarray(np.ones(T.shape, dtype=np.uint8))
+    with tnn.Server(streams=2) as sv:
+        j0 = sv.submit(np.asfortranarray(T), full, tnn.Context.params(max_iter=0), prec="fp64")
+        j1 = sv.submit(np.asfortranarray(T), full, tnn.Context.params(max_iter=20), prec="fp64")
+        t_end = time.time() + 60
+        while sv.state(j0) < 2 or sv.state(j1) < 2:
+            sv.step()
+            assert time.time() < t_end
+        st0, X0, r0, _ = sv.take(j0)
+        st1, X1, r1, _ = sv.take(j1)
+    assert r0["iters"] == 0 and np.array_equal(X0, T)   # X = B on the mask, nothing run
+    assert np.array_equal(X1, T)                        # everything observed: X stays B

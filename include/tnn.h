@@ -10,8 +10,10 @@
  * X(i,j,:) has stride n1*n2 (Section 2).  Element type: double for
  * TNN_FP64, float for every other precision.
  *
- * Pointers.  Tensor arguments may be device pointers or host pointers; the
- * library asks the CUDA runtime which.  Host buffers are staged through the
+ * Pointers.  Tensor arguments of the single-tensor calls may be device
+ * pointers or host pointers; the library asks the CUDA runtime which (the
+ * batched plans and the DFT comparison path take device pointers only, the
+ * server copies its jobs' inputs itself).  Host buffers are staged through the
  * context's device workspace with copies on the given stream (pinned host
  * memory makes those copies asynchronous) and the call then synchronises the
  * stream before it returns.  The caller owns every buffer it passes; the
@@ -67,7 +69,8 @@ typedef enum {
     TNN_FP64 = 0,           /* double data, FP64 arithmetic everywhere (the plain path) */
     TNN_FP32 = 1,           /* float data, FP32 arithmetic on CUDA cores */
     TNN_FP32_TF32X3 = 2,    /* float data, tube DCT on tcgen05 tensor cores, 3xTF32 split */
-    TNN_FP32_BF16SPLIT = 3  /* float data, tube DCT on tcgen05 tensor cores, BF16 hi/mid/lo split */
+    TNN_FP32_BF16SPLIT = 3  /* float data, tube DCT on tcgen05 tensor cores, BF16 hi/lo split (three
+                               products accumulated in FP32) */
 } tnn_precision;
 
 typedef struct {
@@ -239,12 +242,15 @@ tnn_status tsvt_dct_plain(tnn_ctx* ctx, const void* Z, tnn_shape shape, double t
  * memory for the transformed tensors and its launch tables (allocated here,
  * freed by tnn_tsvt_batch_destroy).  A run launches, on one stream, the
  * forward tube transforms of all tensors (one grid), one Jacobi SVT launch
- * per group of slices sharing a kernel variant, and the inverse transforms;
+ * per group of slices sharing a kernel variant and residency (one CTA per
+ * slice, or one thread-block cluster per slice too large for one CTA; the
+ * groups on parallel streams), and the inverse transforms;
  * with TNN_BATCH_GRAPH the sequence is recorded once as a CUDA graph and a
  * run is a single graph launch.  With TNN_BATCH_AUTOTUNE the plan times
  * every compiled Jacobi variant that covers a group on its own data when it
  * is created and keeps the fastest (cached per shape class for the process).
- * Precisions: TNN_FP64 and TNN_FP32 (TNN_FP32_TF32X3 runs as TNN_FP32 here).
+ * Precisions: TNN_FP64 and TNN_FP32 (the tensor-core forms TNN_FP32_TF32X3
+ * and TNN_FP32_BF16SPLIT run as TNN_FP32 here).
  * Host pointers are rejected (TNN_EINVAL).  Creation synchronises `stream`
  * and writes no item buffer; runs are stream-ordered and must not overlap one
  * another (they share the plan's buffers).  Slices are 512 x 512 at most. */

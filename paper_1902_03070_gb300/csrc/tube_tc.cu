@@ -13,15 +13,18 @@
 // accumulation: what it drops (A_lo B_lo and the part of x below x_hi + x_lo)
 // is of order 2^-16 relative, a transform error of a few 1e-6.
 //
-// Staging: the 128 threads load the input strip with coalesced loads (the
-// ADMM prologue Z = X - M/beta is applied here), split it and write the
-// K-major core-matrix layout (8 rows x 16 bytes per core matrix, no swizzle);
+// Staging: 256 threads, two per pixel row (each takes half of a K chunk), load
+// the input strip with coalesced loads (the ADMM prologue Z = X - M/beta is
+// applied here), split it and write the K-major core-matrix layout (8 rows x
+// 16 bytes per core matrix, no swizzle);
 // the operator's hi/lo images are prebuilt in the same layout, chunk by chunk,
 // and each chunk is copied in by bulk asynchronous copies (TMA engine) that
 // complete on an mbarrier.  One thread issues the MMAs and commits them to a
 // second mbarrier; the epilogue reads the accumulator with tcgen05.ld (warp w
-// owns TMEM lanes 32w..32w+31 = pixels) and writes the output coalesced,
-// with the ADMM update fused in the inverse direction.
+// reads TMEM lanes 32 (w % 4) .. + 31 = pixels, the two warps of a lane
+// quarter taking alternate 16-column chunks, so twice the loads are in
+// flight) and writes the output coalesced, with the ADMM update fused in the
+// inverse direction.
 //
 // Every mbarrier wait is bounded: on timeout the kernel records an error,
 // stops issuing work, waits (bounded) for what it has in flight, frees its
@@ -38,7 +41,8 @@ namespace {
 
 constexpr int TBM = 128;          // pixels per CTA (MMA M)
 constexpr int TKC = 32;           // K chunk (input tube positions per stage)
-constexpr int TTHREADS = 128;     // one thread per pixel row
+constexpr int TTHREADS = 256;     // two threads per pixel row (each stages half of a K chunk)
+constexpr int TKH = TKC / 2;      // K values a thread stages per chunk
 constexpr uint32_t kSpinLimit = 1u << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -177,7 +181,7 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar_b[2], bar_mma;
     __shared__ uint32_t s_taddr;
-    __shared__ double red[4][4];
+    __shared__ double red[TTHREADS / 32][4];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t p0 = (int64_t)blockIdx.x * TBM;
@@ -211,7 +215,8 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t taddr = s_taddr;
     const uint32_t idesc = BF ? make_idesc_bf16(TBM, NP) : make_idesc_tf32(TBM, NP);
-    const int64_t p = p0 + tid;
+    const int row = tid & (TBM - 1), half = tid / TBM;  // staging: pixel row, half of the K chunk
+    const int64_t p = p0 + row;
     const bool prow = p < P;
 
     uint32_t phase_b[2] = {0u, 0u}, phase_m = 0;
@@ -229,10 +234,10 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
     if (tid == 0) issue_b(0);
     for (int c = 0; c < nchunks; ++c) {
         // this chunk's inputs: all loads first, in flight while the previous chunk's MMAs run
-        const int k0 = c * TKC;
-        float v[TKC], w[TKC];
+        const int k0 = c * TKC + half * TKH;
+        float v[TKH], w[TKH];
 #pragma unroll
-        for (int u = 0; u < TKC; ++u) {
+        for (int u = 0; u < TKH; ++u) {
             const int j = k0 + u;
             const bool ld = prow && j < n3;
             const size_t e = (size_t)p + (size_t)P * (ld ? j : 0);
@@ -252,7 +257,7 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
         }
         if (!BF) {
 #pragma unroll
-            for (int g = 0; g < TKC / 4; ++g) {
+            for (int g = 0; g < TKH / 4; ++g) {
                 float x[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) x[u] = (MODE == 1) ? fmaf(-w[g * 4 + u], rinv, v[g * 4 + u]) : v[g * 4 + u];
@@ -261,13 +266,13 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
                 hi.y = tf32_hi(x[1]); lo.y = x[1] - hi.y;
                 hi.z = tf32_hi(x[2]); lo.z = x[2] - hi.z;
                 hi.w = tf32_hi(x[3]); lo.w = x[3] - hi.w;
-                const uint32_t off = kmajor_off<false>(tid, g * 4);
+                const uint32_t off = kmajor_off<false>(row, half * TKH + g * 4);
                 *reinterpret_cast<float4*>(Ahi + off) = hi;
                 *reinterpret_cast<float4*>(Alo + off) = lo;
             }
         } else {
 #pragma unroll
-            for (int g = 0; g < TKC / 8; ++g) {
+            for (int g = 0; g < TKH / 8; ++g) {
                 uint32_t hw[4], lw[4];
 #pragma unroll
                 for (int u = 0; u < 8; u += 2) {
@@ -281,7 +286,7 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
                     hw[u / 2] = (uint32_t)h0 | ((uint32_t)h1 << 16);
                     lw[u / 2] = (uint32_t)l0 | ((uint32_t)l1 << 16);
                 }
-                const uint32_t off = kmajor_off<true>(tid, g * 8);
+                const uint32_t off = kmajor_off<true>(row, half * TKH + g * 8);
                 *reinterpret_cast<uint4*>(Ahi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
                 *reinterpret_cast<uint4*>(Alo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
             }
@@ -338,16 +343,20 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
     }
 
     if (ok) {
-        // epilogue: warp w reads TMEM lanes 32w..32w+31 (its pixels), 16 columns at a time
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its pixels), 16
+        // columns at a time, the two warps of a lane quarter alternating chunks
+        const int quarter = warp & 3, qhalf = warp >> 2;
+        const int64_t pe = p0 + quarter * 32 + lane;
+        const bool erow = pe < P;
         float sdx = 0.f, sxx = 0.f, syx = 0.f, snx = 0.f;
-        for (int q0 = 0; q0 < NP; q0 += 16) {
+        for (int q0 = qhalf * 16; q0 < NP; q0 += 32) {
             float v[16];
-            tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)q0, v);
+            tmem_ld16(taddr + ((uint32_t)(quarter * 32) << 16) + (uint32_t)q0, v);
             if (MODE != 2) {
 #pragma unroll
                 for (int u = 0; u < 16; ++u) {
                     const int q = q0 + u;
-                    if (prow && q < n3) out[(size_t)p + (size_t)P * q] = v[u];
+                    if (erow && q < n3) out[(size_t)pe + (size_t)P * q] = v[u];
                 }
             } else {
                 // the group's X, M, B, mask loads first, then Algorithm 1's update
@@ -357,8 +366,8 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
 #pragma unroll
                 for (int u = 0; u < 16; ++u) {
                     const int q = q0 + u;
-                    const bool ld = prow && q < n3;
-                    const size_t e = (size_t)p + (size_t)P * (ld ? q : 0);
+                    const bool ld = erow && q < n3;
+                    const size_t e = (size_t)pe + (size_t)P * (ld ? q : 0);
                     xv[u] = ld ? Xs[e] : 0.f;
                     mv[u] = ld ? Ms[e] : 0.f;
                     kv[u] = ld ? mask[e] : (uint8_t)0;
@@ -368,8 +377,8 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
 #pragma unroll
                 for (int u = 0; u < 16; ++u) {
                     const int q = q0 + u;
-                    if (!prow || q >= n3) continue;
-                    const size_t e = (size_t)p + (size_t)P * q;
+                    if (!erow || q >= n3) continue;
+                    const size_t e = (size_t)pe + (size_t)P * q;
                     const float y = v[u];
                     const float x = xv[u], mm = mv[u];
                     const float xn = kv[u] ? bv[u] : fmaf(mm, rinv, y);

@@ -286,6 +286,44 @@ tnn_status tnn_tsvt_batch_profile(tnn_tsvt_batch* plan, void* stream, double* ms
 tnn_status tnn_tsvt_batch_stats(tnn_tsvt_batch* plan, void* stream, int64_t out[4]);
 void tnn_tsvt_batch_destroy(tnn_tsvt_batch* plan);
 
+/* Batched ADMM: Algorithm 1 for many completion problems of different
+ * shapes at once, each iteration of all of them one launch sequence (one
+ * CUDA-graph launch with TNN_BATCH_GRAPH): the forward transforms with the
+ * Z = X - M/beta prologue of every tensor (one grid), the per-slice Jacobi
+ * SVTs of all tensors (one launch per group of slices sharing a kernel
+ * variant and residency, threshold 1/beta from each job's control block),
+ * the inverse transforms with the fused X/M update (one grid) and every
+ * job's stop test and beta update.  Each job computes exactly what
+ * tnn_complete computes for it alone with TNN_FP32 (or TNN_FP64) transforms,
+ * iterate for iterate, and a job that has stopped is skipped.  Items: device
+ * buffers B, mask (as tnn_complete), X and M (n1 x n2 x n3, the job's state,
+ * owned by the caller and updated in place); one parameter set for all jobs.
+ * Create initialises X = B on the mask, M = 0 and the control blocks (as
+ * tnn_admm_batch_reset does) and synchronises `stream`.  step queues `iters`
+ * iterations (stream-ordered, no host wait); sync waits for them and gives
+ * the number of jobs still running; run steps in growing chunks until every
+ * job stopped or max_iter; report reads job i's state after a sync (returns
+ * TNN_ENOCONV for a job that stopped on max_iter).  TNN_FP32_TF32X3 and
+ * TNN_FP32_BF16SPLIT run as TNN_FP32 here.  The plan owns the transformed
+ * tensors, partial sums, statistics, control blocks and launch tables. */
+typedef struct {
+    const void* B;
+    const uint8_t* mask;
+    void* X;
+    void* M;
+    tnn_shape shape;
+} tnn_admm_item;
+typedef struct tnn_admm_batch tnn_admm_batch;
+tnn_status tnn_admm_batch_create(tnn_ctx* ctx, const tnn_admm_item* items, int32_t count,
+                                 const tnn_admm_params* params, tnn_precision prec, int32_t flags, void* stream,
+                                 tnn_admm_batch** plan);
+tnn_status tnn_admm_batch_reset(tnn_admm_batch* plan, void* stream);
+tnn_status tnn_admm_batch_step(tnn_admm_batch* plan, int32_t iters, void* stream);
+tnn_status tnn_admm_batch_sync(tnn_admm_batch* plan, void* stream, int32_t* running);
+tnn_status tnn_admm_batch_run(tnn_admm_batch* plan, void* stream);
+tnn_status tnn_admm_batch_report(const tnn_admm_batch* plan, int32_t job, tnn_admm_report* rep);
+void tnn_admm_batch_destroy(tnn_admm_batch* plan);
+
 /* Completion server (no counterpart in the paper: the serving layer around
  * Algorithm 1).  A job is a completion problem with tnn_complete's
  * arguments.  Queued jobs are admitted in submission order while the device

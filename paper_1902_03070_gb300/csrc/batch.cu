@@ -175,7 +175,7 @@ std::vector<SliceItem> group_slices(const tnn_tsvt_batch& b, const std::vector<i
         const Shape s = shape_of(b.items[t].shape);
         const int nb = q * ((s.n + q * gp.K - 1) / (q * gp.K));
         for (int k = 0; k < s.n3; ++k) {
-            SliceItem it;
+            SliceItem it{};
             it.data = wbuf[t] + (size_t)k * s.n1 * s.n2 * b.elem;
             it.n1 = s.n1; it.n2 = s.n2;
             it.m = s.m; it.n = s.n; it.tr = s.tr; it.nb = nb;

@@ -618,6 +618,9 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
     const int nthr = blockDim.x;
     const int slice = blockIdx.x;
     const SliceItem* item = ITEMS ? a.items + slice : nullptr;  // batched: per-CTA slice parameters
+    // a batched ADMM job that has stopped: its slices are left as they are
+    const AdmmCtl* ictl = item ? item->ctl : nullptr;
+    if (ictl && ictl->done) return;
     const int m = item ? item->m : a.m, n = item ? item->n : a.n, nb = item ? item->nb : a.nb;
     const int ldA = a.ldA, tr = item ? item->tr : a.tr;
     const int npad = nb * K;
@@ -685,7 +688,7 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
     // the full computation would).  The margin covers the rounding of the sum.
     bool skip = false;
     if (!WITHV) {
-        const double tau0 = a.ctl ? 1.0 / a.ctl->beta : (item ? item->tau : a.tau);
+        const double tau0 = a.ctl ? 1.0 / a.ctl->beta : (ictl ? 1.0 / ictl->beta : (item ? item->tau : a.tau));
         skip = s_fro * (1.0 + 1e-3) < tau0 * tau0;
     }
 
@@ -746,7 +749,7 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
     }
     __syncthreads();
 
-    const T tau = a.ctl ? (T)(1.0 / a.ctl->beta) : (T)(item ? item->tau : a.tau);
+    const T tau = a.ctl ? (T)(1.0 / a.ctl->beta) : (ictl ? (T)(1.0 / ictl->beta) : (T)(item ? item->tau : a.tau));
 
     if (!WITHV) {
         // ---- SVT: kept columns (sigma > tau) and their coefficients

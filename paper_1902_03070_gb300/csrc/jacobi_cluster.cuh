@@ -158,6 +158,9 @@ __global__ void __launch_bounds__(ClusterBound<T, K, R>::value) jacobi_cluster_k
     const int slice = blockIdx.x / C;
     // batched: per-cluster slice parameters from the item table
     const SliceItem* item = ITEMS ? a.items + slice : nullptr;
+    // a batched ADMM job that has stopped (the same flag for every CTA of the cluster)
+    const AdmmCtl* ictl = item ? item->ctl : nullptr;
+    if (ictl && ictl->done) return;
     const int m = item ? item->m : a.m, n = item ? item->n : a.n, nb = item ? item->nb : a.nb;
     const int ldA = a.ldA, tr = item ? item->tr : a.tr;
     const int npad = nb * K;
@@ -225,7 +228,7 @@ __global__ void __launch_bounds__(ClusterBound<T, K, R>::value) jacobi_cluster_k
     // same value, hence the same decision, in every CTA): a slice whose
     // Frobenius norm is below the threshold has every singular value below
     // it, so Y = 0 and the sweeps are skipped (the rebuild keeps nothing)
-    const T tau = a.ctl ? (T)(1.0 / a.ctl->beta) : (T)(item ? item->tau : a.tau);
+    const T tau = a.ctl ? (T)(1.0 / a.ctl->beta) : (ictl ? (T)(1.0 / ictl->beta) : (T)(item ? item->tau : a.tau));
     double fro_all = 0.0;
     for (int r = 0; r < C; ++r) fro_all += *cl.map_shared_rank(&s_fro, r);
     const bool skip = fro_all * (1.0 + 1e-3) < (double)tau * (double)tau;

@@ -102,8 +102,9 @@ struct SliceItem {
     void* data;         // the slice (n1 x n2, leading dimension n1), overwritten by its SVT
     int n1, n2;         // slice shape
     int m, n, tr, nb;   // oriented shape (m >= n), transposed flag, column blocks
-    double tau;         // threshold
+    double tau;         // threshold (when ctl is null)
     SliceStats* stats;  // where the slice's statistics go
+    const AdmmCtl* ctl; // batched ADMM: threshold 1/beta from here; nothing runs once done
 };
 
 enum JacobiMode { JAC_SVT = 0, JAC_SVD = 1 };
@@ -170,6 +171,43 @@ struct TubeItem {
 template <typename T>
 cudaError_t launch_tube_batched(const TubeItem* items, int count, cudaStream_t s);
 int tube_batched_tile();
+
+// ---- batched ADMM steps (tube.cu kernels, batch.cu plans) -----------------------
+// One 128-pixel x 64-position tile of one tensor's forward (MODE 1: in = X,
+// in2 = M, out = W) or inverse (MODE 2: in = W, ADMM update of X, M from B
+// and the mask, partial sums to partials[4 tile ..]) transform.
+struct AdmmTileItem {
+    const void* in;
+    const void* in2;
+    void* out;
+    const void* op;
+    void* X;
+    void* M;
+    const void* B;
+    const uint8_t* mask;
+    double* partials;
+    const AdmmCtl* ctl;
+    int64_t P, p0, tile;
+    int n3, q0;
+};
+// One job's finalize (the per-iteration stop test and beta update).
+struct AdmmJobItem {
+    AdmmCtl* ctl;
+    const double* partials;
+    const SliceStats* stats;
+    int64_t n3;
+    int nblocks, pad_;
+};
+template <typename T>
+cudaError_t launch_tube_admm_batched(const AdmmTileItem* items, int count, int mode, cudaStream_t s);
+cudaError_t launch_admm_finalize_batched(const AdmmJobItem* jobs, int count, cudaStream_t s);
+// Tile grid of the CUDA-core transforms: tile (x, y) covers pixels
+// [x tube_tile_pixels(), ..) and positions [y tube_tile_outputs(), ..);
+// its partial-sum index is y tube_tiles_x(P) + x.
+int tube_tiles_x(int64_t P);
+int tube_tiles_y(int64_t n3);
+int tube_tile_pixels();
+int tube_tile_outputs();
 
 // ---- DFT comparison path (dft.cu) ------------------------------------------------
 // out(p, q) = sum_j in(p, j) op(j, q), q < nout; op nin x nout column-major.

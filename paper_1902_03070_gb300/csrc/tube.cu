@@ -48,23 +48,25 @@ __global__ void build_operator(T* op, int n3, int inverse, int scaled)
 
 struct NoPro {};
 
-// Tile kernel.  MODE 0: plain; MODE 1: forward with prologue Z = X - M/beta;
-// MODE 2: inverse with the ADMM epilogue.
+// One 128-pixel x 64-frequency tile (pixels p0.., output positions q0..).
+// MODE 0: plain; MODE 1: forward with prologue Z = X - M/beta; MODE 2:
+// inverse with the ADMM epilogue, its four partial sums written to
+// partials[4 tile .. 4 tile + 3].  Shared by the per-tensor kernel (one tile
+// per CTA of a 2-D grid) and the batched ADMM step (tiles of many tensors
+// from an item table), so both compute the same bits.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(NT)
-tube_kernel(const T* __restrict__ in, const T* __restrict__ in2, T* __restrict__ out, const T* __restrict__ op,
-            int64_t P, int n3, const AdmmCtl* __restrict__ ctl, T* __restrict__ Xs, T* __restrict__ Ms,
-            const T* __restrict__ Bs, const uint8_t* __restrict__ mask, double* __restrict__ partials)
+__device__ __forceinline__ void tube_tile(const T* __restrict__ in, const T* __restrict__ in2, T* __restrict__ out,
+                                          const T* __restrict__ op, int64_t P, int n3,
+                                          const AdmmCtl* __restrict__ ctl, T* __restrict__ Xs, T* __restrict__ Ms,
+                                          const T* __restrict__ Bs, const uint8_t* __restrict__ mask,
+                                          double* __restrict__ partials, int64_t p0, int q0, int64_t tile)
 {
-    if (MODE != 0 && ctl->done) return;
     __shared__ __align__(16) T As[BK][BM];
     __shared__ T Ts[BK][BN];
 
     const int tid = threadIdx.x;
     const int tp = tid & 31;     // pixel group: pixels tp*4 .. tp*4+3 of the tile
     const int tq = tid >> 5;     // frequency group: q = tq + 8*i
-    const int64_t p0 = (int64_t)blockIdx.x * BM;
-    const int q0 = blockIdx.y * BN;
 
     T rbeta = T(0);
     double beta = 0.0;
@@ -166,8 +168,31 @@ tube_kernel(const T* __restrict__ in, const T* __restrict__ in2, T* __restrict__
     if (tid < 4) {
         double t = 0.0;
         for (int w = 0; w < NT / 32; ++w) t += red[w][tid];
-        partials[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 4 + tid] = t;
+        partials[(size_t)tile * 4 + tid] = t;
     }
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(NT)
+tube_kernel(const T* __restrict__ in, const T* __restrict__ in2, T* __restrict__ out, const T* __restrict__ op,
+            int64_t P, int n3, const AdmmCtl* __restrict__ ctl, T* __restrict__ Xs, T* __restrict__ Ms,
+            const T* __restrict__ Bs, const uint8_t* __restrict__ mask, double* __restrict__ partials)
+{
+    if (MODE != 0 && ctl->done) return;
+    tube_tile<T, MODE>(in, in2, out, op, P, n3, ctl, Xs, Ms, Bs, mask, partials, (int64_t)blockIdx.x * BM,
+                       (int)blockIdx.y * BN, (int64_t)blockIdx.y * gridDim.x + blockIdx.x);
+}
+
+// Batched ADMM step: tiles of many tensors, one CTA each (AdmmTileItem).
+template <typename T, int MODE>
+__global__ void __launch_bounds__(NT) tube_admm_batched_kernel(const AdmmTileItem* __restrict__ items)
+{
+    const AdmmTileItem it = items[blockIdx.x];
+    if (it.ctl->done) return;
+    tube_tile<T, MODE>(static_cast<const T*>(it.in), static_cast<const T*>(it.in2), static_cast<T*>(it.out),
+                       static_cast<const T*>(it.op), it.P, it.n3, it.ctl, static_cast<T*>(it.X),
+                       static_cast<T*>(it.M), static_cast<const T*>(it.B), it.mask, it.partials, it.p0, it.q0,
+                       it.tile);
 }
 
 template <typename T>
@@ -201,10 +226,9 @@ __global__ void ctl_init_kernel(AdmmCtl* ctl, double beta, double rho, double be
 }
 
 // One block, fixed-order reduction: results do not depend on timing.
-__global__ void admm_finalize_kernel(AdmmCtl* ctl, const double* __restrict__ partials, int nblocks,
-                                     const SliceStats* __restrict__ stats, int64_t n3)
+__device__ __forceinline__ void admm_finalize_block(AdmmCtl* ctl, const double* __restrict__ partials, int nblocks,
+                                                    const SliceStats* __restrict__ stats, int64_t n3)
 {
-    if (ctl->done) return;
     __shared__ double red[256][4];
     __shared__ int sw[256], un[256], nf[256];
     const int t = threadIdx.x;
@@ -251,6 +275,21 @@ __global__ void admm_finalize_kernel(AdmmCtl* ctl, const double* __restrict__ pa
     }
 }
 
+__global__ void admm_finalize_kernel(AdmmCtl* ctl, const double* __restrict__ partials, int nblocks,
+                                     const SliceStats* __restrict__ stats, int64_t n3)
+{
+    if (ctl->done) return;
+    admm_finalize_block(ctl, partials, nblocks, stats, n3);
+}
+
+// Batched ADMM step: one block per job.
+__global__ void admm_finalize_batched_kernel(const AdmmJobItem* __restrict__ jobs)
+{
+    const AdmmJobItem j = jobs[blockIdx.x];
+    if (j.ctl->done) return;
+    admm_finalize_block(j.ctl, j.partials, j.nblocks, j.stats, j.n3);
+}
+
 inline dim3 tube_grid(int64_t P, int64_t n3)
 {
     return dim3((unsigned)((P + BM - 1) / BM), (unsigned)((n3 + BN - 1) / BN), 1);
@@ -295,6 +334,27 @@ cudaError_t launch_tube_inv_admm_op(const T* Ybar, T* X, T* M, const T* B, const
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_tube_admm_batched(const AdmmTileItem* items, int count, int mode, cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    if (mode == 1) tube_admm_batched_kernel<T, 1><<<count, NT, 0, s>>>(items);
+    else tube_admm_batched_kernel<T, 2><<<count, NT, 0, s>>>(items);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_admm_finalize_batched(const AdmmJobItem* jobs, int count, cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    admm_finalize_batched_kernel<<<count, 256, 0, s>>>(jobs);
+    return cudaGetLastError();
+}
+
+int tube_tiles_x(int64_t P) { return (int)((P + BM - 1) / BM); }
+int tube_tiles_y(int64_t n3) { return (int)((n3 + BN - 1) / BN); }
+int tube_tile_pixels() { return BM; }
+int tube_tile_outputs() { return BN; }
+
 int tube_partials_count(int64_t P, int64_t n3)
 {
     dim3 g = tube_grid(P, n3);
@@ -333,7 +393,8 @@ cudaError_t launch_admm_finalize(AdmmCtl* ctl, const double* partials, int nbloc
     template cudaError_t launch_tube_inv_admm_op<T>(const T*, T*, T*, const T*, const uint8_t*, const T*,        \
                                                     int64_t, int64_t, const AdmmCtl*, double*, int*,             \
                                                     cudaStream_t);                                               \
-    template cudaError_t launch_admm_init<T>(const T*, const uint8_t*, T*, T*, int64_t, cudaStream_t);
+    template cudaError_t launch_admm_init<T>(const T*, const uint8_t*, T*, T*, int64_t, cudaStream_t);      \
+    template cudaError_t launch_tube_admm_batched<T>(const AdmmTileItem*, int, int, cudaStream_t);
 TNN_INST(float)
 TNN_INST(double)
 #undef TNN_INST

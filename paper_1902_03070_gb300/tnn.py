@@ -127,6 +127,27 @@ _lib.tnn_server_stats.argtypes = [_vp, _ct.POINTER(_ct.c_int64)]
 _lib.tnn_server_stats.restype = _st
 _lib.tnn_server_destroy.argtypes = [_vp]
 _lib.tnn_server_destroy.restype = None
+
+
+class AdmmItem(_ct.Structure):
+    _fields_ = [("B", _vp), ("mask", _vp), ("X", _vp), ("M", _vp), ("shape", Shape)]
+
+
+_lib.tnn_admm_batch_create.argtypes = [_vp, _ct.POINTER(AdmmItem), _ct.c_int32, _ct.POINTER(AdmmParams), _ct.c_int,
+                                       _ct.c_int32, _vp, _ct.POINTER(_vp)]
+_lib.tnn_admm_batch_create.restype = _st
+_lib.tnn_admm_batch_reset.argtypes = [_vp, _vp]
+_lib.tnn_admm_batch_reset.restype = _st
+_lib.tnn_admm_batch_step.argtypes = [_vp, _ct.c_int32, _vp]
+_lib.tnn_admm_batch_step.restype = _st
+_lib.tnn_admm_batch_sync.argtypes = [_vp, _vp, _ct.POINTER(_ct.c_int32)]
+_lib.tnn_admm_batch_sync.restype = _st
+_lib.tnn_admm_batch_run.argtypes = [_vp, _vp]
+_lib.tnn_admm_batch_run.restype = _st
+_lib.tnn_admm_batch_report.argtypes = [_vp, _ct.c_int32, _ct.POINTER(AdmmReport)]
+_lib.tnn_admm_batch_report.restype = _st
+_lib.tnn_admm_batch_destroy.argtypes = [_vp]
+_lib.tnn_admm_batch_destroy.restype = None
 BATCH_GRAPH = 1
 BATCH_AUTOTUNE = 2
 NKERNELS = 11
@@ -143,7 +164,9 @@ EXPORTS = ["tnn_create", "tnn_destroy", "tnn_status_string", "tnn_last_error", "
            "tnn_tsvt_batch_create", "tnn_tsvt_batch_run", "tnn_tsvt_batch_info", "tnn_tsvt_batch_group",
            "tnn_tsvt_batch_profile", "tnn_tsvt_batch_stats", "tnn_tsvt_batch_destroy",
            "tnn_server_create", "tnn_server_submit", "tnn_server_step", "tnn_server_job_state", "tnn_server_take",
-           "tnn_server_stats", "tnn_server_destroy", "tsvt_dft", "tsvt_dct_plain"]
+           "tnn_server_stats", "tnn_server_destroy", "tsvt_dft", "tsvt_dct_plain", "tnn_admm_batch_create",
+           "tnn_admm_batch_reset", "tnn_admm_batch_step", "tnn_admm_batch_sync", "tnn_admm_batch_run",
+           "tnn_admm_batch_report", "tnn_admm_batch_destroy"]
 
 
 class TnnError(RuntimeError):
@@ -398,6 +421,25 @@ class Context:
                   "tnn_tsvt_batch_create")
         return TsvtBatch(h, list(Zs), list(Ys))
 
+    def admm_batch(self, Bs, masks, Xs, Ms, params, prec="fp32", graph=True):
+        """Plan for Algorithm 1 over many device problems at once (initialises
+        X = B on the mask and M = 0).  Returns an AdmmBatch."""
+        if not (len(Bs) == len(masks) == len(Xs) == len(Ms)) or not Bs:
+            raise ValueError("Bs, masks, Xs and Ms must be non-empty and of equal length")
+        arr = (AdmmItem * len(Bs))()
+        for i, (B, m, X, M) in enumerate(zip(Bs, masks, Xs, Ms)):
+            for t in (B, m, X, M):
+                _check_layout(t, B.shape)
+            for t in (B, X, M):
+                _dtype_ok(t, prec)
+            arr[i] = AdmmItem(_ptr(B)[0], _ptr(m)[0], _ptr(X)[0], _ptr(M)[0], Shape(*B.shape))
+        h = _vp()
+        stream = _stream(list(Bs) + list(Xs))
+        self._chk(_lib.tnn_admm_batch_create(self._h, arr, len(Bs), _ct.byref(params), PRECISIONS[prec],
+                                             BATCH_GRAPH if graph else 0, stream, _ct.byref(h)),
+                  "tnn_admm_batch_create")
+        return AdmmBatch(h, (list(Bs), list(masks), list(Xs), list(Ms)))
+
     def last_jacobi_stats(self):
         out = (_ct.c_int64 * 6)()
         self._chk(_lib.tnn_last_jacobi_stats(self._h, out), "tnn_last_jacobi_stats")
@@ -556,6 +598,53 @@ class Server:
 
     def __exit__(self, *a):
         self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class AdmmBatch:
+    """A batched ADMM plan (tnn_admm_batch_*); keeps its tensors alive."""
+
+    def __init__(self, h, keep):
+        self._h = h
+        self._keep = keep
+
+    def _stream(self):
+        return _stream(self._keep[0])
+
+    def _call(self, st, what):
+        if st != OK:
+            raise TnnError(st, what)
+
+    def reset(self):
+        self._call(_lib.tnn_admm_batch_reset(self._h, self._stream()), "tnn_admm_batch_reset")
+
+    def step(self, iters=1):
+        self._call(_lib.tnn_admm_batch_step(self._h, int(iters), self._stream()), "tnn_admm_batch_step")
+
+    def sync(self):
+        r = _ct.c_int32(0)
+        self._call(_lib.tnn_admm_batch_sync(self._h, self._stream(), _ct.byref(r)), "tnn_admm_batch_sync")
+        return r.value
+
+    def run(self):
+        self._call(_lib.tnn_admm_batch_run(self._h, self._stream()), "tnn_admm_batch_run")
+
+    def report(self, i):
+        rep = AdmmReport()
+        st = _lib.tnn_admm_batch_report(self._h, int(i), _ct.byref(rep))
+        if st not in (OK, ENOCONV, ENONFINITE):
+            raise TnnError(st, "tnn_admm_batch_report")
+        return st, rep.as_dict()
+
+    def close(self):
+        if self._h:
+            _lib.tnn_admm_batch_destroy(self._h)
+            self._h = None
 
     def __del__(self):
         try:

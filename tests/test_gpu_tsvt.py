@@ -228,3 +228,30 @@ def test_tsvt_forced_cluster(ctx, monkeypatch, prec, C):
         assert np.linalg.norm(Y2 - ref) <= bound
         assert np.linalg.norm(Y1 - ref) <= bound
     assert abs(t1 - t2) <= (1e-12 if prec == "fp64" else 1e-5) * abs(t1)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_tsvt_random_shape_sweep(ctx, prec):
+    """Seeded random shapes across the variant, shared-memory, global-memory
+    and cluster boundaries (m up to 512, either orientation, n3 up to 6),
+    each against the oracle."""
+    rng = np.random.default_rng(2026 if prec == "fp64" else 2027)
+    for _ in range(14):
+        n1 = int(rng.integers(1, 513))
+        n2 = int(rng.integers(1, 513))
+        n3 = int(rng.integers(1, 7))
+        if n1 * n2 * n3 > 600_000:
+            n3 = max(1, 600_000 // (n1 * n2))
+        shape = (n1, n2, n3)
+        Z = inputs.random_tensor(shape, rng)
+        if prec != "fp64":
+            Z = Z.astype(np.float32).astype(np.float64)
+        tau = tau_at_quantile(Z, float(rng.uniform(0.1, 0.9)))
+        Y = _run(ctx, Z, tau, prec)
+        ref = O.tsvt(Z, tau, nthreads=THREADS)
+        if prec == "fp64":
+            assert rel_err(Y, ref, Z) <= TOL["fp64"], shape
+        else:
+            m, n = max(n1, n2), min(n1, n2)
+            bound = max(1e-5, 2.0 * np.sqrt(m * n) * U32) * np.linalg.norm(Z)
+            assert np.linalg.norm(Y - ref) <= bound, shape

@@ -473,6 +473,10 @@ def next_legs(ctx, torch, dev, flush, serve_jobs):
     summ.update({"rate_jobs_per_s": 200.0, "policy": "shortest estimated work first, at most 8 running",
                  "note": "the stream's offered load is far above what one GPU completes: latency is queueing"})
     out["serving"] = summ
+    _, summ = serve.run(jobs, streams=8, chunk=8, max_active=8, policy=1, batch_kernels=True)
+    summ.update({"rate_jobs_per_s": 200.0, "policy": "as serving, FP32 and FP64 jobs' iterations batched (one "
+                                                     "launch sequence per precision per iteration)"})
+    out["serving_batched"] = summ
     return out
 
 

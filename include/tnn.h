@@ -335,10 +335,19 @@ void tnn_admm_batch_destroy(tnn_admm_batch* plan);
  * next `chunk` iterations of every running job; jobs are spread over
  * `streams` CUDA streams so their kernels overlap, and a step never waits on
  * the GPU.  A job runs exactly tnn_complete's kernels on its own buffers, so
- * its result does not depend on what else is running.  Not thread-safe: one
- * host thread drives a server. */
+ * its result does not depend on what else is running.  With
+ * TNN_SERVER_BATCH_KERNELS in flags, the running FP32 and FP64 jobs (CUDA-core
+ * transforms) run batched instead: per precision, one launch sequence per
+ * iteration covers all of them (the kernels of tnn_admm_batch, tables
+ * rebuilt whenever a job joins or leaves), on one extra stream per
+ * precision; each job still gets the iterates it would get alone, bit for
+ * bit, and jobs with another jacobi_max_sweeps than the first running one
+ * wait for a later pass.  The tables and Jacobi scratch of a batch count
+ * towards the footprint.  Not thread-safe: one host thread drives a
+ * server. */
 #define TNN_SERVER_FIFO 0           /* admit in submission order */
 #define TNN_SERVER_SHORTEST_FIRST 1 /* admit the least estimated work first (iterations x n3 x m n^2) */
+#define TNN_SERVER_BATCH_KERNELS 1  /* flags: batched iterations for FP32 and FP64 jobs */
 typedef struct {
     uint64_t hbm_cap_bytes; /* 0: 150e9 */
     int32_t max_active;     /* 0: no limit beyond the footprint cap */
@@ -346,6 +355,7 @@ typedef struct {
     int32_t chunk;          /* iterations queued per job per step; 0: 8 */
     int32_t device;
     int32_t policy;         /* TNN_SERVER_FIFO or TNN_SERVER_SHORTEST_FIRST */
+    int32_t flags;          /* 0 or TNN_SERVER_BATCH_KERNELS; other bits: TNN_EINVAL */
 } tnn_server_params;
 typedef struct tnn_server tnn_server;
 tnn_status tnn_server_create(const tnn_server_params* params, tnn_server** server);

@@ -23,17 +23,171 @@
 
 using namespace tnn;
 
-struct tnn_admm_batch {
-    struct Group {
-        JacobiPlan plan;
-        int off = 0, count = 0;
-        void* work = nullptr;
-        double cost = 0;
+namespace tnn {
+
+void build_admm_tiles(const std::vector<const AdmmJob*>& jobs, std::vector<AdmmTileItem>& fwd,
+                      std::vector<AdmmTileItem>& inv, std::vector<AdmmJobItem>& jt)
+{
+    const int tp = tube_tile_pixels(), tq = tube_tile_outputs();
+    fwd.clear();
+    inv.clear();
+    jt.assign(jobs.size(), AdmmJobItem{});
+    for (size_t i = 0; i < jobs.size(); ++i) {
+        const AdmmJob& j = *jobs[i];
+        const int64_t P = j.sh.n1 * j.sh.n2;
+        const int tx = tube_tiles_x(P), ty = tube_tiles_y(j.sh.n3);
+        for (int y = 0; y < ty; ++y)
+            for (int x = 0; x < tx; ++x) {
+                AdmmTileItem a{};
+                a.P = P;
+                a.n3 = (int)j.sh.n3;
+                a.p0 = (int64_t)x * tp;
+                a.q0 = y * tq;
+                a.tile = (int64_t)y * tx + x;
+                a.ctl = j.ctl;
+                a.partials = j.partials;
+                AdmmTileItem fw = a, iv = a;
+                fw.in = j.X;
+                fw.in2 = j.M;
+                fw.out = j.W;
+                fw.op = j.opf.op;
+                iv.in = j.W;
+                iv.op = j.opi.op;
+                iv.X = j.X;
+                iv.M = j.M;
+                iv.B = j.B;
+                iv.mask = j.mask;
+                fwd.push_back(fw);
+                inv.push_back(iv);
+            }
+        jt[i].ctl = j.ctl;
+        jt[i].partials = j.partials;
+        jt[i].stats = j.stats;
+        jt[i].n3 = j.sh.n3;
+        jt[i].nblocks = tx * ty;
+    }
+}
+
+bool build_admm_slices(int elem, const std::vector<const AdmmJob*>& jobs, std::vector<SliceGroup>& groups,
+                       std::vector<SliceItem>& slices)
+{
+    groups.clear();
+    slices.clear();
+    auto vkey = [](const JacobiPlan& p) { return p.L * 1000 + p.RA * 10 + p.K; };
+    std::map<std::tuple<int, int, int>, std::vector<int>> byv;
+    for (size_t i = 0; i < jobs.size(); ++i) {
+        const tnn_shape& sh = jobs[i]->sh;
+        JacobiPlan jp;
+        if (!jacobi_plan_mode(sh.n1, sh.n2, sh.n3, elem, false, &jp, true)) return false;
+        byv[std::make_tuple(vkey(jp), (int)jp.in_smem, jp.cluster)].push_back((int)i);
+    }
+    struct G { std::vector<int> tensors; int mmax = 0, nmax = 0, count = 0, key = 0, cluster = 0; double cost = 0; };
+    std::vector<G> gs;
+    for (auto& kv : byv) {
+        G g;
+        g.tensors = kv.second;
+        g.key = std::get<0>(kv.first);
+        g.cluster = std::get<2>(kv.first);
+        for (int t : g.tensors) {
+            const tnn_shape& sh = jobs[t]->sh;
+            const int m = (int)std::max(sh.n1, sh.n2), n = (int)std::min(sh.n1, sh.n2);
+            g.mmax = std::max(g.mmax, m);
+            g.nmax = std::max(g.nmax, n);
+            g.count += (int)sh.n3;
+            g.cost = std::max(g.cost, (double)m * n * n);
+        }
+        gs.push_back(g);
+    }
+    // groups with the longest slices first, so they start at once
+    std::sort(gs.begin(), gs.end(), [](const G& x, const G& y) { return x.cost > y.cost; });
+    for (const G& g : gs) {
+        SliceGroup grp;
+        bool ok;
+        if (g.cluster > 1) {
+            ok = jacobi_plan_mode(g.mmax, g.nmax, g.count, elem, false, &grp.plan, true) &&
+                 grp.plan.cluster == g.cluster && vkey(grp.plan) == g.key;
+        } else {
+            ok = jacobi_plan_variant(g.mmax, g.nmax, g.count, elem, g.key / 1000, (g.key / 10) % 100, g.key % 10,
+                                     &grp.plan);
+        }
+        if (!ok) return false;
+        grp.off = (int)slices.size();
+        grp.count = g.count;
+        // longest slices first within the group as well
+        std::vector<int> order(g.tensors);
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+            const tnn_shape &a = jobs[x]->sh, &c = jobs[y]->sh;
+            const double ma = (double)std::max(a.n1, a.n2), na = (double)std::min(a.n1, a.n2);
+            const double mc = (double)std::max(c.n1, c.n2), nc = (double)std::min(c.n1, c.n2);
+            return ma * na * na > mc * nc * nc;
+        });
+        const int q = grp.plan.cluster > 1 ? 4 * grp.plan.cluster : 2;
+        for (int t : order) {
+            const AdmmJob& j = *jobs[t];
+            const int n1 = (int)j.sh.n1, n2 = (int)j.sh.n2;
+            const int m = std::max(n1, n2), n = std::min(n1, n2);
+            const int nb = q * ((n + q * grp.plan.K - 1) / (q * grp.plan.K));
+            for (int k = 0; k < (int)j.sh.n3; ++k) {
+                SliceItem it{};
+                it.data = static_cast<char*>(j.W) + (size_t)k * n1 * n2 * elem;
+                it.n1 = n1;
+                it.n2 = n2;
+                it.m = m;
+                it.n = n;
+                it.tr = n1 < n2 ? 1 : 0;
+                it.nb = nb;
+                it.tau = 0.0;
+                it.ctl = j.ctl;
+                it.stats = j.stats + k;
+                slices.push_back(it);
+            }
+        }
+        groups.push_back(grp);
+    }
+    return true;
+}
+
+cudaError_t enqueue_admm_iteration(int elem, const AdmmTileItem* fwd, const AdmmTileItem* inv, int ntiles,
+                                   const AdmmJobItem* jobs, int njobs, const std::vector<SliceGroup>& groups,
+                                   const SliceItem* slices, int sweeps, cudaStream_t s, const cudaStream_t* side,
+                                   int nside, cudaEvent_t fork, const cudaEvent_t* join)
+{
+    cudaError_t e;
+    auto tiles = [&](const AdmmTileItem* d, int mode, cudaStream_t st) {
+        return elem == 8 ? launch_tube_admm_batched<double>(d, ntiles, mode, st)
+                         : launch_tube_admm_batched<float>(d, ntiles, mode, st);
     };
+    auto jac = [&](const SliceGroup& g, cudaStream_t st) {
+        return elem == 8 ? launch_jacobi_svt_items<double>(g.plan, slices + g.off, g.count, sweeps, g.work, st)
+                         : launch_jacobi_svt_items<float>(g.plan, slices + g.off, g.count, sweeps, g.work, st);
+    };
+    if ((e = tiles(fwd, 1, s)) != cudaSuccess) return e;
+    const int ns = std::min<int>(nside, (int)groups.size());
+    if (ns <= 1) {
+        for (const auto& g : groups)
+            if ((e = jac(g, s)) != cudaSuccess) return e;
+    } else {
+        if ((e = cudaEventRecord(fork, s)) != cudaSuccess) return e;
+        for (int i = 0; i < ns; ++i)
+            if ((e = cudaStreamWaitEvent(side[i], fork, 0)) != cudaSuccess) return e;
+        for (size_t gi = 0; gi < groups.size(); ++gi)
+            if ((e = jac(groups[gi], side[gi % ns])) != cudaSuccess) return e;
+        for (int i = 0; i < ns; ++i) {
+            if ((e = cudaEventRecord(join[i], side[i])) != cudaSuccess) return e;
+            if ((e = cudaStreamWaitEvent(s, join[i], 0)) != cudaSuccess) return e;
+        }
+    }
+    if ((e = tiles(inv, 2, s)) != cudaSuccess) return e;
+    return launch_admm_finalize_batched(jobs, njobs, s);
+}
+
+}  // namespace tnn
+
+struct tnn_admm_batch {
     int device = 0, elem = 4, count = 0;
     tnn_admm_params prm{};
     std::vector<tnn_admm_item> items;
-    std::vector<Group> groups;
+    std::vector<SliceGroup> groups;
     void* mem = nullptr;
     void* mem_w = nullptr;
     AdmmTileItem* d_fwd = nullptr;
@@ -56,49 +210,12 @@ namespace {
 
 size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-int vkey(const JacobiPlan& p) { return p.L * 1000 + p.RA * 10 + p.K; }
-
-cudaError_t jacobi_items(int elem, const JacobiPlan& gp, const SliceItem* d, int count, int sweeps, void* work,
-                         cudaStream_t s)
-{
-    return elem == 8 ? launch_jacobi_svt_items<double>(gp, d, count, sweeps, work, s)
-                     : launch_jacobi_svt_items<float>(gp, d, count, sweeps, work, s);
-}
-
-cudaError_t tiles(int elem, const AdmmTileItem* d, int count, int mode, cudaStream_t s)
-{
-    return elem == 8 ? launch_tube_admm_batched<double>(d, count, mode, s)
-                     : launch_tube_admm_batched<float>(d, count, mode, s);
-}
-
 // One iteration of every job (valid on a live stream and under capture).
 cudaError_t enqueue_step(tnn_admm_batch* b, cudaStream_t s)
 {
-    cudaError_t e;
-    if ((e = tiles(b->elem, b->d_fwd, b->ntiles, 1, s)) != cudaSuccess) return e;
-    const int ns = std::min<int>(tnn_admm_batch::kStreams, (int)b->groups.size());
-    if (ns <= 1) {
-        for (auto& g : b->groups)
-            if ((e = jacobi_items(b->elem, g.plan, b->d_slices + g.off, g.count, b->prm.jacobi_max_sweeps, g.work,
-                                  s)) != cudaSuccess)
-                return e;
-    } else {
-        if ((e = cudaEventRecord(b->fork, s)) != cudaSuccess) return e;
-        for (int i = 0; i < ns; ++i)
-            if ((e = cudaStreamWaitEvent(b->side[i], b->fork, 0)) != cudaSuccess) return e;
-        for (size_t gi = 0; gi < b->groups.size(); ++gi) {
-            auto& g = b->groups[gi];
-            if ((e = jacobi_items(b->elem, g.plan, b->d_slices + g.off, g.count, b->prm.jacobi_max_sweeps, g.work,
-                                  b->side[gi % ns])) != cudaSuccess)
-                return e;
-        }
-        for (int i = 0; i < ns; ++i) {
-            if ((e = cudaEventRecord(b->join[i], b->side[i])) != cudaSuccess) return e;
-            if ((e = cudaStreamWaitEvent(s, b->join[i], 0)) != cudaSuccess) return e;
-        }
-    }
-    if ((e = tiles(b->elem, b->d_inv, b->ntiles, 2, s)) != cudaSuccess) return e;
-    return launch_admm_finalize_batched(b->d_jobs, b->count, s);
+    return enqueue_admm_iteration(b->elem, b->d_fwd, b->d_inv, b->ntiles, b->d_jobs, b->count, b->groups,
+                                  b->d_slices, b->prm.jacobi_max_sweeps, s, b->side, tnn_admm_batch::kStreams,
+                                  b->fork, b->join);
 }
 
 cudaError_t enqueue_reset(tnn_admm_batch* b, cudaStream_t s)
@@ -186,7 +303,6 @@ tnn_status tnn_admm_batch_create(tnn_ctx* ctx, const tnn_admm_item* items, int32
 
     // ---- device layout: per job W, partials, statistics, control block;
     // operators per tube length; tile, job and slice tables
-    const int tp = tube_tile_pixels(), tq = tube_tile_outputs();
     std::vector<size_t> oW(count), oP(count), oS(count);
     std::vector<int> ntile(count);
     std::map<int64_t, std::pair<size_t, size_t>> ops;
@@ -243,132 +359,48 @@ tnn_status tnn_admm_batch_create(tnn_ctx* ctx, const tnn_admm_item* items, int32
             BCK(launch_build_operator<float>((float*)(base + kv.second.second), kv.first, 1, 0, s), "operator");
         }
     }
+    std::vector<AdmmJob> jobs(count);
+    std::vector<const AdmmJob*> jp(count);
+    for (int i = 0; i < count; ++i) {
+        const tnn_admm_item& it = items[i];
+        AdmmJob& j = jobs[i];
+        j = AdmmJob{};
+        j.sh = it.shape;
+        j.prec = prec;
+        j.elem = elem;
+        j.B = it.B;
+        j.mask = it.mask;
+        j.X = it.X;
+        j.M = it.M;
+        j.W = base + oW[i];
+        j.ctl = b->d_ctl + i;
+        j.partials = reinterpret_cast<double*>(base + oP[i]);
+        j.stats = reinterpret_cast<SliceStats*>(base + oS[i]);
+        j.opf.op = base + ops[it.shape.n3].first;
+        j.opi.op = base + ops[it.shape.n3].second;
+        jp[i] = &j;
+    }
     {
         std::vector<AdmmTileItem> f, v;
-        std::vector<AdmmJobItem> jt(count);
-        f.reserve(ntiles);
-        v.reserve(ntiles);
-        for (int i = 0; i < count; ++i) {
-            const tnn_admm_item& it = items[i];
-            const int64_t P = it.shape.n1 * it.shape.n2;
-            const int tx = tube_tiles_x(P), ty = tube_tiles_y(it.shape.n3);
-            const auto& oo = ops[it.shape.n3];
-            double* part = reinterpret_cast<double*>(base + oP[i]);
-            for (int y = 0; y < ty; ++y)
-                for (int x = 0; x < tx; ++x) {
-                    AdmmTileItem a{};
-                    a.P = P;
-                    a.n3 = (int)it.shape.n3;
-                    a.p0 = (int64_t)x * tp;
-                    a.q0 = y * tq;
-                    a.tile = (int64_t)y * tx + x;
-                    a.ctl = b->d_ctl + i;
-                    a.partials = part;
-                    AdmmTileItem fw = a, iv = a;
-                    fw.in = it.X;
-                    fw.in2 = it.M;
-                    fw.out = base + oW[i];
-                    fw.op = base + oo.first;
-                    iv.in = base + oW[i];
-                    iv.op = base + oo.second;
-                    iv.X = it.X;
-                    iv.M = it.M;
-                    iv.B = it.B;
-                    iv.mask = it.mask;
-                    f.push_back(fw);
-                    v.push_back(iv);
-                }
-            jt[i].ctl = b->d_ctl + i;
-            jt[i].partials = part;
-            jt[i].stats = reinterpret_cast<SliceStats*>(base + oS[i]);
-            jt[i].n3 = it.shape.n3;
-            jt[i].nblocks = tx * ty;
-        }
+        std::vector<AdmmJobItem> jt;
+        build_admm_tiles(jp, f, v, jt);
         BCK(cudaMemcpyAsync(b->d_fwd, f.data(), sizeof(AdmmTileItem) * ntiles, cudaMemcpyHostToDevice, s), "table");
         BCK(cudaMemcpyAsync(b->d_inv, v.data(), sizeof(AdmmTileItem) * ntiles, cudaMemcpyHostToDevice, s), "table");
         BCK(cudaMemcpyAsync(b->d_jobs, jt.data(), sizeof(AdmmJobItem) * count, cudaMemcpyHostToDevice, s), "table");
     }
 
     // ---- Jacobi groups: tensors by the plan each would get alone
-    std::map<std::tuple<int, int, int>, std::vector<int>> byv;
-    for (int i = 0; i < count; ++i) {
-        JacobiPlan jp;
-        jacobi_plan_mode(items[i].shape.n1, items[i].shape.n2, items[i].shape.n3, elem, false, &jp, true);
-        byv[std::make_tuple(vkey(jp), (int)jp.in_smem, jp.cluster)].push_back(i);
-    }
-    struct G { std::vector<int> tensors; int mmax = 0, nmax = 0, count = 0, key = 0, cluster = 0; double cost = 0; };
-    std::vector<G> gs;
-    for (auto& kv : byv) {
-        G g;
-        g.tensors = kv.second;
-        g.key = std::get<0>(kv.first);
-        g.cluster = std::get<2>(kv.first);
-        for (int t : g.tensors) {
-            const tnn_shape& sh = items[t].shape;
-            const int m = (int)std::max(sh.n1, sh.n2), n = (int)std::min(sh.n1, sh.n2);
-            g.mmax = std::max(g.mmax, m);
-            g.nmax = std::max(g.nmax, n);
-            g.count += (int)sh.n3;
-            g.cost = std::max(g.cost, (double)m * n * n);
-        }
-        gs.push_back(g);
-    }
-    std::sort(gs.begin(), gs.end(), [](const G& x, const G& y) { return x.cost > y.cost; });
     std::vector<SliceItem> all;
-    all.reserve(nslices);
-    std::vector<size_t> woff(gs.size(), 0);
+    if (!build_admm_slices(elem, jp, b->groups, all)) return bail(TNN_EINVAL, "admm batch: no plan covers a group");
     size_t wtotal = 0;
-    for (size_t gi = 0; gi < gs.size(); ++gi) {
-        tnn_admm_batch::Group grp;
-        const G& g = gs[gi];
-        bool ok;
-        if (g.cluster > 1) {
-            ok = jacobi_plan_mode(g.mmax, g.nmax, g.count, elem, false, &grp.plan, true) &&
-                 grp.plan.cluster == g.cluster && vkey(grp.plan) == g.key;
-        } else {
-            ok = jacobi_plan_variant(g.mmax, g.nmax, g.count, elem, g.key / 1000, (g.key / 10) % 100, g.key % 10,
-                                     &grp.plan);
-        }
-        if (!ok) return bail(TNN_EINVAL, "admm batch: no plan covers a group");
-        grp.off = (int)all.size();
-        grp.count = g.count;
-        grp.cost = g.cost;
-        // longest slices first, so the block scheduler starts them first
-        std::vector<int> order(g.tensors);
-        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-            const tnn_shape &a = items[x].shape, &c = items[y].shape;
-            const double ma = (double)std::max(a.n1, a.n2), na = (double)std::min(a.n1, a.n2);
-            const double mc = (double)std::max(c.n1, c.n2), nc = (double)std::min(c.n1, c.n2);
-            return ma * na * na > mc * nc * nc;
-        });
-        const int q = grp.plan.cluster > 1 ? 4 * grp.plan.cluster : 2;
-        for (int t : order) {
-            const tnn_shape& sh = items[t].shape;
-            const int n1 = (int)sh.n1, n2 = (int)sh.n2;
-            const int m = std::max(n1, n2), n = std::min(n1, n2);
-            const int nb = q * ((n + q * grp.plan.K - 1) / (q * grp.plan.K));
-            for (int k = 0; k < (int)sh.n3; ++k) {
-                SliceItem it{};
-                it.data = base + oW[t] + (size_t)k * n1 * n2 * elem;
-                it.n1 = n1;
-                it.n2 = n2;
-                it.m = m;
-                it.n = n;
-                it.tr = n1 < n2 ? 1 : 0;
-                it.nb = nb;
-                it.tau = 0.0;
-                it.ctl = b->d_ctl + t;
-                it.stats = reinterpret_cast<SliceStats*>(base + oS[t]) + k;
-                all.push_back(it);
-            }
-        }
+    std::vector<size_t> woff(b->groups.size(), 0);
+    for (size_t gi = 0; gi < b->groups.size(); ++gi) {
         woff[gi] = wtotal;
-        wtotal += up256(grp.plan.work_bytes);
-        b->groups.push_back(grp);
+        wtotal += up256(b->groups[gi].plan.work_bytes);
     }
     if (wtotal) {
         if (cudaMalloc(&b->mem_w, wtotal) != cudaSuccess) return bail(TNN_ENOMEM, "admm batch: allocation failed");
-        for (size_t gi = 0; gi < gs.size(); ++gi)
+        for (size_t gi = 0; gi < b->groups.size(); ++gi)
             if (b->groups[gi].plan.work_bytes) b->groups[gi].work = static_cast<char*>(b->mem_w) + woff[gi];
     }
     BCK(cudaMemcpyAsync(b->d_slices, all.data(), sizeof(SliceItem) * all.size(), cudaMemcpyHostToDevice, s),

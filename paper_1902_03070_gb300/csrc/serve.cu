@@ -12,7 +12,13 @@
 // the next queued job.  The host never waits on the GPU inside a pass.
 //
 // Each job runs exactly the kernels of tnn_complete, on its own buffers, so
-// its result is the same bit for bit whatever else is running.
+// its result is the same bit for bit whatever else is running.  With
+// TNN_SERVER_BATCH_KERNELS, the running jobs of a CUDA-core precision (FP32,
+// FP64) instead share one launch sequence per iteration on a batch stream of
+// their precision: the tables of the batched ADMM iteration (forward and
+// inverse tiles, finalize items, slice groups) are rebuilt whenever the set
+// of jobs in it changes, and every job still gets the iterates it would get
+// alone, bit for bit.
 #include <cuda_runtime.h>
 
 #include <string.h>
@@ -53,6 +59,28 @@ struct SJob {
     double work = 0;  // estimated: iterations x slices x m n^2 (one-sided Jacobi sweep cost)
     void* stage = nullptr;  // pinned copy of pageable host inputs (from the server's pool)
     size_t stage_size = 0;
+    int batch = -1;  // batch lane (0 FP32, 1 FP64) when its iterations run batched
+};
+
+// One launch sequence per iteration for the running jobs of one precision.
+struct BatchLane {
+    static constexpr int kSide = 8;
+    int elem = 4;
+    int lane = -1;  // index of its stream among the server's lanes
+    cudaStream_t side[kSide] = {};
+    cudaEvent_t fork = nullptr, join[kSide] = {}, done = nullptr;
+    bool in_flight = false;
+    std::vector<int64_t> ids;  // jobs the device tables describe, in order
+    std::vector<SliceGroup> groups;
+    void* dmem = nullptr;  // tables and Jacobi scratch
+    size_t dcap = 0;
+    void* hstage = nullptr;  // pinned staging of the tables
+    size_t hcap = 0;
+    AdmmTileItem *d_fwd = nullptr, *d_inv = nullptr;
+    AdmmJobItem* d_jobs = nullptr;
+    SliceItem* d_slices = nullptr;
+    int ntiles = 0, njobs = 0;
+    int64_t passes = 0, rebuilds = 0;
 };
 
 // True for pageable host memory (a copy from it would block the host until
@@ -136,6 +164,8 @@ struct tnn_server {
         return p;
     }
     void stage_put(void* p, size_t sz) { stage_free.emplace(sz, p); }
+    BatchLane batch[2];  // FP32, FP64 (TNN_SERVER_BATCH_KERNELS)
+    cudaStream_t xfer = nullptr;  // result copies
     std::chrono::steady_clock::time_point t0;
 
     double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
@@ -167,8 +197,15 @@ bool admit(tnn_server* sv, SJob& j)
     jacobi_plan(j.sh.n1, j.sh.n2, j.sh.n3, elem, &jp);
     const Layout L = layout_of(j.sh, elem, jp);
     int lane = 0;
-    for (int i = 1; i < (int)sv->lanes.size(); ++i)
-        if (sv->lane_load[i] < sv->lane_load[lane]) lane = i;
+    const int bl = (sv->p.flags & TNN_SERVER_BATCH_KERNELS) && (j.prec == TNN_FP32 || j.prec == TNN_FP64)
+                       ? (j.prec == TNN_FP64 ? 1 : 0)
+                       : -1;
+    if (bl >= 0) {
+        lane = sv->batch[bl].lane;
+    } else {
+        for (int i = 1; i < sv->p.streams; ++i)
+            if (sv->lane_load[i] < sv->lane_load[lane]) lane = i;
+    }
     cudaStream_t s = sv->lanes[lane];
     void* mem = nullptr;
     if (cudaMallocAsync(&mem, L.total, s) != cudaSuccess) {
@@ -215,6 +252,9 @@ bool admit(tnn_server* sv, SJob& j)
                  cudaSuccess &&
              admm_prepare_job(sv->ctx, j.aj, s) == TNN_OK;
     }
+    // batched iterations take the CUDA-core operators; a job given
+    // tensor-core ones runs alone on the batch stream
+    j.batch = ok && bl >= 0 && !j.aj.opf.tc && !j.aj.opi.tc ? bl : -1;
     sv->bytes += L.total;
     if (sv->bytes > sv->peak) sv->peak = sv->bytes;
     sv->lane_load[lane] += 1;
@@ -264,6 +304,124 @@ void release(tnn_server* sv, SJob& j)
     }
 }
 
+void fail_job(tnn_server* sv, SJob& j, int* nfin)
+{
+    j.state = 3;
+    j.result = TNN_ECUDA;
+    j.t_finish = sv->now();
+    j.in_flight = false;
+    sv->running -= 1;
+    sv->lane_load[j.lane] -= 1;
+    sv->completed += 1;
+    ++*nfin;
+}
+
+// Point the batch lane's device tables at the jobs `ids` (uploaded through
+// pinned staging on the batch stream).  The previous pass has completed.
+cudaError_t batch_tables(tnn_server* sv, BatchLane& b, const std::vector<int64_t>& ids)
+{
+    std::vector<const AdmmJob*> jobs;
+    for (int64_t id : ids) jobs.push_back(&sv->jobs[id]->aj);
+    std::vector<AdmmTileItem> f, v;
+    std::vector<AdmmJobItem> jt;
+    std::vector<SliceItem> sl;
+    build_admm_tiles(jobs, f, v, jt);
+    if (!build_admm_slices(b.elem, jobs, b.groups, sl)) return cudaErrorInvalidValue;
+    const size_t sf = up256(sizeof(AdmmTileItem) * f.size()), sj = up256(sizeof(AdmmJobItem) * jt.size()),
+                 ss = up256(sizeof(SliceItem) * sl.size());
+    const size_t tables = 2 * sf + sj + ss;
+    size_t work = 0;
+    for (auto& g : b.groups) work += up256(g.plan.work_bytes);
+    cudaStream_t s = sv->lanes[b.lane];
+    cudaError_t e;
+    if (tables + work > b.dcap) {
+        if (b.dmem) {
+            cudaFreeAsync(b.dmem, s);
+            sv->bytes -= b.dcap;
+            b.dmem = nullptr;
+            b.dcap = 0;
+        }
+        const size_t cap = (tables + work) * 5 / 4;
+        if ((e = cudaMallocAsync(&b.dmem, cap, s)) != cudaSuccess) return e;
+        b.dcap = cap;
+        sv->bytes += cap;
+        if (sv->bytes > sv->peak) sv->peak = sv->bytes;
+    }
+    if (tables > b.hcap) {
+        if (b.hstage) sv->stage_put(b.hstage, b.hcap);
+        b.hstage = sv->stage_get(tables, &b.hcap);
+        if (!b.hstage) {
+            b.hcap = 0;
+            return cudaErrorMemoryAllocation;
+        }
+    }
+    char* h = static_cast<char*>(b.hstage);
+    char* d = static_cast<char*>(b.dmem);
+    memcpy(h, f.data(), sizeof(AdmmTileItem) * f.size());
+    memcpy(h + sf, v.data(), sizeof(AdmmTileItem) * v.size());
+    memcpy(h + 2 * sf, jt.data(), sizeof(AdmmJobItem) * jt.size());
+    memcpy(h + 2 * sf + sj, sl.data(), sizeof(SliceItem) * sl.size());
+    if ((e = cudaMemcpyAsync(d, h, tables, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
+    b.d_fwd = reinterpret_cast<AdmmTileItem*>(d);
+    b.d_inv = reinterpret_cast<AdmmTileItem*>(d + sf);
+    b.d_jobs = reinterpret_cast<AdmmJobItem*>(d + 2 * sf);
+    b.d_slices = reinterpret_cast<SliceItem*>(d + 2 * sf + sj);
+    size_t w = tables;
+    for (auto& g : b.groups) {
+        g.work = g.plan.work_bytes ? d + w : nullptr;
+        w += up256(g.plan.work_bytes);
+    }
+    b.ntiles = (int)f.size();
+    b.njobs = (int)jt.size();
+    b.ids = ids;
+    b.rebuilds += 1;
+    return cudaSuccess;
+}
+
+// Queue the next chunk of iterations of the batch lane's running jobs.
+// Jobs with another Jacobi sweep cap than the first one wait for a later
+// pass (the cap is one launch argument).
+void batch_pass(tnn_server* sv, BatchLane& b, int* nfin)
+{
+    if (b.in_flight) return;
+    std::vector<int64_t> ids;
+    int sweeps = -1;
+    for (auto& kv : sv->jobs) {
+        const SJob& j = *kv.second;
+        if (j.state != 1 || j.in_flight || j.batch != (int)(&b - sv->batch)) continue;
+        if (sweeps < 0) sweeps = j.prm.jacobi_max_sweeps;
+        if (j.prm.jacobi_max_sweeps == sweeps) ids.push_back(kv.first);
+    }
+    if (ids.empty()) return;
+    cudaStream_t s = sv->lanes[b.lane];
+    cudaError_t e = ids == b.ids ? cudaSuccess : batch_tables(sv, b, ids);
+    if (e != cudaSuccess) b.ids.clear();
+    for (int it = 0; e == cudaSuccess && it < sv->p.chunk; ++it)
+        e = enqueue_admm_iteration(b.elem, b.d_fwd, b.d_inv, b.ntiles, b.d_jobs, b.njobs, b.groups, b.d_slices,
+                                   sweeps, s, b.side, BatchLane::kSide, b.fork,
+                                   b.join);
+    for (int64_t id : ids) {
+        SJob& j = *sv->jobs[id];
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(j.h_ctl, j.aj.ctl, sizeof(AdmmCtl), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaEventRecord(j.ev, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            fail_job(sv, j, nfin);
+            continue;
+        }
+        j.queued += std::min(sv->p.chunk, std::max(0, j.prm.max_iter - j.queued));
+        j.in_flight = true;
+    }
+    if (e == cudaSuccess && cudaEventRecord(b.done, s) == cudaSuccess) {
+        b.in_flight = true;
+        b.passes += 1;
+    } else {
+        cudaGetLastError();
+        b.ids.clear();
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -276,6 +434,7 @@ tnn_status tnn_server_create(const tnn_server_params* p, tnn_server** out)
     if (p) q = *p;
     if (q.max_active < 0 || q.streams < 0 || q.chunk < 0) return TNN_EINVAL;
     if (q.policy != TNN_SERVER_FIFO && q.policy != TNN_SERVER_SHORTEST_FIRST) return TNN_EINVAL;
+    if (q.flags & ~TNN_SERVER_BATCH_KERNELS) return TNN_EINVAL;
     if (q.hbm_cap_bytes == 0) q.hbm_cap_bytes = 150ull * 1000 * 1000 * 1000;
     if (q.streams == 0) q.streams = 8;
     if (q.chunk == 0) q.chunk = 8;
@@ -290,16 +449,30 @@ tnn_status tnn_server_create(const tnn_server_params* p, tnn_server** out)
         cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
     }
     cudaGetLastError();
-    for (int i = 0; i < q.streams; ++i) {
+    const int nbl = (q.flags & TNN_SERVER_BATCH_KERNELS) ? 2 : 0;
+    bool ok = true;
+    for (int i = 0; ok && i < q.streams + nbl; ++i) {
         cudaStream_t s = nullptr;
-        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
-            cudaGetLastError();
-            for (auto x : sv->lanes) cudaStreamDestroy(x);
-            tnn_destroy(sv->ctx);
-            return TNN_ECUDA;
-        }
+        ok = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;
+        if (!ok) break;
         sv->lanes.push_back(s);
         sv->lane_load.push_back(0);
+    }
+    ok = ok && cudaStreamCreateWithFlags(&sv->xfer, cudaStreamNonBlocking) == cudaSuccess;
+    for (int b = 0; ok && b < nbl; ++b) {
+        BatchLane& L = sv->batch[b];
+        L.elem = b == 1 ? 8 : 4;
+        L.lane = q.streams + b;
+        for (int i = 0; ok && i < BatchLane::kSide; ++i)
+            ok = cudaStreamCreateWithFlags(&L.side[i], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&L.join[i], cudaEventDisableTiming) == cudaSuccess;
+        ok = ok && cudaEventCreateWithFlags(&L.fork, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!ok) {
+        cudaGetLastError();
+        tnn_server_destroy(sv.release());
+        return TNN_ECUDA;
     }
     sv->t0 = std::chrono::steady_clock::now();
     *out = sv.release();
@@ -364,6 +537,13 @@ tnn_status tnn_server_step(tnn_server* sv, int32_t* finished)
         return TNN_ECUDA;
     }
     int nfin = 0;
+    // a finished batch pass: its jobs' events have completed too
+    for (auto& b : sv->batch)
+        if (b.in_flight) {
+            const cudaError_t q = cudaEventQuery(b.done);
+            if (q != cudaErrorNotReady) b.in_flight = false;
+            if (q != cudaSuccess) cudaGetLastError();
+        }
     // retire: running jobs whose last chunk has landed and that stopped
     for (auto& kv : sv->jobs) {
         SJob& j = *kv.second;
@@ -424,7 +604,7 @@ tnn_status tnn_server_step(tnn_server* sv, int32_t* finished)
     // queue the next chunk of every running job that is not in flight
     for (auto& kv : sv->jobs) {
         SJob& j = *kv.second;
-        if (j.state != 1 || j.in_flight) continue;
+        if (j.state != 1 || j.in_flight || j.batch >= 0) continue;
         cudaStream_t s = sv->lanes[j.lane];
         int n = j.prm.max_iter - j.queued;
         if (n > sv->p.chunk) n = sv->p.chunk;
@@ -453,6 +633,8 @@ tnn_status tnn_server_step(tnn_server* sv, int32_t* finished)
         }
         j.in_flight = true;
     }
+    if (sv->p.flags & TNN_SERVER_BATCH_KERNELS)
+        for (auto& b : sv->batch) batch_pass(sv, b, &nfin);
     if (finished) *finished = nfin;
     return TNN_OK;
 }
@@ -476,8 +658,11 @@ tnn_status tnn_server_take(tnn_server* sv, int64_t id, void* X_out, tnn_admm_rep
     tnn_status res = j.result;
     if (j.state == 2 && X_out) {
         const size_t bytes = (size_t)j.sh.n1 * j.sh.n2 * j.sh.n3 * (j.prec == TNN_FP64 ? 8 : 4);
-        cudaStream_t s = sv->lanes[j.lane];
-        if (cudaMemcpyAsync(X_out, j.aj.X, bytes, cudaMemcpyDefault, s) != cudaSuccess ||
+        // on the transfer stream, after the job's last chunk only (its lane
+        // may already run other jobs' iterations)
+        cudaStream_t s = sv->xfer;
+        if (cudaStreamWaitEvent(s, j.ev, 0) != cudaSuccess ||
+            cudaMemcpyAsync(X_out, j.aj.X, bytes, cudaMemcpyDefault, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess) {
             cudaGetLastError();
             res = TNN_ECUDA;
@@ -529,8 +714,19 @@ void tnn_server_destroy(tnn_server* sv)
     for (auto s : sv->lanes) cudaStreamSynchronize(s);
     for (auto& kv : sv->jobs)
         if (kv.second->lane >= 0) release(sv, *kv.second);
+    for (auto& b : sv->batch) {
+        if (b.dmem && b.lane >= 0) cudaFreeAsync(b.dmem, sv->lanes[b.lane]);
+        for (int i = 0; i < BatchLane::kSide; ++i) {
+            if (b.side[i]) cudaStreamSynchronize(b.side[i]);
+            if (b.side[i]) cudaStreamDestroy(b.side[i]);
+            if (b.join[i]) cudaEventDestroy(b.join[i]);
+        }
+        if (b.fork) cudaEventDestroy(b.fork);
+        if (b.done) cudaEventDestroy(b.done);
+    }
     for (auto s : sv->lanes) cudaStreamSynchronize(s);
     for (auto s : sv->lanes) cudaStreamDestroy(s);
+    if (sv->xfer) cudaStreamDestroy(sv->xfer);
     for (auto b : sv->pinned_blocks) cudaFreeHost(b);
     for (auto b : sv->stage_all) cudaFreeHost(b);
     tnn_destroy(sv->ctx);

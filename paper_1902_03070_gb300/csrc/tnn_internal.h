@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/tnn.h"
 
 namespace tnn {
@@ -201,6 +203,30 @@ struct AdmmJobItem {
 template <typename T>
 cudaError_t launch_tube_admm_batched(const AdmmTileItem* items, int count, int mode, cudaStream_t s);
 cudaError_t launch_admm_finalize_batched(const AdmmJobItem* jobs, int count, cudaStream_t s);
+// A group of slices sharing one Jacobi launch (plan: variant, residency,
+// largest block count; n3 = slices).
+struct SliceGroup {
+    JacobiPlan plan;
+    int off = 0, count = 0;
+    void* work = nullptr;  // plan.work_bytes of scratch when not in shared memory
+};
+struct AdmmJob;
+// Launch tables of one batched ADMM iteration over `jobs` (CUDA-core
+// transforms: opf.op / opi.op): forward and inverse tiles, finalize items,
+// and the slice items grouped by the plan each job's slices would get alone
+// (longest slices first).  false if a shape has no plan.
+void build_admm_tiles(const std::vector<const AdmmJob*>& jobs, std::vector<AdmmTileItem>& fwd,
+                      std::vector<AdmmTileItem>& inv, std::vector<AdmmJobItem>& jt);
+bool build_admm_slices(int elem, const std::vector<const AdmmJob*>& jobs, std::vector<SliceGroup>& groups,
+                       std::vector<SliceItem>& slices);
+// One iteration from device tables: forward tiles, the groups (spread over
+// the side streams between fork and join events when more than one), inverse
+// tiles, finalize.
+cudaError_t enqueue_admm_iteration(int elem, const AdmmTileItem* fwd, const AdmmTileItem* inv, int ntiles,
+                                   const AdmmJobItem* jobs, int njobs, const std::vector<SliceGroup>& groups,
+                                   const SliceItem* slices, int sweeps, cudaStream_t s, const cudaStream_t* side,
+                                   int nside, cudaEvent_t fork, const cudaEvent_t* join);
+
 // Tile grid of the CUDA-core transforms: tile (x, y) covers pixels
 // [x tube_tile_pixels(), ..) and positions [y tube_tile_outputs(), ..);
 // its partial-sum index is y tube_tiles_x(P) + x.

@@ -77,12 +77,14 @@ def make_stream(n_jobs, rate, seed=1902_03075, tprod=None, n_batch_shapes=8):
     return jobs
 
 
-def run(jobs, hbm_cap_bytes=150e9, streams=8, chunk=8, max_active=0, policy=0, device=0, timeout_s=600.0):
-    """Drive a server through the stream; returns per-job records and a summary."""
+def run(jobs, hbm_cap_bytes=150e9, streams=8, chunk=8, max_active=0, policy=0, device=0, timeout_s=600.0,
+        batch_kernels=False):
+    """Drive a server through the stream; returns per-job records and a summary.
+    `batch_kernels`: FP32 and FP64 jobs share one launch sequence per iteration."""
     from . import tnn
     recs = [None] * len(jobs)
     with tnn.Server(hbm_cap_bytes=int(hbm_cap_bytes), streams=streams, chunk=chunk, max_active=max_active,
-                    policy=policy, device=device) as sv:
+                    policy=policy, device=device, batch_kernels=batch_kernels) as sv:
         t0 = time.perf_counter()
         pending = {}
         nxt = 0
@@ -133,14 +135,16 @@ def main():
     p.add_argument("--max-active", type=int, default=0)
     p.add_argument("--policy", choices=["fifo", "shortest"], default="fifo")
     p.add_argument("--seed", type=int, default=1902_03075)
+    p.add_argument("--batch-kernels", action="store_true")
     a = p.parse_args()
     from . import tnn
     with tnn.Context(0) as ctx:
         jobs = make_stream(a.jobs, a.rate, seed=a.seed, tprod=library_tprod(ctx))
     _, summary = run(jobs, hbm_cap_bytes=a.hbm_cap_gb * 1e9, streams=a.streams, chunk=a.chunk,
-                     max_active=a.max_active, policy=1 if a.policy == "shortest" else 0)
+                     max_active=a.max_active, policy=1 if a.policy == "shortest" else 0,
+                     batch_kernels=a.batch_kernels)
     summary.update({"rate": a.rate, "streams": a.streams, "chunk": a.chunk, "hbm_cap_gb": a.hbm_cap_gb,
-                    "max_active": a.max_active, "policy": a.policy})
+                    "max_active": a.max_active, "policy": a.policy, "batch_kernels": a.batch_kernels})
     print(json.dumps(summary))
 
 

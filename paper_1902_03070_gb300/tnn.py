@@ -110,7 +110,7 @@ _lib.tnn_tsvt_batch_destroy.restype = None
 
 class ServerParams(_ct.Structure):
     _fields_ = [("hbm_cap_bytes", _ct.c_uint64), ("max_active", _ct.c_int32), ("streams", _ct.c_int32),
-                ("chunk", _ct.c_int32), ("device", _ct.c_int32), ("policy", _ct.c_int32)]
+                ("chunk", _ct.c_int32), ("device", _ct.c_int32), ("policy", _ct.c_int32), ("flags", _ct.c_int32)]
 
 
 _lib.tnn_server_create.argtypes = [_ct.POINTER(ServerParams), _ct.POINTER(_vp)]
@@ -526,9 +526,11 @@ class Server:
     QUEUED, RUNNING, FINISHED, FAILED = range(4)
 
     FIFO, SHORTEST_FIRST = 0, 1
+    BATCH_KERNELS = 1
 
-    def __init__(self, hbm_cap_bytes=0, max_active=0, streams=0, chunk=0, device=0, policy=0):
-        p = ServerParams(int(hbm_cap_bytes), int(max_active), int(streams), int(chunk), int(device), int(policy))
+    def __init__(self, hbm_cap_bytes=0, max_active=0, streams=0, chunk=0, device=0, policy=0, batch_kernels=False):
+        p = ServerParams(int(hbm_cap_bytes), int(max_active), int(streams), int(chunk), int(device), int(policy),
+                         self.BATCH_KERNELS if batch_kernels else 0)
         h = _vp()
         st = _lib.tnn_server_create(_ct.byref(p), _ct.byref(h))
         if st != OK:

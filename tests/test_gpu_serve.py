@@ -1,7 +1,8 @@
 """GPU tests of the completion server (tnn_server_*): a job's result is the
 same, bit for bit, whether it runs alone through tnn_complete or in a mix of
-concurrent jobs of other shapes and precisions; admission keeps the device
-footprint under the cap; invalid jobs are refused at submission."""
+concurrent jobs of other shapes and precisions, with each job's own kernels or
+with batched iterations for the FP32 and FP64 jobs; admission keeps the
+device footprint under the cap; invalid jobs are refused at submission."""
 import time
 
 import numpy as np
@@ -76,11 +77,12 @@ def _run_server(server, jobs, device_inputs, stagger=0.0):
     return [results[j] for j in ids]
 
 
-def test_alone_equals_in_mix(ctx):
+@pytest.mark.parametrize("batch_kernels", [False, True])
+def test_alone_equals_in_mix(ctx, batch_kernels):
     from paper_1902_03070_gb300 import tnn
     jobs = _jobs()
     alone = [_alone(ctx, j) for j in jobs]
-    with tnn.Server(streams=4, chunk=3) as sv:
+    with tnn.Server(streams=4, chunk=3, batch_kernels=batch_kernels) as sv:
         mixed = _run_server(sv, jobs, device_inputs=True, stagger=0.002)
         st = sv.stats()
     assert st["queued"] == 0 and st["running"] == 0
@@ -182,3 +184,34 @@ def test_server_zero_iterations_and_full_observation(ctx):
         st1, X1, r1, _ = sv.take(j1)
     assert r0["iters"] == 0 and np.array_equal(X0, T)   # X = B on the mask, nothing run
     assert np.array_equal(X1, T)                        # everything observed: X stays B
+
+
+def test_batched_jobs_join_and_leave(ctx):
+    """Many FP32 and FP64 jobs of uneven shapes (several Jacobi plans, one
+    cluster-sized) with uneven iteration caps and two Jacobi sweep caps, so
+    that the batch is rebuilt as jobs join and leave: every job's result
+    equals its run alone."""
+    from paper_1902_03070_gb300 import tnn
+    rng = np.random.default_rng(31)
+    shapes = [(32, 40, 8), (96, 64, 16), (50, 120, 9), (256, 200, 4), (40, 40, 33), (70, 30, 12), (129, 65, 5),
+              (300, 260, 2)]
+    jobs = []
+    for i, shape in enumerate(shapes * 2):
+        n1, n2, n3 = shape
+        A, F = inputs.lowrank_factors(n1, n2, n3, 2 + i % 5, rng)
+        T = O.tprod(A, F)
+        mask = inputs.uniform_mask(shape, float(rng.uniform(0.2, 0.5)), rng)
+        prm = dict(beta0=1e-4, rho=1.1, beta_max=1e10, tol=1e-6, max_iter=int(rng.integers(5, 40)))
+        if i % 7 == 3:
+            prm["jacobi_max_sweeps"] = 6
+        jobs.append(dict(shape=shape, prec="fp64" if i % 3 == 0 else "fp32", B=inputs.fortran(T * mask), mask=mask,
+                         prm=prm))
+    alone = [_alone(ctx, j) for j in jobs]
+    with tnn.Server(streams=2, chunk=4, batch_kernels=True) as sv:
+        mixed = _run_server(sv, jobs, device_inputs=True, stagger=0.001)
+        st = sv.stats()
+    assert st["running"] == 0 and st["completed"] == len(jobs)
+    for job, (Xa, ra), (status, Xm, rm, times) in zip(jobs, alone, mixed):
+        assert status in (tnn.OK, tnn.ENOCONV), (job["shape"], status)
+        assert rm["iters"] == ra["iters"], (job["shape"], rm, ra)
+        assert np.array_equal(Xa, Xm), job["shape"]

@@ -396,6 +396,16 @@ void tnn_server_destroy(tnn_server* server);
 tnn_status tnn_profile(tnn_ctx* ctx, int enable);
 tnn_status tnn_profile_read(tnn_ctx* ctx, double ms[TNN_NKERNELS], int64_t launches[TNN_NKERNELS]);
 
+/* Measured peak of a CUDA-core FMA pipe on `device` (no counterpart in the
+ * paper: the roofline denominator of the Jacobi kernels).  kind 0: FP32 FMA,
+ * 1: packed FP32 FMA (fma.rn.f32x2, two per instruction), 2: FP64 FMA.
+ * Runs eight independent FMA chains per thread on eight 256-thread blocks per
+ * SM for a few milliseconds (10 timed launches after 3 warm-ups, CUDA events)
+ * and writes the rate in flop/s (2 per FMA) to *flops_per_s.  Allocates and
+ * frees a small device buffer; synchronises.  TNN_EINVAL for a null pointer
+ * or an unknown kind, TNN_ECUDA on a CUDA error. */
+tnn_status tnn_fma_peak(int32_t device, int32_t kind, double* flops_per_s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -79,6 +79,8 @@ _lib.tnn_admm_iterate.argtypes = [_vp, _vp, _vp, Shape, _ct.POINTER(AdmmParams),
 _lib.tnn_admm_iterate.restype = _st
 _lib.tnn_last_jacobi_stats.argtypes = [_vp, _ct.POINTER(_ct.c_int64)]
 _lib.tnn_last_jacobi_stats.restype = _st
+_lib.tnn_fma_peak.argtypes = [_ct.c_int32, _ct.c_int32, _ct.POINTER(_ct.c_double)]
+_lib.tnn_fma_peak.restype = _st
 _lib.tnn_profile.argtypes = [_vp, _ct.c_int]
 _lib.tnn_profile.restype = _st
 _lib.tnn_profile_read.argtypes = [_vp, _ct.POINTER(_ct.c_double), _ct.POINTER(_ct.c_int64)]
@@ -166,13 +168,25 @@ EXPORTS = ["tnn_create", "tnn_destroy", "tnn_status_string", "tnn_last_error", "
            "tnn_server_create", "tnn_server_submit", "tnn_server_step", "tnn_server_job_state", "tnn_server_take",
            "tnn_server_stats", "tnn_server_destroy", "tsvt_dft", "tsvt_dct_plain", "tnn_admm_batch_create",
            "tnn_admm_batch_reset", "tnn_admm_batch_step", "tnn_admm_batch_sync", "tnn_admm_batch_run",
-           "tnn_admm_batch_report", "tnn_admm_batch_destroy"]
+           "tnn_admm_batch_report", "tnn_admm_batch_destroy", "tnn_fma_peak"]
 
 
 class TnnError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__("%s: %s" % (_lib.tnn_status_string(status).decode(), msg))
         self.status = status
+
+
+FMA_KINDS = {"fp32": 0, "fp32x2": 1, "fp64": 2}
+
+
+def fma_peak(kind="fp32", device=0):
+    """Measured FMA-pipe rate of the device in flop/s (tnn_fma_peak)."""
+    out = _ct.c_double(0.0)
+    st = _lib.tnn_fma_peak(int(device), FMA_KINDS[kind], _ct.byref(out))
+    if st != OK:
+        raise TnnError(st, "tnn_fma_peak")
+    return out.value
 
 
 def status_string(s):

@@ -378,9 +378,7 @@ __device__ __forceinline__ void cross_round(Regs<T, K, R, WITHV>& S, Slot<T>& st
 #pragma unroll
         for (int q = 0; q < K; ++q) {
             const unsigned sq = ((1u << G) - 1u) << (q * G);   // slot q's lanes in a group
-            unsigned wq = 0u;                                   // ... in every group of the warp
-#pragma unroll
-            for (int g = 0; g < 32 / L; ++g) wq |= sq << (g * L);
+            const unsigned wq = (L == 32) ? sq : (sq | (sq << 16));
             if ((bi & wq) != 0u) {
                 T acc = T(0);
 #pragma unroll

@@ -54,8 +54,15 @@ template <> struct Num<double> {
     static __device__ __forceinline__ double fold() { return 6.223015277861142e-61; }    // 2^-200
 };
 
-// IEEE round-to-nearest reciprocal (intrinsic form).
-__device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+// Reciprocal: the hardware's approximate FP32 reciprocal (rcp.approx.f32,
+// subnormals kept), within about one unit in the last place; FP64 is the IEEE
+// round-to-nearest intrinsic.
+__device__ __forceinline__ float rcp(float x)
+{
+    float y;
+    asm("rcp.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 __device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
 
 // Lane layout.  A block pair is owned by a group of L lanes (L = 16: two

@@ -65,6 +65,21 @@ __device__ __forceinline__ float rcp(float x)
 }
 __device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
 
+// sum_q x[q] y[q] over a lane's R rows as two FMA chains (even and odd rows)
+// added at the end: half the dependent chain of one accumulator.
+template <typename T, int R>
+__device__ __forceinline__ T dot_rows(const T (&x)[R], const T (&y)[R])
+{
+    T e = T(0), o = T(0);
+#pragma unroll
+    for (int q = 0; q + 1 < R; q += 2) {
+        e = fma(x[q], y[q], e);
+        o = fma(x[q + 1], y[q + 1], o);
+    }
+    if (R % 2) e = fma(x[R - 1], y[R - 1], e);
+    return e + o;
+}
+
 // Lane layout.  A block pair is owned by a group of L lanes (L = 16: two
 // groups per warp; L = 32: one).  Register q of group lane hl holds row
 //   ((q / VN) * L + hl) * VN + q % VN,
@@ -220,10 +235,7 @@ __device__ __forceinline__ void do_round(Regs<T, K, R, WITHV>& S, const T tol, c
 #pragma unroll
     for (int p = 0; p < K; ++p) {
         const int i = pair_i<CROSS>(K, r, p), j = pair_j<CROSS>(K, r, p);
-        T acc = T(0);
-#pragma unroll
-        for (int q = 0; q < R; ++q) acc = fma(S.a[i][q], S.a[j][q], acc);
-        g[p] = acc;
+        g[p] = dot_rows<T, R>(S.a[i], S.a[j]);
     }
     const T gs = reduce_scatter<T, K, L>(g, hl);
     // this slot's pair state
@@ -321,10 +333,7 @@ __device__ __forceinline__ void cross_round(Regs<T, K, R, WITHV>& S, Slot<T>& st
 #pragma unroll
     for (int p = 0; p < K; ++p) {
         const int j = K + (p + r) % K;
-        T acc = T(0);
-#pragma unroll
-        for (int q = 0; q < R; ++q) acc = fma(S.a[p][q], S.a[j][q], acc);
-        g[p] = acc;
+        g[p] = dot_rows<T, R>(S.a[p], S.a[j]);
     }
     const T gs = reduce_scatter<T, K, L>(g, hl);
     const T gam = (st.dI * st.dJ) * gs;
@@ -430,9 +439,12 @@ template <typename T, int K, int R, int L, bool WITHV>
 // (dscJ): the same array for a slice held by one CTA; for a slice spread over
 // a cluster, each base is the owning CTA's array (offset so that global
 // column indices address it).
+// With anorm set, the slot's squared norms are the ones carried from the
+// previous step (anorm[c] = d_c^2 |s_c|^2, written by store_cols); without
+// it they are recomputed from the loaded columns.
 __device__ __forceinline__ void load_cols(Regs<T, K, R, WITHV>& S, Slot<T>& st, const T* AwI, const T* AwJ,
                                           const T* Vw, const T* dscI, const T* dscJ, int ldA, int bI, int bJ,
-                                          int hl, bool active)
+                                          int hl, bool active, const T* anorm = nullptr)
 {
     constexpr int VN = VecOf<T, R>::N;
     constexpr int G = L / K;
@@ -463,6 +475,11 @@ __device__ __forceinline__ void load_cols(Regs<T, K, R, WITHV>& S, Slot<T>& st, 
     const int cI = bI * K + slot, cJ = bJ * K + slot;
     st.dI = dscI[cI];
     st.dJ = dscJ[cJ];
+    if (anorm) {
+        st.aI = active ? anorm[cI] : T(-1);
+        st.aJ = active ? anorm[cJ] : T(-1);
+        return;
+    }
     // fresh squared norms of the 2K columns, ordered (I_0, J_0, I_1, J_1, ...)
     // so that the reduce-scatter leaves I_p and J_p in the two halves of slot p
     T nv[2 * K];
@@ -522,7 +539,8 @@ __device__ __forceinline__ void scatter_state(const Regs<T, K, R, WITHV>& S, Slo
 // Write the columns and the slot state back; fold tiny scales into the data.
 template <typename T, int K, int R, int L, bool WITHV>
 __device__ __forceinline__ void store_cols(Regs<T, K, R, WITHV>& S, Slot<T>& st, T* AwI, T* AwJ, T* Vw, T* dscI,
-                                           T* dscJ, int ldA, int bI, int bJ, int hl, bool active)
+                                           T* dscJ, int ldA, int bI, int bJ, int hl, bool active,
+                                           T* anorm = nullptr)
 {
     constexpr int VN = VecOf<T, R>::N;
     constexpr int G = L / K;
@@ -577,6 +595,10 @@ __device__ __forceinline__ void store_cols(Regs<T, K, R, WITHV>& S, Slot<T>& st,
     if (hl % G == 0) {
         dscI[bI * K + slot] = st.dI;
         dscJ[bJ * K + slot] = st.dJ;
+        if (anorm) {
+            anorm[bI * K + slot] = st.aI;
+            anorm[bJ * K + slot] = st.aJ;
+        }
     }
 }
 
@@ -654,7 +676,7 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
     T* dsc = reinterpret_cast<T*>(rest);
     T* sig = dsc + npad;
     T* cf = sig + npad;
-    T* anorm = cf + npad;  // carried squared norms d^2 |s|^2
+    T* anorm = cf + npad;  // squared norms d^2 |s|^2 carried from step to step within a sweep
     int* kidx = reinterpret_cast<int*>(anorm + npad);
     int* rank = kidx + npad;
     T* gbuf = reinterpret_cast<T*>(rank + npad);
@@ -719,14 +741,16 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
                 Regs<T, K, R, WITHV> Sr;
                 Slot<T> st;
                 const Counters cnt0 = cnt;
-                load_cols<T, K, R, L, WITHV>(Sr, st, Aw, Aw, Vw, dsc, dsc, ldA, bI, bJ, hl, active);
+                // squared norms: recomputed at a sweep's first step, carried after it
+                load_cols<T, K, R, L, WITHV>(Sr, st, Aw, Aw, Vw, dsc, dsc, ldA, bI, bJ, hl, active,
+                                             step == 0 ? nullptr : anorm);
                 if (step == 0) {
                     gather_state<T, K, R, L, WITHV>(Sr, st);
                     do_rounds<T, K, R, L, WITHV, false>(Sr, tol, hl, cnt, std::make_integer_sequence<int, K - 1>{});
                     scatter_state<T, K, R, L, WITHV>(Sr, st, hl);
                 }
                 cross_rounds<T, K, R, L, WITHV>(Sr, st, tol, hl, cnt, std::make_integer_sequence<int, K>{});
-                store_cols<T, K, R, L, WITHV>(Sr, st, Aw, Aw, Vw, dsc, dsc, ldA, bI, bJ, hl, active);
+                store_cols<T, K, R, L, WITHV>(Sr, st, Aw, Aw, Vw, dsc, dsc, ldA, bI, bJ, hl, active, anorm);
                 if (!active) cnt = cnt0;  // an inactive group's work is discarded, and so are its counts
             }
             __syncthreads();

@@ -226,8 +226,11 @@ __device__ __forceinline__ void recompute_norm(Regs<T, K, R, WITHV>& S, int c)
 // One round: K disjoint pairs (pair_i(p), pair_j(p)) of the 2K register
 // columns.  Each of the K slots of L/K lanes computes one pair's rotation and
 // the group learns all K of them by shuffles.
+// lm: the group's 2K column flags (bit c: register column c belongs to the
+// sweep's set of small columns); a pair of two flagged columns is left alone.
 template <typename T, int K, int R, int L, bool WITHV, bool CROSS, int r>
-__device__ __forceinline__ void do_round(Regs<T, K, R, WITHV>& S, const T tol, const int hl, Counters& cnt)
+__device__ __forceinline__ void do_round(Regs<T, K, R, WITHV>& S, const T tol, const int hl, Counters& cnt,
+                                         const unsigned lm)
 {
     constexpr int G = L / K;
     const int slot = hl / G;
@@ -241,6 +244,7 @@ __device__ __forceinline__ void do_round(Regs<T, K, R, WITHV>& S, const T tol, c
     // this slot's pair state
     T ai = S.al[pair_i<CROSS>(K, r, 0)], aj = S.al[pair_j<CROSS>(K, r, 0)];
     T di = S.d[pair_i<CROSS>(K, r, 0)], dj = S.d[pair_j<CROSS>(K, r, 0)];
+    unsigned lo = (lm >> pair_i<CROSS>(K, r, 0)) & (lm >> pair_j<CROSS>(K, r, 0)) & 1u;
 #pragma unroll
     for (int p = 1; p < K; ++p) {
         const bool me = slot == p;
@@ -248,10 +252,11 @@ __device__ __forceinline__ void do_round(Regs<T, K, R, WITHV>& S, const T tol, c
         aj = me ? S.al[pair_j<CROSS>(K, r, p)] : aj;
         di = me ? S.d[pair_i<CROSS>(K, r, p)] : di;
         dj = me ? S.d[pair_j<CROSS>(K, r, p)] : dj;
+        lo = me ? ((lm >> pair_i<CROSS>(K, r, p)) & (lm >> pair_j<CROSS>(K, r, p)) & 1u) : lo;
     }
     const T gam = (di * dj) * gs;
     T t1 = T(0), t2 = T(0), cc = T(1), tg = T(0);
-    const T off = fabs(gam) * rsqrt(ai) * rsqrt(aj);
+    const T off = lo ? T(0) : fabs(gam) * rsqrt(ai) * rsqrt(aj);
     const bool bigp = off > T(2) * tol;
     // false for a zero column (0 * inf = NaN) and for a carried norm gone negative
     if (off > tol) {
@@ -325,7 +330,7 @@ struct Slot {
 // (t1, t2) by shuffles.
 template <typename T, int K, int R, int L, bool WITHV, int r>
 __device__ __forceinline__ void cross_round(Regs<T, K, R, WITHV>& S, Slot<T>& st, const T tol, const int hl,
-                                            Counters& cnt)
+                                            Counters& cnt, const unsigned lm)
 {
     constexpr int G = L / K;
     const int slot = hl / G;
@@ -339,7 +344,8 @@ __device__ __forceinline__ void cross_round(Regs<T, K, R, WITHV>& S, Slot<T>& st
     const T gam = (st.dI * st.dJ) * gs;
     T t1 = T(0), t2 = T(0);
     bool needI = false, needJ = false;
-    const T off = fabs(gam) * rsqrt(st.aI) * rsqrt(st.aJ);
+    const unsigned lo = (lm >> slot) & (lm >> (K + (slot + r) % K)) & 1u;
+    const T off = lo ? T(0) : fabs(gam) * rsqrt(st.aI) * rsqrt(st.aJ);
     if (off > T(2) * tol && hl % G == 0) ++cnt.big;
     // false for a zero column (0 * inf = NaN) and for a carried norm gone negative
     if (off > tol) {
@@ -420,16 +426,16 @@ __device__ __forceinline__ void cross_round(Regs<T, K, R, WITHV>& S, Slot<T>& st
 
 template <typename T, int K, int R, int L, bool WITHV, int... Rs>
 __device__ __forceinline__ void cross_rounds(Regs<T, K, R, WITHV>& S, Slot<T>& st, const T tol, const int hl,
-                                             Counters& cnt, std::integer_sequence<int, Rs...>)
+                                             Counters& cnt, std::integer_sequence<int, Rs...>, const unsigned lm = 0u)
 {
-    (cross_round<T, K, R, L, WITHV, Rs>(S, st, tol, hl, cnt), ...);
+    (cross_round<T, K, R, L, WITHV, Rs>(S, st, tol, hl, cnt, lm), ...);
 }
 
 template <typename T, int K, int R, int L, bool WITHV, bool CROSS, int... Rs>
 __device__ __forceinline__ void do_rounds(Regs<T, K, R, WITHV>& S, const T tol, const int hl, Counters& cnt,
-                                          std::integer_sequence<int, Rs...>)
+                                          std::integer_sequence<int, Rs...>, const unsigned lm = 0u)
 {
-    (do_round<T, K, R, L, WITHV, CROSS, Rs>(S, tol, hl, cnt), ...);
+    (do_round<T, K, R, L, WITHV, CROSS, Rs>(S, tol, hl, cnt, lm), ...);
 }
 
 // Load the 2K columns of blocks bI, bJ into the group's registers and the
@@ -680,8 +686,8 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
     int* kidx = reinterpret_cast<int*>(anorm + npad);
     int* rank = kidx + npad;
     T* gbuf = reinterpret_cast<T*>(rank + npad);
-    __shared__ int s_rot, s_keep, s_nonfinite;
-    __shared__ double s_nuc, s_fro;
+    __shared__ int s_rot, s_keep, s_nonfinite, s_nlo;
+    __shared__ double s_nuc, s_fro, s_lo;
     __shared__ unsigned long long s_pairs, s_rots;
 
     T* src = item ? static_cast<T*>(item->data) : a.data + (size_t)slice * n1 * n2;
@@ -722,45 +728,121 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
     }
 
     // ---- sweeps
+    //
+    // SVT: columns whose squared norms sum to at most tau^2 need no rotation
+    // among themselves.  If, at the end, every pair involving another column
+    // has converged, the slice is S_H V_H^T + S_Lo V_Lo^T with S_H's columns
+    // orthogonal to each other and to S_Lo's, so its SVT is that of the
+    // first term plus that of the second, and the second is zero because
+    // ||S_Lo||_2 <= ||S_Lo||_F <= tau; the rebuild below keeps only columns
+    // with sigma > tau, none of them in S_Lo.  Each sweep flags the columns
+    // with alpha < tau^2 / 4 (from the carried squared norms) and, if their
+    // alphas sum to at most 0.9 tau^2, leaves pairs of two flagged columns
+    // alone (when at least half of the columns are flagged).  A sweep without
+    // rotation ends the iteration only if the flagged
+    // columns' alphas still sum below tau^2 (a rotation with a column that
+    // has shrunk below them can grow them); otherwise full sweeps follow.
     const T tol = sqrt((T)m) * Num<T>::unit();
     Counters cnt{0, 0, 0};
     int sweeps = 0, converged = skip ? 1 : 0;
     const int max_sweeps = a.max_sweeps > 0 ? a.max_sweeps : 30;
     const int npairs = nb / 2;
-    while (!skip && sweeps < max_sweeps) {
-        if (tid == 0) s_rot = 0;
-        __syncthreads();
-        const int big0 = cnt.big;
-        for (int step = 0; step < nb - 1; ++step) {
-            // iterations are warp-uniform: a group without a block pair works on block 0 with zero norms
-            for (int base = warp * GPW; base < npairs; base += NG) {
-                const int pr = base + lane / L;
-                const bool active = pr < npairs;
-                const int bI = active ? block_at(nb, pr, step) : 0;
-                const int bJ = active ? block_at(nb, nb - 1 - pr, step) : 0;
-                Regs<T, K, R, WITHV> Sr;
-                Slot<T> st;
-                const Counters cnt0 = cnt;
-                // squared norms: recomputed at a sweep's first step, carried after it
-                load_cols<T, K, R, L, WITHV>(Sr, st, Aw, Aw, Vw, dsc, dsc, ldA, bI, bJ, hl, active,
-                                             step == 0 ? nullptr : anorm);
-                if (step == 0) {
-                    gather_state<T, K, R, L, WITHV>(Sr, st);
-                    do_rounds<T, K, R, L, WITHV, false>(Sr, tol, hl, cnt, std::make_integer_sequence<int, K - 1>{});
-                    scatter_state<T, K, R, L, WITHV>(Sr, st, hl);
-                }
-                cross_rounds<T, K, R, L, WITHV>(Sr, st, tol, hl, cnt, std::make_integer_sequence<int, K>{});
-                store_cols<T, K, R, L, WITHV>(Sr, st, Aw, Aw, Vw, dsc, dsc, ldA, bI, bJ, hl, active, anorm);
-                if (!active) cnt = cnt0;  // an inactive group's work is discarded, and so are its counts
-            }
-            __syncthreads();
+    const double tau_s = WITHV ? 0.0
+                               : (a.ctl ? 1.0 / a.ctl->beta : (ictl ? 1.0 / ictl->beta : (item ? item->tau : a.tau)));
+    bool full_only = WITHV;
+    int* loflag = kidx;  // free until the rebuild
+    if (!WITHV && !skip) {
+        for (int c = warp; c < npad; c += W) {
+            const T* col = Aw + (size_t)c * ldA;
+            T s2 = T(0);
+            for (int r = lane; r < ldA; r += 32) s2 = fma(col[r], col[r], s2);
+            s2 = group_sum<32>(s2);
+            if (lane == 0) anorm[c] = s2;  // the scales are all 1 here
         }
+    }
+    while (!skip && sweeps < max_sweeps) {
+        if (tid == 0) { s_rot = 0; s_lo = 0.0; s_nlo = 0; }
+        __syncthreads();
+        if (!full_only) {
+            const double thr = 0.25 * tau_s * tau_s;
+            double part = 0.0;
+            int nf = 0;
+            for (int c = tid; c < npad; c += nthr) {
+                const double an = (double)anorm[c];
+                const int f = an < thr ? 1 : 0;
+                loflag[c] = f;
+                part += f ? fabs(an) : 0.0;  // a carried alpha gone negative counts by its size
+                nf += (f && c < n) ? 1 : 0;
+            }
+            part = group_sum<32>(part);
+            nf = group_sum<32>(nf);
+            if (lane == 0) {
+                if (part != 0.0) atomicAdd(&s_lo, part);
+                if (nf) atomicAdd(&s_nlo, nf);
+            }
+        }
+        __syncthreads();
+        // flagged sweeps only where they pay: most columns flagged (a few
+        // tiny columns save nothing and can cost a closing full sweep)
+        const bool partial = !full_only && s_lo <= 0.9 * tau_s * tau_s && 2 * s_nlo >= n;
+        const int big0 = cnt.big;
+        // one sweep; compiled twice, so that a sweep without flagged columns
+        // runs code without the flag tests
+        auto sweep = [&](auto flagged) {
+            constexpr bool FL = decltype(flagged)::value;
+            for (int step = 0; step < nb - 1; ++step) {
+                // iterations are warp-uniform: a group without a block pair works on block 0 with zero norms
+                for (int base = warp * GPW; base < npairs; base += NG) {
+                    const int pr = base + lane / L;
+                    const bool active = pr < npairs;
+                    const int bI = active ? block_at(nb, pr, step) : 0;
+                    const int bJ = active ? block_at(nb, nb - 1 - pr, step) : 0;
+                    Regs<T, K, R, WITHV> Sr;
+                    Slot<T> st;
+                    const Counters cnt0 = cnt;
+                    // squared norms: recomputed at a sweep's first step, carried after it
+                    load_cols<T, K, R, L, WITHV>(Sr, st, Aw, Aw, Vw, dsc, dsc, ldA, bI, bJ, hl, active,
+                                                 step == 0 ? nullptr : anorm);
+                    unsigned lm = 0u;  // flags of the 2K columns (I block: bits 0..K-1, J block: K..2K-1)
+                    if constexpr (FL) {
+#pragma unroll
+                        for (int c = 0; c < K; ++c)
+                            lm |= ((unsigned)loflag[bI * K + c] << c) | ((unsigned)loflag[bJ * K + c] << (K + c));
+                    }
+                    if (step == 0) {
+                        gather_state<T, K, R, L, WITHV>(Sr, st);
+                        do_rounds<T, K, R, L, WITHV, false>(Sr, tol, hl, cnt,
+                                                            std::make_integer_sequence<int, K - 1>{}, lm);
+                        scatter_state<T, K, R, L, WITHV>(Sr, st, hl);
+                    }
+                    cross_rounds<T, K, R, L, WITHV>(Sr, st, tol, hl, cnt, std::make_integer_sequence<int, K>{}, lm);
+                    store_cols<T, K, R, L, WITHV>(Sr, st, Aw, Aw, Vw, dsc, dsc, ldA, bI, bJ, hl, active, anorm);
+                    if (!active) cnt = cnt0;  // an inactive group's work is discarded, and so are its counts
+                }
+                __syncthreads();
+            }
+        };
+        if (!WITHV && partial) sweep(std::true_type{});
+        else sweep(std::false_type{});
         if (cnt.big != big0) atomicAdd(&s_rot, cnt.big - big0);
         __syncthreads();
         const int nrot = s_rot;
         ++sweeps;
+        bool done = nrot == 0;
+        if (done && partial) {
+            // the flagged columns' alphas after the sweep
+            if (tid == 0) s_lo = 0.0;
+            __syncthreads();
+            double part = 0.0;
+            for (int c = tid; c < npad; c += nthr) part += loflag[c] ? fabs((double)anorm[c]) : 0.0;
+            part = group_sum<32>(part);
+            if (lane == 0 && part != 0.0) atomicAdd(&s_lo, part);
+            __syncthreads();
+            done = s_lo <= (1.0 - 1e-3) * tau_s * tau_s;
+            if (!done) full_only = true;
+        }
         __syncthreads();
-        if (nrot == 0) { converged = 1; break; }
+        if (done) { converged = 1; break; }
     }
     if (cnt.pairs) atomicAdd(&s_pairs, (unsigned long long)cnt.pairs);
     if (cnt.rots) atomicAdd(&s_rots, (unsigned long long)cnt.rots);

@@ -255,3 +255,36 @@ def test_tsvt_random_shape_sweep(ctx, prec):
             m, n = max(n1, n2), min(n1, n2)
             bound = max(1e-5, 2.0 * np.sqrt(m * n) * U32) * np.linalg.norm(Z)
             assert np.linalg.norm(Y - ref) <= bound, shape
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("shape", [(120, 96, 2), (80, 130, 2)])
+@pytest.mark.parametrize("f", [0.3, 0.8, 0.95, 1.2, 2.0])
+def test_tsvt_dominant_plus_small_tail(ctx, prec, shape, f):
+    # Each transformed slice is one singular value of 10 tau plus a Gaussian
+    # tail of Frobenius norm f tau: the shape of the DC slice in the early
+    # completion iterations.  Below f = 0.9 the tail's columns can be left
+    # unrotated among themselves (their block's SVT is zero); around and above
+    # it the kernel must fall back to full sweeps.  Either way the result is
+    # the SVT.
+    n1, n2, n3 = shape
+    rng = np.random.default_rng(int(f * 100) + n1)
+    tau = 0.7
+    Zb = np.zeros(shape)
+    for k in range(n3):
+        u = rng.standard_normal(n1)
+        v = rng.standard_normal(n2)
+        N = rng.standard_normal((n1, n2))
+        Zb[:, :, k] = 10 * tau * np.outer(u / np.linalg.norm(u), v / np.linalg.norm(v)) + f * tau * N / np.linalg.norm(N)
+    Z = O.tube_transform(Zb, inverse=True)
+    if prec != "fp64":
+        Z = Z.astype(np.float32).astype(np.float64)
+    Y = _run(ctx, Z, tau, prec)
+    ref = O.tsvt(Z, tau, nthreads=THREADS)
+    err_y = rel_err(Y, ref, Z)
+    err_z = np.linalg.norm(Y - ref) / np.linalg.norm(Z)
+    log_err("tsvt tail %s %s f=%s" % (prec, shape, f), err_y=err_y, err_z=err_z)
+    if prec == "fp64":
+        assert err_y <= TOL["fp64"], err_y
+    else:
+        assert err_z <= TOL["fp32"], (err_z, err_y)

@@ -1,0 +1,67 @@
+"""The property behind the Jacobi SVT's small-column sweeps (Theorem 5's SVT,
+checked against the oracle's matrix SVT).
+
+Let A = S V^T with V orthogonal and S = [S_H | S_Lo], where S_H's columns are
+orthogonal to each other and to every column of S_Lo, and S_Lo's columns are
+not orthogonal to each other.  If ||S_Lo||_F <= tau, then the SVT of A equals
+the rebuild over S_H's columns with sigma > tau, sum (1 - tau/sigma_i)
+/ |s_i|^2 s_i (s_i^T A), whatever S_Lo's inner structure.  If S_Lo carries a
+singular value above tau, the same rebuild is wrong: the block cannot be left
+unrotated."""
+import numpy as np
+import pytest
+
+import oracle as O
+
+
+def _case(rng, m, n, nh, lo_fro, tau):
+    # S_H: nh orthogonal columns with norms spread around tau; S_Lo: the rest,
+    # correlated columns in the orthogonal complement of S_H, Frobenius lo_fro
+    Q, _ = np.linalg.qr(rng.standard_normal((m, m)))
+    sig = tau * np.linspace(0.5, 6.0, nh)
+    SH = Q[:, :nh] * sig
+    base = Q[:, nh:nh + 3] @ rng.standard_normal((3, n - nh))  # rank 3: far from orthogonal
+    base += 1e-3 * Q[:, nh:] @ rng.standard_normal((m - nh, n - nh))
+    SLo = base * (lo_fro / np.linalg.norm(base))
+    S = np.hstack([SH, SLo])
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    return S, V, S @ V.T
+
+
+def _rebuild(S, A, nh, tau):
+    Y = np.zeros_like(A)
+    for i in range(nh):
+        s = S[:, i]
+        n2 = s @ s
+        sg = np.sqrt(n2)
+        if sg > tau:
+            Y += (1.0 - tau / sg) / n2 * np.outer(s, s @ A)
+    return Y
+
+
+@pytest.mark.parametrize("m,n,nh", [(40, 30, 5), (60, 60, 12), (25, 24, 1)])
+@pytest.mark.parametrize("frac", [0.3, 0.9, 0.999])
+def test_small_block_needs_no_rotation(m, n, nh, frac):
+    rng = np.random.default_rng(m * 100 + n + int(frac * 1000))
+    tau = 0.8
+    S, V, A = _case(rng, m, n, nh, frac * tau, tau)
+    # S_Lo is far from orthogonal (the premise of the shortcut)
+    SLo = S[:, nh:]
+    G = SLo.T @ SLo
+    off = np.abs(G - np.diag(np.diag(G))).max() / np.diag(G).max()
+    assert off > 1e-2
+    Y, _ = O.svt_matrix(A, tau)
+    Yb = _rebuild(S, A, nh, tau)
+    assert np.linalg.norm(Yb - Y) <= 1e-12 * np.linalg.norm(A)
+
+
+def test_large_block_must_be_rotated():
+    # S_Lo with Frobenius norm 3 tau on three directions: its top singular
+    # value is above tau, so leaving it out changes the SVT
+    rng = np.random.default_rng(7)
+    tau = 0.8
+    S, V, A = _case(rng, 40, 30, 5, 3.0 * tau, tau)
+    assert np.linalg.svd(S[:, 5:], compute_uv=False)[0] > tau
+    Y, _ = O.svt_matrix(A, tau)
+    Yb = _rebuild(S, A, 5, tau)
+    assert np.linalg.norm(Yb - Y) > 1e-3 * np.linalg.norm(A)

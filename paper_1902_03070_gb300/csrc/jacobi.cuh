@@ -687,7 +687,8 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
     int* rank = kidx + npad;
     T* gbuf = reinterpret_cast<T*>(rank + npad);
     __shared__ int s_rot, s_keep, s_nonfinite, s_nlo;
-    __shared__ double s_nuc, s_fro, s_lo;
+    __shared__ double s_nuc, s_fro, s_lo, s_s1;
+    __shared__ unsigned long long s_maxb;  // bits of a nonnegative double (ordered as integers)
     __shared__ unsigned long long s_pairs, s_rots;
 
     T* src = item ? static_cast<T*>(item->data) : a.data + (size_t)slice * n1 * n2;
@@ -750,6 +751,7 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
     const double tau_s = WITHV ? 0.0
                                : (a.ctl ? 1.0 / a.ctl->beta : (ictl ? 1.0 / ictl->beta : (item ? item->tau : a.tau)));
     bool full_only = WITHV;
+    int cert_left = WITHV ? 0 : 2;  // zero-SVT certificate attempts (below)
     int* loflag = kidx;  // free until the rebuild
     if (!WITHV && !skip) {
         for (int c = warp; c < npad; c += W) {
@@ -840,6 +842,92 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
             __syncthreads();
             done = s_lo <= (1.0 - 1e-3) * tau_s * tau_s;
             if (!done) full_only = true;
+        }
+        // Zero-SVT certificate.  sigma_1^2 is the largest eigenvalue of the
+        // Gram matrix G = S^T S of the current columns (V orthogonal), so by
+        // Gershgorin sigma_1^2 <= max_i sum_j |G_ij|.  A slice whose columns
+        // are all below tau after a sweep (necessary for sigma_1 <= tau) gets
+        // that bound, with the rounding of the computed G (|dG_ij| <= m u
+        // |a_i| |a_j|) and of the row sums added; if it is below tau^2, every
+        // singular value is at most tau, the SVT is zero and the sweeps stop
+        // (the rebuild keeps no column: each column's norm is at most
+        // sigma_1).  Tried after the first two sweeps only.
+        if (!WITHV && !done && cert_left > 0) {
+            --cert_left;
+            if (tid == 0) { s_maxb = 0ull; s_s1 = 0.0; }
+            __syncthreads();
+            double amx = 0.0, s1 = 0.0;
+            for (int c = tid; c < n; c += nthr) {
+                const double an = fmax((double)anorm[c], 0.0);
+                amx = fmax(amx, an);
+                s1 += sqrt(an);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) amx = fmax(amx, __shfl_xor_sync(FULL, amx, o));
+            s1 = group_sum<32>(s1);
+            if (lane == 0) {
+                atomicMax(&s_maxb, (unsigned long long)__double_as_longlong(amx));
+                if (s1 != 0.0) atomicAdd(&s_s1, s1);
+            }
+            __syncthreads();
+            const double amax = __longlong_as_double((long long)s_maxb);
+            const double S1 = 1.01 * s_s1;
+            __syncthreads();
+            if (amax < 0.999 * tau_s * tau_s) {
+                if (tid == 0) s_maxb = 0ull;
+                __syncthreads();
+                constexpr int RG = (R * L + 31) / 32;  // rows per lane (lane-strided; rows past L R are padding)
+                const double uu = (double)Num<T>::unit();
+                double wmax = 0.0;
+                for (int i0 = 2 * warp; i0 < n; i0 += 2 * W) {
+                    const int i1 = i0 + 1 < n ? i0 + 1 : i0;
+                    T x0[RG], x1[RG];
+#pragma unroll
+                    for (int q = 0; q < RG; ++q) {
+                        const int r = q * 32 + lane;
+                        x0[q] = r < ldA ? Aw[(size_t)i0 * ldA + r] : T(0);
+                        x1[q] = r < ldA ? Aw[(size_t)i1 * ldA + r] : T(0);
+                    }
+                    T r0 = T(0), r1 = T(0);
+                    for (int j0 = 0; j0 < n; j0 += 32) {
+                        T p0[32], p1[32];
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj) {
+                            p0[jj] = T(0);
+                            p1[jj] = T(0);
+                            const int j = j0 + jj;
+                            if (j < n) {
+                                const T* col = Aw + (size_t)j * ldA;
+#pragma unroll
+                                for (int q = 0; q < RG; ++q) {
+                                    const int r = q * 32 + lane;
+                                    const T v = r < ldA ? col[r] : T(0);
+                                    p0[jj] = fma(x0[q], v, p0[jj]);
+                                    p1[jj] = fma(x1[q], v, p1[jj]);
+                                }
+                            }
+                        }
+                        const T g0 = reduce_scatter<T, 32, 32>(p0, lane);  // lane: G(i, j0 + lane) / scales
+                        const T g1 = reduce_scatter<T, 32, 32>(p1, lane);
+                        const int j = j0 + lane;
+                        if (j < n) {
+                            const T dj = dsc[j];
+                            r0 += fabs(g0 * dj);
+                            r1 += fabs(g1 * dj);
+                        }
+                    }
+                    r0 = group_sum<32>(r0);
+                    r1 = group_sum<32>(r1);
+                    const double b0 = (double)(r0 * dsc[i0]) * (1.0 + 2.0 * n * uu) +
+                                      2.0 * m * uu * sqrt(fmax((double)anorm[i0], 0.0)) * S1;
+                    const double b1 = (double)(r1 * dsc[i1]) * (1.0 + 2.0 * n * uu) +
+                                      2.0 * m * uu * sqrt(fmax((double)anorm[i1], 0.0)) * S1;
+                    wmax = fmax(wmax, fmax(b0, b1));
+                }
+                if (lane == 0) atomicMax(&s_maxb, (unsigned long long)__double_as_longlong(wmax));
+                __syncthreads();
+                done = __longlong_as_double((long long)s_maxb) <= (1.0 - 1e-4) * tau_s * tau_s;
+            }
         }
         __syncthreads();
         if (done) { converged = 1; break; }

@@ -288,3 +288,34 @@ def test_tsvt_dominant_plus_small_tail(ctx, prec, shape, f):
         assert err_y <= TOL["fp64"], err_y
     else:
         assert err_z <= TOL["fp32"], (err_z, err_y)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("shape", [(176, 144, 2), (60, 90, 3)])
+@pytest.mark.parametrize("s1", [0.3, 0.7, 0.97, 1.03, 1.3])
+def test_tsvt_top_singular_value_near_tau(ctx, prec, shape, s1):
+    # Transformed slices with Frobenius norm above tau (so the slice is not
+    # skipped) and largest singular value s1 tau spread over all columns:
+    # below tau the SVT is zero (the kernel may stop early on a Gershgorin
+    # bound); just above it, that bound must not fire.
+    n1, n2, n3 = shape
+    rng = np.random.default_rng(int(s1 * 1000) + n1 + n3)
+    tau = 0.5
+    r = min(n1, n2)
+    Zb = np.zeros(shape)
+    for k in range(n3):
+        U, _ = np.linalg.qr(rng.standard_normal((n1, r)))
+        V, _ = np.linalg.qr(rng.standard_normal((n2, r)))
+        sig = s1 * tau * np.linspace(1.0, 0.2, r)  # ||.||_F well above tau
+        Zb[:, :, k] = (U * sig) @ V.T
+    Z = O.tube_transform(Zb, inverse=True)
+    if prec != "fp64":
+        Z = Z.astype(np.float32).astype(np.float64)
+    Y = _run(ctx, Z, tau, prec)
+    ref = O.tsvt(Z, tau, nthreads=THREADS)
+    err_z = np.linalg.norm(Y - ref) / np.linalg.norm(Z)
+    log_err("tsvt near-tau %s %s s1=%s" % (prec, shape, s1), err_z=err_z)
+    if s1 < 1.0:
+        assert np.count_nonzero(ref) == 0 or np.abs(ref).max() == 0.0
+        assert np.abs(Y).max() == 0.0
+    assert err_z <= (TOL["fp64"] if prec == "fp64" else TOL["fp32"]), err_z

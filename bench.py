@@ -44,7 +44,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one Jacobi SVT launch on this workload, from
 # an ncu capture of the current kernel (dram__bytes.sum.per_second x
 # gpu__time_duration); the slices stay in L2 between the transforms.
-JACOBI_TRAFFIC_BYTES = 10.44e6
+JACOBI_TRAFFIC_BYTES = 10.45e6
 
 
 def parse():

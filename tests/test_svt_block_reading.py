@@ -7,7 +7,12 @@ not orthogonal to each other.  If ||S_Lo||_F <= tau, then the SVT of A equals
 the rebuild over S_H's columns with sigma > tau, sum (1 - tau/sigma_i)
 / |s_i|^2 s_i (s_i^T A), whatever S_Lo's inner structure.  If S_Lo carries a
 singular value above tau, the same rebuild is wrong: the block cannot be left
-unrotated."""
+unrotated.
+
+And the zero-SVT certificate: when the Gershgorin bound on S^T S, computed in
+FP32 with the kernel's rounding margins, is below tau^2, the oracle's SVT is
+exactly zero; the bound never fires for a slice whose top singular value is
+above tau."""
 import numpy as np
 import pytest
 
@@ -65,3 +70,41 @@ def test_large_block_must_be_rotated():
     Y, _ = O.svt_matrix(A, tau)
     Yb = _rebuild(S, A, 5, tau)
     assert np.linalg.norm(Yb - Y) > 1e-3 * np.linalg.norm(A)
+
+
+def _gershgorin_fp32(S, tau):
+    # the kernel's certificate, in FP32 like the FP32 kernel: row sums of
+    # |S^T S| plus the rounding margins (m u |a_i| sum_j |a_j|, 2 n u)
+    S32 = S.astype(np.float32)
+    G = S32.T @ S32
+    m, n = S.shape
+    u = 2.0 ** -24
+    nrm = np.linalg.norm(S, axis=0)
+    rows = np.abs(G).astype(np.float64).sum(1) * (1 + 2 * n * u) + 2 * m * u * nrm * 1.01 * nrm.sum()
+    return rows.max() <= (1 - 1e-4) * tau * tau
+
+
+@pytest.mark.parametrize("s1", [0.2, 0.6, 0.9, 0.99, 1.01, 1.2])
+@pytest.mark.parametrize("ortho", [0.0, 1e-4, 1e-2])
+def test_zero_svt_certificate(s1, ortho):
+    # S = U diag(sigma) W with W close to orthogonal (columns nearly
+    # orthogonal after a Jacobi sweep or two); A = S V^T.  Where the bound
+    # certifies, the oracle's SVT is exactly zero; it never certifies a slice
+    # whose top singular value is above tau.
+    rng = np.random.default_rng(int(s1 * 100) + int(ortho * 1e5))
+    m, n, tau = 50, 40, 0.6
+    U, _ = np.linalg.qr(rng.standard_normal((m, n)))
+    sig = s1 * tau * np.linspace(1.0, 0.1, n)
+    W = np.eye(n) + ortho * rng.standard_normal((n, n))
+    S = (U * sig) @ W
+    S *= s1 * tau / np.linalg.svd(S, compute_uv=False)[0]  # top singular value exactly s1 tau
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = S @ V.T
+    cert = _gershgorin_fp32(S, tau)
+    Y, _ = O.svt_matrix(A, tau)
+    if cert:
+        assert np.abs(Y).max() == 0.0
+    if s1 > 1.0:
+        assert not cert
+    if s1 <= 0.9 and ortho <= 1e-4:
+        assert cert  # nearly orthogonal columns well below tau: the bound is tight enough

@@ -396,6 +396,17 @@ void tnn_server_destroy(tnn_server* server);
 tnn_status tnn_profile(tnn_ctx* ctx, int enable);
 tnn_status tnn_profile_read(tnn_ctx* ctx, double ms[TNN_NKERNELS], int64_t launches[TNN_NKERNELS]);
 
+/* Host only (no device needed): the Jacobi SVT launch the library plans for
+ * the slices of a tensor of this shape and precision (one-sided Jacobi,
+ * Algorithm 1's per-slice SVD).  out = {L lanes per column-block pair, R rows
+ * per lane, K columns per block, nb column blocks (after padding), W warps per
+ * CTA, 1 if a slice's working copy is in shared memory, cluster size (1: one
+ * CTA per slice; > 1: each slice spread over a thread-block cluster), dynamic
+ * shared memory bytes per CTA, global scratch bytes for the tensor}.  Honours
+ * the same tuning overrides as the launches.  TNN_EINVAL for a null out, an
+ * unknown precision, a non-positive extent or max(n1, n2) > 512. */
+tnn_status tnn_jacobi_plan_info(tnn_shape shape, tnn_precision prec, int64_t out[9]);
+
 /* Measured peak of a CUDA-core FMA pipe on `device` (no counterpart in the
  * paper: the roofline denominator of the Jacobi kernels).  kind 0: FP32 FMA,
  * 1: packed FP32 FMA (fma.rn.f32x2, two per instruction), 2: FP64 FMA.

@@ -156,3 +156,22 @@ bool jacobi_plan(int64_t n1, int64_t n2, int64_t n3, int elem, JacobiPlan* plan)
 }
 
 }  // namespace tnn
+
+extern "C" tnn_status tnn_jacobi_plan_info(tnn_shape shape, tnn_precision prec, int64_t out[9])
+{
+    if (!out) return TNN_EINVAL;
+    if (!(prec == TNN_FP64 || prec == TNN_FP32 || prec == TNN_FP32_TF32X3 || prec == TNN_FP32_BF16SPLIT))
+        return TNN_EINVAL;
+    tnn::JacobiPlan p;
+    if (!tnn::jacobi_plan(shape.n1, shape.n2, shape.n3, prec == TNN_FP64 ? 8 : 4, &p)) return TNN_EINVAL;
+    out[0] = p.L;
+    out[1] = p.RA;
+    out[2] = p.K;
+    out[3] = p.nb;
+    out[4] = p.W;
+    out[5] = p.in_smem;
+    out[6] = p.cluster > 1 ? p.cluster : 1;
+    out[7] = (int64_t)p.smem_bytes;
+    out[8] = (int64_t)p.work_bytes;
+    return TNN_OK;
+}

@@ -81,6 +81,8 @@ _lib.tnn_last_jacobi_stats.argtypes = [_vp, _ct.POINTER(_ct.c_int64)]
 _lib.tnn_last_jacobi_stats.restype = _st
 _lib.tnn_fma_peak.argtypes = [_ct.c_int32, _ct.c_int32, _ct.POINTER(_ct.c_double)]
 _lib.tnn_fma_peak.restype = _st
+_lib.tnn_jacobi_plan_info.argtypes = [Shape, _ct.c_int, _ct.POINTER(_ct.c_int64)]
+_lib.tnn_jacobi_plan_info.restype = _st
 _lib.tnn_profile.argtypes = [_vp, _ct.c_int]
 _lib.tnn_profile.restype = _st
 _lib.tnn_profile_read.argtypes = [_vp, _ct.POINTER(_ct.c_double), _ct.POINTER(_ct.c_int64)]
@@ -168,7 +170,7 @@ EXPORTS = ["tnn_create", "tnn_destroy", "tnn_status_string", "tnn_last_error", "
            "tnn_server_create", "tnn_server_submit", "tnn_server_step", "tnn_server_job_state", "tnn_server_take",
            "tnn_server_stats", "tnn_server_destroy", "tsvt_dft", "tsvt_dct_plain", "tnn_admm_batch_create",
            "tnn_admm_batch_reset", "tnn_admm_batch_step", "tnn_admm_batch_sync", "tnn_admm_batch_run",
-           "tnn_admm_batch_report", "tnn_admm_batch_destroy", "tnn_fma_peak"]
+           "tnn_admm_batch_report", "tnn_admm_batch_destroy", "tnn_fma_peak", "tnn_jacobi_plan_info"]
 
 
 class TnnError(RuntimeError):
@@ -178,6 +180,17 @@ class TnnError(RuntimeError):
 
 
 FMA_KINDS = {"fp32": 0, "fp32x2": 1, "fp64": 2}
+
+
+def jacobi_plan_info(shape, prec="fp32"):
+    """The Jacobi SVT launch planned for slices of `shape` (host only;
+    tnn_jacobi_plan_info)."""
+    out = (_ct.c_int64 * 9)()
+    st = _lib.tnn_jacobi_plan_info(Shape(*shape), PRECISIONS[prec], out)
+    if st != OK:
+        raise TnnError(st, "tnn_jacobi_plan_info")
+    keys = ["L", "R", "K", "nb", "W", "in_smem", "cluster", "smem_bytes", "work_bytes"]
+    return dict(zip(keys, list(out)))
 
 
 def fma_peak(kind="fp32", device=0):

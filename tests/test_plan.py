@@ -1,0 +1,68 @@
+"""The Jacobi launch planner on the host (tnn_jacobi_plan_info, no device):
+every plan covers its slice (rows L R >= m, columns nb K >= n, an even block
+count), fits the CTA limits (at most 1024 threads, 227 KB of shared memory),
+sends only large slices to thread-block clusters, and the limits and
+invalid arguments are refused."""
+import numpy as np
+import pytest
+
+SMEM_MAX = 227 * 1024
+
+
+@pytest.fixture(scope="module")
+def tnn():
+    from paper_1902_03070_gb300 import tnn as t
+    return t
+
+
+def _check(plan, n1, n2, prec):
+    m, n = max(n1, n2), min(n1, n2)
+    elem = 8 if prec == "fp64" else 4
+    L, R, K, nb, W = plan["L"], plan["R"], plan["K"], plan["nb"], plan["W"]
+    C = plan["cluster"]
+    assert L in (8, 16, 32) and L * R >= m
+    assert nb % 2 == 0 and nb * K >= n
+    assert 1 <= W <= 32
+    assert plan["smem_bytes"] <= SMEM_MAX
+    if C > 1:
+        assert C in (2, 4, 8, 16) and nb % (4 * C) == 0 and plan["in_smem"] == 1
+        # only slices whose working copy is large go to clusters (one CTA holds
+        # a copy of up to about 200 KB next to its other shared arrays)
+        assert (L * R + (2 if elem == 4 else 1)) * n * elem > 100 * 1024
+    if plan["in_smem"]:
+        assert plan["work_bytes"] == 0
+    else:
+        assert plan["work_bytes"] > 0
+
+
+def test_workload_plans(tnn):
+    p = tnn.jacobi_plan_info((144, 176, 100), "fp32")
+    _check(p, 144, 176, "fp32")
+    assert p["cluster"] == 1 and p["in_smem"] == 1 and (p["L"], p["R"], p["K"]) == (16, 12, 4)
+    p = tnn.jacobi_plan_info((512, 512, 31), "bf16split")
+    _check(p, 512, 512, "bf16split")
+    assert p["cluster"] >= 2
+    p = tnn.jacobi_plan_info((48, 48, 16), "fp64")
+    _check(p, 48, 48, "fp64")
+    assert p["in_smem"] == 1 and p["cluster"] == 1
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_random_shapes(tnn, prec):
+    rng = np.random.default_rng(5 if prec == "fp32" else 6)
+    for _ in range(300):
+        n1, n2 = (int(x) for x in rng.integers(1, 513, size=2))
+        n3 = int(rng.integers(1, 65))
+        p = tnn.jacobi_plan_info((n1, n2, n3), prec)
+        _check(p, n1, n2, prec)
+        assert tnn.jacobi_plan_info((n2, n1, n3), prec) == p  # orientation does not change the plan
+
+
+def test_limits_refused(tnn):
+    for shape in ((513, 10, 2), (10, 513, 2), (0, 5, 5), (5, 0, 5), (5, 5, 0), (-1, 4, 4)):
+        with pytest.raises(tnn.TnnError):
+            tnn.jacobi_plan_info(shape, "fp32")
+    import ctypes
+    out = (ctypes.c_int64 * 9)()
+    assert tnn._lib.tnn_jacobi_plan_info(tnn.Shape(4, 4, 4), 7, out) == tnn.EINVAL
+    assert tnn._lib.tnn_jacobi_plan_info(tnn.Shape(4, 4, 4), 1, None) == tnn.EINVAL

@@ -359,6 +359,12 @@ typedef struct {
 } tnn_server_params;
 typedef struct tnn_server tnn_server;
 tnn_status tnn_server_create(const tnn_server_params* params, tnn_server** server);
+/* Host only: the device bytes a job of this shape and precision holds while
+ * admitted (B, mask, X, M, the transformed tensor, partial sums, Jacobi
+ * statistics and scratch, control block; each 256-byte aligned), the figure
+ * admission compares with hbm_cap_bytes.  TNN_EINVAL for a null pointer, an
+ * unknown precision, a non-positive extent or slices too large to plan. */
+tnn_status tnn_server_footprint(tnn_shape shape, tnn_precision prec, uint64_t* bytes);
 /* B (FP64 for TNN_FP64, else FP32) and mask (uint8, 1 = observed): pageable
  * host memory is copied at submission (into pinned memory the job owns);
  * pinned host or device memory is read at admission and must stay valid and

@@ -426,6 +426,19 @@ void batch_pass(tnn_server* sv, BatchLane& b, int* nfin)
 
 extern "C" {
 
+tnn_status tnn_server_footprint(tnn_shape sh, tnn_precision prec, uint64_t* bytes)
+{
+    if (!bytes) return TNN_EINVAL;
+    *bytes = 0;
+    if (sh.n1 <= 0 || sh.n2 <= 0 || sh.n3 <= 0) return TNN_EINVAL;
+    if (!(prec == TNN_FP64 || prec == TNN_FP32 || prec == TNN_FP32_TF32X3 || prec == TNN_FP32_BF16SPLIT))
+        return TNN_EINVAL;
+    const size_t fp = footprint(sh, prec);
+    if (fp == 0) return TNN_EINVAL;
+    *bytes = fp;
+    return TNN_OK;
+}
+
 tnn_status tnn_server_create(const tnn_server_params* p, tnn_server** out)
 {
     if (!out) return TNN_EINVAL;

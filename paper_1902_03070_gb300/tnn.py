@@ -83,6 +83,8 @@ _lib.tnn_fma_peak.argtypes = [_ct.c_int32, _ct.c_int32, _ct.POINTER(_ct.c_double
 _lib.tnn_fma_peak.restype = _st
 _lib.tnn_jacobi_plan_info.argtypes = [Shape, _ct.c_int, _ct.POINTER(_ct.c_int64)]
 _lib.tnn_jacobi_plan_info.restype = _st
+_lib.tnn_server_footprint.argtypes = [Shape, _ct.c_int, _ct.POINTER(_ct.c_uint64)]
+_lib.tnn_server_footprint.restype = _st
 _lib.tnn_profile.argtypes = [_vp, _ct.c_int]
 _lib.tnn_profile.restype = _st
 _lib.tnn_profile_read.argtypes = [_vp, _ct.POINTER(_ct.c_double), _ct.POINTER(_ct.c_int64)]
@@ -170,7 +172,8 @@ EXPORTS = ["tnn_create", "tnn_destroy", "tnn_status_string", "tnn_last_error", "
            "tnn_server_create", "tnn_server_submit", "tnn_server_step", "tnn_server_job_state", "tnn_server_take",
            "tnn_server_stats", "tnn_server_destroy", "tsvt_dft", "tsvt_dct_plain", "tnn_admm_batch_create",
            "tnn_admm_batch_reset", "tnn_admm_batch_step", "tnn_admm_batch_sync", "tnn_admm_batch_run",
-           "tnn_admm_batch_report", "tnn_admm_batch_destroy", "tnn_fma_peak", "tnn_jacobi_plan_info"]
+           "tnn_admm_batch_report", "tnn_admm_batch_destroy", "tnn_fma_peak", "tnn_jacobi_plan_info",
+           "tnn_server_footprint"]
 
 
 class TnnError(RuntimeError):
@@ -191,6 +194,16 @@ def jacobi_plan_info(shape, prec="fp32"):
         raise TnnError(st, "tnn_jacobi_plan_info")
     keys = ["L", "R", "K", "nb", "W", "in_smem", "cluster", "smem_bytes", "work_bytes"]
     return dict(zip(keys, list(out)))
+
+
+def server_footprint(shape, prec="fp32"):
+    """Device bytes a completion job of `shape` holds in the server (host
+    only; tnn_server_footprint)."""
+    out = _ct.c_uint64(0)
+    st = _lib.tnn_server_footprint(Shape(*shape), PRECISIONS[prec], _ct.byref(out))
+    if st != OK:
+        raise TnnError(st, "tnn_server_footprint")
+    return out.value
 
 
 def fma_peak(kind="fp32", device=0):

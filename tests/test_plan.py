@@ -66,3 +66,20 @@ def test_limits_refused(tnn):
     out = (ctypes.c_int64 * 9)()
     assert tnn._lib.tnn_jacobi_plan_info(tnn.Shape(4, 4, 4), 7, out) == tnn.EINVAL
     assert tnn._lib.tnn_jacobi_plan_info(tnn.Shape(4, 4, 4), 1, None) == tnn.EINVAL
+
+
+def test_server_footprint(tnn):
+    # B, X, M and the transformed tensor (elem bytes each) plus the mask, at
+    # least; the Jacobi scratch only when the slices are not in shared memory
+    for shape, prec in (((144, 176, 100), "tf32x3"), ((48, 48, 16), "fp64"), ((512, 512, 31), "bf16split"),
+                        ((300, 20, 7), "fp32")):
+        N = int(np.prod(shape))
+        elem = 8 if prec == "fp64" else 4
+        fp = tnn.server_footprint(shape, prec)
+        plan = tnn.jacobi_plan_info(shape, prec)
+        assert fp >= 4 * N * elem + N + plan["work_bytes"]
+        assert fp <= 4 * N * elem + N + plan["work_bytes"] + 64 * 1024 + 64 * shape[2] + 16 * N // 32
+    assert tnn.server_footprint((64, 64, 8), "fp32") < tnn.server_footprint((64, 64, 16), "fp32")
+    for shape in ((513, 4, 4), (0, 4, 4)):
+        with pytest.raises(tnn.TnnError):
+            tnn.server_footprint(shape, "fp32")

@@ -190,6 +190,10 @@ tnn_status tnn_admm_iterate(tnn_ctx* ctx, const void* B, const uint8_t* mask, tn
  * on ctx: out[0] = slices, out[1] = column pairs visited, out[2] = rotations
  * applied, out[3] = most sweeps of any slice, out[4] = slices that hit the
  * sweep cap, out[5] = singular values kept (above tau) over all slices.
+ * For the SVT, a slice whose Frobenius norm is below tau runs no sweep, a
+ * slice whose top singular value is certified below tau stops after the
+ * sweep that certified it, and pairs of small columns left unrotated are
+ * still counted as visited (their dot products are computed).
  * Synchronises the last stream used. */
 tnn_status tnn_last_jacobi_stats(tnn_ctx* ctx, int64_t out[6]);
 

@@ -6,8 +6,10 @@ N(0, 0.01^2) noise, 20% observed; beta0 = 1e-4, rho = 1.1, beta_max = 1e10,
 200 ADMM iterations), synthetic and seeded.  One step = one ADMM iteration of
 Algorithm 1 (forward tube DCT with the Z = X - M/beta prologue, per-slice
 Jacobi SVT, inverse DCT with the ADMM update), run through the C ABI.  The
-W warm-up steps and K timed steps continue one run from its start; the L2
-cache is flushed between timed steps.
+K timed steps are the LAST K iterations of the 200-iteration job (200 - K ..
+199), where every slice's SVD runs: an untimed prefix of the job comes first,
+its last W iterations counting as the warm-up.  The L2 cache is flushed
+between timed steps.
 
 Prints one JSON line.  `value` is t-SVT slices/s over all ranks (100 slices
 per step); the line also carries ADMM iterations/s, p50/p99 step latency, the
@@ -17,7 +19,14 @@ seen during the timed region.
 
 --impl reference times the FP64 CPU oracle instead (rank 0 only): each step
 is one oracle ADMM iteration on a 144 x 176 x 8 frame window of the same
-workload.
+workload, at the same point of the job as the timed window.
+
+--probe OP runs one library call repeatedly on a seeded tensor instead (for
+profilers that capture a launch of it) and prints its per-kernel device
+times: OP is tsvt, tdct3, tsvd, tsvt_dft, tsvt_dct_plain (--shape, --prec,
+--reps, --tau), batch (the 64-tensor uneven batch, one graph replay per
+repetition) or admm_trace (the video-shaped job one iteration at a time,
+with each iteration's device time and Jacobi statistics).
 """
 import argparse
 import json
@@ -33,7 +42,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N1, N2, N3 = 144, 176, 100
-ADMM = dict(beta0=1e-4, rho=1.1, beta_max=1e10, tol=1e-8, max_iter=200)
+JOB_ITERS = 200
+ADMM = dict(beta0=1e-4, rho=1.1, beta_max=1e10, tol=1e-8, max_iter=JOB_ITERS)
 WORKLOAD = ("video-shaped 144x176x100 FP32 TNN-C completion: tubal-rank-10 t-product of U[0,1) factors "
             "rescaled to [0,1] + period-50 drift + N(0,0.01^2) noise, 20% observed, beta0=1e-4, rho=1.1, "
             "200 ADMM iterations")
@@ -41,24 +51,47 @@ METRIC = "t-SVT slices/s (one ADMM iteration = 100 slices)"
 PREC = "tf32x3"   # FP32 data; tube DCT on tcgen05 with a 3xTF32 split; FP32 Jacobi
 FP32_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# DRAM bytes (read + write) of one Jacobi SVT launch on this workload, from
-# an ncu capture of the current kernel (dram__bytes.sum.per_second x
-# gpu__time_duration); the slices stay in L2 between the transforms.
-JACOBI_TRAFFIC_BYTES = 10.45e6
+# DRAM bytes (read + write) of one Jacobi SVT launch in the timed window,
+# from an ncu capture of the current kernel; None until one is taken.
+JACOBI_TRAFFIC_BYTES = None
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=197)
-    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--steps", type=int, default=20, help="timed ADMM iterations: the job's last K (K <= 200)")
+    p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-next", action="store_true", help="skip the batched, multispectral and serving legs")
-    p.add_argument("--serve-jobs", type=int, default=24)
-    return p.parse_args()
+    p.add_argument("--serve-jobs", type=int, default=500, help="jobs of the 200 jobs/s serving stream")
+    p.add_argument("--serve-jobs-low", type=int, default=150, help="jobs of the under-capacity stream")
+    p.add_argument("--serve-rate-low", type=float, default=1.0, help="arrival rate (jobs/s) of that stream")
+    p.add_argument("--probe", default=None, choices=["tsvt", "tdct3", "tsvd", "tsvt_dft", "tsvt_dct_plain", "batch",
+                                                     "admm_trace"])
+    p.add_argument("--shape", default="144,176,100")
+    p.add_argument("--prec", default="fp32")
+    p.add_argument("--reps", type=int, default=3)
+    p.add_argument("--tau", type=float, default=1.0)
+    p.add_argument("--seed", type=int, default=0)
+    a = p.parse_args()
+    if a.steps < 1 or a.steps > JOB_ITERS:
+        p.error("--steps must be between 1 and %d (the job's iterations)" % JOB_ITERS)
+    if a.warmup < 0:
+        p.error("--warmup must be nonnegative")
+    return a
+
+
+def window(K, W):
+    """Iterations of the timed window and of its warm-up: the window is the
+    job's last K iterations (start = 200 - K); the W iterations right before
+    it are the warm-up, the rest of the prefix is run untimed first, and any
+    warm-up the prefix cannot hold runs on a throw-away copy of the job."""
+    start = JOB_ITERS - K
+    warm_in = min(W, start)
+    return {"start": start, "prefix": start - warm_in, "warm_in": warm_in, "warm_extra": W - warm_in}
 
 
 def max_over_ranks(value, ws, dist, device):
@@ -162,12 +195,20 @@ def make_problem(ctx, torch):
 
 
 def jacobi_flops(st, m, n):
-    """FP32 flops of the Jacobi SVT formulation, per launch: m FMAs for the
+    """FP32 flops of the kernel's own formulation, per launch: m FMAs for the
     dot product of every visited pair, 2m for every rotation (scaled form),
     m per column for the singular values, and 2 m n per kept singular value
     for the V-free rebuild."""
     fma = st["pairs"] * m + st["rotations"] * 2 * m + st["slices"] * n * m + st["kept"] * 2 * m * n
     return 2.0 * fma
+
+
+def textbook_flops(st, m, n):
+    """Flops of textbook one-sided Jacobi for the same pairs and rotations:
+    three length-m dot products per visited pair (6m), a plain rotation of
+    the two columns (6m) and of the two columns of V (6n) per rotation, and
+    2 m n per kept singular value for the rebuild."""
+    return st["pairs"] * 6.0 * m + st["rotations"] * (6.0 * m + 6.0 * n) + st["kept"] * 2.0 * m * n
 
 
 def run_ours(args):
@@ -195,20 +236,31 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
     stream = torch.cuda.current_stream(dev)
 
-    # ---- chosen form: FP32 data, tube DCT on tcgen05 (3xTF32), FP32 Jacobi;
-    # W warm-up + K timed ADMM iterations of one run
+    # ---- chosen form: FP32 data, tube DCT on tcgen05 (3xTF32), FP32 Jacobi.
+    # The timed window is the job's last K iterations: warm-up that does not
+    # fit before the window runs on a throw-away copy, then one run of the
+    # job goes through its untimed prefix and the W warm-up iterations right
+    # before the window.
+    K, W = args.steps, args.warmup
+    win = window(K, W)
+    if win["warm_extra"]:
+        Bd, md, X, M = fresh(torch.float32)
+        ctx.admm_iterate(Bd, md, X, M, ADMM["beta0"], win["warm_extra"], prm, prec=PREC)
     Bd, md, X, M = fresh(torch.float32)
     beta = ADMM["beta0"]
-    for _ in range(args.warmup):
+    if win["prefix"]:
+        beta, _ = ctx.admm_iterate(Bd, md, X, M, beta, win["prefix"], prm, prec=PREC)
+    for _ in range(win["warm_in"]):
         beta, _ = ctx.admm_iterate(Bd, md, X, M, beta, 1, prm, prec=PREC)
-    step_ms, flops, jac_launch_ms = [], 0.0, 0.0
+    step_ms, flops, tflops = [], 0.0, 0.0
+    jw = {"pairs": 0, "rotations": 0, "kept": 0, "max_sweeps": 0, "unconverged": 0}
     clocks = Clocks(gpu_id_for_smi(torch, lrank))
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
     ctx.profile(True)
-    for _ in range(args.steps):
+    for _ in range(K):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -217,7 +269,12 @@ def run_ours(args):
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
-        flops += jacobi_flops(ctx.last_jacobi_stats(), m, n)
+        st = ctx.last_jacobi_stats()
+        flops += jacobi_flops(st, m, n)
+        tflops += textbook_flops(st, m, n)
+        for k in ("pairs", "rotations", "kept", "unconverged"):
+            jw[k] += st[k]
+        jw["max_sweeps"] = max(jw["max_sweeps"], st["max_sweeps"])
     prof = ctx.profile_read()
     ctx.profile(False)
     torch.cuda.synchronize()
@@ -225,11 +282,14 @@ def run_ours(args):
         dist.barrier()
     clk = clocks.stop()
     total_ms = max_over_ranks(float(np.sum(step_ms)), ws, dist, dev)
-    K = args.steps
     value = job_rate(ws, N3, K, total_ms)
     jac_ms, jac_n = prof.get("jacobi_svt", (0.0, 0))
     launches = sum(c for _, c in prof.values())
-    achieved = flops / (jac_ms / 1e3) / 1e12 if jac_ms > 0 else None
+    achieved = tflops / (jac_ms / 1e3) / 1e12 if jac_ms > 0 else None
+    achieved_own = flops / (jac_ms / 1e3) / 1e12 if jac_ms > 0 else None
+    jw.update({"iterations": [win["start"], JOB_ITERS - 1], "kept_per_step": jw["kept"] / K,
+               "pairs_per_step": jw["pairs"] / K, "rotations_per_step": jw["rotations"] / K,
+               "textbook_gflop_per_step": tflops / K / 1e9, "kernel_gflop_per_step": flops / K / 1e9})
 
     # ---- accuracy of one t-SVT of the chosen form at the end of the timed
     # run, against the FP64 GPU path on the same input Z = X - M/beta
@@ -247,17 +307,18 @@ def run_ours(args):
         dn = np.linalg.norm(y32 - y64)
         acc = {"tsvt_rel_err_vs_fp64": float(dn / max(np.linalg.norm(y64), 1e-300)),
                "tsvt_err_over_input_norm": float(dn / np.linalg.norm(Z)), "tau": tau,
-               "where": "t-SVT of Z = X - M/beta after the timed iterations"}
+               "where": "t-SVT of Z = X - M/beta after the last iteration of the job"}
 
     # ---- plain FP64 GPU path on the same workload and the same iterations
-    # (its own run: W untimed + K timed ADMM iterations, FP64 data,
-    # transforms and Jacobi), and the two runs' final X against each other
+    # (its own run of the job: untimed prefix, then the same K timed
+    # iterations; FP64 data, transforms and Jacobi), and the two runs' final
+    # X against each other
     fp64 = None
     if not args.no_fp64:
         Bd64, md64, X64, M64 = fresh(torch.float64)
         b64 = ADMM["beta0"]
-        for _ in range(args.warmup):
-            b64, _ = ctx.admm_iterate(Bd64, md64, X64, M64, b64, 1, prm, prec="fp64")
+        if win["start"]:
+            b64, _ = ctx.admm_iterate(Bd64, md64, X64, M64, b64, win["start"], prm, prec="fp64")
         ms64 = []
         for _ in range(K):
             flush.zero_()
@@ -273,11 +334,12 @@ def run_ours(args):
         fp64 = {"value": N3 * K / (float(np.sum(ms64)) / 1e3), "unit": "slices/s", "steps": K,
                 "ms_per_step": float(np.mean(ms64)), "p50_ms": float(np.percentile(ms64, 50)),
                 "p99_ms": float(np.percentile(ms64, 99)),
-                "sample": "ADMM iterations %d-%d of an FP64 run (the FP32 line's iterations), L2 flushed"
-                          % (args.warmup, args.warmup + K - 1),
+                "sample": "ADMM iterations %d-%d of an FP64 run of the job (the FP32 line's iterations), L2 flushed"
+                          % (win["start"], JOB_ITERS - 1),
                 "speedup_fp32_over_fp64": float(np.sum(ms64)) / total_ms,
                 "final_x_rel_diff_fp32_vs_fp64": float(np.linalg.norm(x32 - x64) / np.linalg.norm(x64)),
-                "final_x_rel_err_vs_ground_truth": float(np.linalg.norm(x64 - T) / np.linalg.norm(T))}
+                "final_x_rel_err_vs_ground_truth": float(np.linalg.norm(x64 - T) / np.linalg.norm(T)),
+                "final_x_rel_err_vs_ground_truth_fp32": float(np.linalg.norm(x32 - T) / np.linalg.norm(T))}
         del Bd64, md64, X64, M64
 
     # ---- end to end through the C ABI with pinned host buffers (whole 200-iteration job)
@@ -303,12 +365,13 @@ def run_ours(args):
     # t-SVT, serving stream
     nxt = None
     if rank == 0 and ws == 1 and not args.no_next:
-        nxt = next_legs(ctx, torch, dev, flush, args.serve_jobs)
+        nxt = next_legs(ctx, torch, dev, flush, {"jobs": args.serve_jobs, "jobs_low": args.serve_jobs_low,
+                                                 "rate_low": args.serve_rate_low})
 
     # ---- CPU oracle on the host cores: bounded sample (t-SVT of the full tensor)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
-        cpu = oracle_baseline(B, mask, budget_s=12.0)
+        cpu = oracle_baseline(K, W)
 
     peaks = {}
     try:
@@ -332,11 +395,28 @@ def run_ours(args):
         peak, basis = FP32_PEAK_TFLOPS, FP32_PEAK_NOTE + " (derived, not measured)"
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": (achieved / peak) if achieved else None, "traffic": JACOBI_TRAFFIC_BYTES,
-            "traffic_basis": "ncu dram__bytes of one launch of this kernel on this workload "
-                             "(profiles/jacobi_svt_fp32_144x176x100.md)",
-            "kernel": "jacobi_svt (FP32 CUDA cores)", "peak_basis": basis, "fma_peaks": fma,
+            "kernel": "jacobi_svt (FP32 CUDA cores)",
+            "flops_basis": "textbook one-sided Jacobi count of the window's visited pairs and rotations: 6m per "
+                           "pair (three dot products), 6m + 6n per rotation (columns and V), 2mn per kept singular "
+                           "value (rebuild); m = 176, n = 144",
+            "achieved_kernel_count": achieved_own,
+            "frac_kernel_count": (achieved_own / peak) if achieved_own else None,
+            "kernel_count_basis": "the kernel's own FMAs (V-free, scaled rotations, carried norms): m per pair, "
+                                  "2m per rotation, mn per slice, 2mn per kept singular value",
+            "peak_basis": basis, "fma_peaks": fma,
             "launches": jac_n, "avg_launch_ms": jac_ms / max(jac_n, 1),
             "share_of_step": jac_ms / total_ms if total_ms > 0 else None}
+    # the transforms' HBM roofline: algorithmic bytes per launch (forward with
+    # the Z = X - M/beta prologue: X, M in, Z-bar out = 12 B per element;
+    # inverse with the ADMM update: Y-bar, X, M, B in, X, M out, mask = 25 B)
+    hbm = peaks.get("hbm_gbs")
+    tr = {}
+    for name, bpe in (("tube_fwd_admm", 12), ("tube_inv_admm", 25)):
+        t_ms, t_n = prof.get(name, (0.0, 0))
+        if t_n:
+            gbs = bpe * N1 * N2 * N3 / (t_ms / t_n / 1e3) / 1e9
+            tr[name] = {"bound": "hbm", "bytes_per_launch": bpe * N1 * N2 * N3, "avg_launch_ms": t_ms / t_n,
+                        "achieved": gbs, "unit": "GB/s", "peak": hbm, "frac": gbs / hbm if hbm else None}
     out = {
         "metric": METRIC, "value": value, "unit": "slices/s", "n_gpus": ws, "steps": K, "warmup": args.warmup,
         "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -345,7 +425,8 @@ def run_ours(args):
                    else "single", "l2": "flushed between timed steps (256 MB write)", "prec": PREC},
         "admm_iters_per_s": ws * K / (total_ms / 1e3),
         "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
-        "roofline": roof, "kernels_ms": {k: v[0] for k, v in prof.items()},
+        "roofline": roof, "transform_roofline": tr, "jacobi_window": jw,
+        "kernels_ms": {k: v[0] for k, v in prof.items()},
         "gpu_launches": launches, "clocks": clk, "e2e": e2e, "fp64_plain": fp64, "accuracy": acc,
         "cpu_baseline": cpu, "other_workloads": nxt,
         "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained")},
@@ -374,13 +455,13 @@ def timed(fn, reps, flush, stream, torch):
     return ms
 
 
-def next_legs(ctx, torch, dev, flush, serve_jobs):
+def next_legs(ctx, torch, dev, flush, serve):
     """Batched uneven t-SVT (64 tensors, n1, n2 in [32, 256], n3 in [8, 64],
     FP32, one graph launch, autotuned) against the per-tensor loop; the
     512 x 512 x 31 multispectral-shaped t-SVT (BF16-split transforms, slices
     on thread-block clusters) and its FP64 plain path; the DCT against the
-    DFT t-SVT at the paper's Table 2 sizes; and a seeded serving stream of
-    completion jobs."""
+    DFT t-SVT at the paper's Table 2 sizes; and seeded serving streams of
+    completion jobs (the offered 200 jobs/s and one under capacity)."""
     from paper_1902_03070_gb300 import inputs, serve, tnn
     stream = torch.cuda.current_stream(dev)
     out = {}
@@ -487,49 +568,39 @@ def next_legs(ctx, torch, dev, flush, serve_jobs):
                                  "vs real slices, n3/2+1 vs n3 of them); dct_tuned is tsvt_dct; dct_tsvd is "
                                  "tsvd_dct_forward (U, S, V)",
                          "rows": cmp}
-    # ---- serving stream
-    jobs = serve.make_stream(serve_jobs, 200.0, tprod=tp)
-    _, summ = serve.run(jobs, streams=8, chunk=8, max_active=8, policy=1)
+    # ---- serving: the offered stream (Poisson, 200 jobs/s, far above what one
+    # GPU completes: latency is queueing), a stream under capacity (latency
+    # is service time), and a prefix of the first with the FP32 and FP64
+    # jobs' iterations batched
+    jobs = serve.make_stream(serve["jobs"], 200.0, tprod=tp)
+    _, summ = serve.run(jobs, streams=8, chunk=8, max_active=8, policy=1, timeout_s=1500.0)
     summ.update({"rate_jobs_per_s": 200.0, "policy": "shortest estimated work first, at most 8 running",
-                 "note": "the stream's offered load is far above what one GPU completes: latency is queueing"})
+                 "note": "the offered load is far above what one GPU completes: latency is queueing"})
     out["serving"] = summ
-    _, summ = serve.run(jobs, streams=8, chunk=8, max_active=8, policy=1, batch_kernels=True)
-    summ.update({"rate_jobs_per_s": 200.0, "policy": "as serving, FP32 and FP64 jobs' iterations batched (one "
-                                                     "launch sequence per precision per iteration)"})
+    nb = min(100, len(jobs))
+    _, summ = serve.run(jobs[:nb], streams=8, chunk=8, max_active=8, policy=1, batch_kernels=True)
+    summ.update({"rate_jobs_per_s": 200.0, "policy": "as serving (its first %d jobs), FP32 and FP64 jobs' "
+                                                     "iterations batched (one launch sequence per precision per "
+                                                     "iteration)" % nb})
     out["serving_batched"] = summ
+    del jobs
+    if serve["jobs_low"] > 0:
+        jobs = serve.make_stream(serve["jobs_low"], serve["rate_low"], seed=1902_03076, tprod=tp)
+        _, summ = serve.run(jobs, streams=8, chunk=8, max_active=8, policy=1, timeout_s=1500.0)
+        summ.update({"rate_jobs_per_s": serve["rate_low"], "policy": "shortest estimated work first, at most 8 "
+                                                                     "running",
+                     "note": "offered load under capacity: latency is service time"})
+        out["serving_low_rate"] = summ
     return out
 
 
-def oracle_baseline(B, mask, budget_s=12.0):
-    """Time the FP64 CPU oracle's t-SVT on the full 144x176x100 tensor (one
-    ADMM iteration's t-SVT at a mid-run threshold) with every host core."""
-    import oracle as O
-    cores = len(os.sched_getaffinity(0))
-    got = O.threads(cores)
-    Z = np.asfortranarray(B)
-    tau = 1.0
-    reps, t0 = 0, time.perf_counter()
-    while True:
-        O.tsvt(Z, tau, nthreads=got)
-        reps += 1
-        el = time.perf_counter() - t0
-        if el >= budget_s or reps >= 20:
-            break
-    # the same t-SVT on one core (10 slices of the tensor, scaled to slices/s)
-    O.threads(1)
-    t1 = time.perf_counter()
-    O.tsvt(np.asfortranarray(Z[:, :, :10]), tau, nthreads=1)
-    single = 10 / (time.perf_counter() - t1)
-    O.threads(got)
-    return {"value": N3 * reps / el, "unit": "slices/s", "cores": got, "kind": "oracle",
-            "sample": "%d oracle t-SVT(s) of the full 144x176x100 tensor (tau=1.0), %.1f s" % (reps, el),
-            "single_core_slices_per_s": single}
-
-
-def run_reference(args):
-    ws, rank, _ = dist_env()
-    if rank != 0:
-        return
+def oracle_window(K, W, nthreads):
+    """The FP64 CPU oracle on a 144 x 176 x 8 frame window of the workload
+    (slices of the full tensor's shape; its own completion problem, same
+    observed fraction and beta schedule), at the point of the job the GPU
+    line times: the prefix of the 200-iteration job untimed (its last W
+    iterations are the warm-up), then the job's last K iterations timed one
+    at a time.  Returns (per-iteration seconds, threads used, window)."""
     import oracle as O
     from paper_1902_03070_gb300 import inputs
     parts = inputs.config2_parts(N1, N2, N3)
@@ -538,21 +609,49 @@ def run_reference(args):
     win = 8
     Bw = np.asfortranarray((T * mask)[:, :, :win])
     mw = np.asfortranarray(mask[:, :, :win])
-    cores = len(os.sched_getaffinity(0))
-    got = O.threads(cores)
+    got = O.threads(nthreads)
     prm = dict(ADMM)
+    prm["tol"] = -1.0   # a fixed number of iterations
+    start = JOB_ITERS - K
+    beta = ADMM["beta0"]
+    X = M = None
+    if start:
+        prm["max_iter"] = start
+        X, M, rep = O.admm(Bw, mw, nthreads=got, **prm)
+        beta = rep["beta_final"]
     prm["max_iter"] = 1
-    prm["tol"] = -1.0
-    for _ in range(args.warmup):
-        O.admm(Bw, mw, nthreads=got, **prm)
     times = []
-    for _ in range(args.steps):
+    for _ in range(K):
+        prm["beta0"] = beta
         t0 = time.perf_counter()
-        O.admm(Bw, mw, nthreads=got, **prm)
+        if X is None:
+            X, M, rep = O.admm(Bw, mw, nthreads=got, **prm)
+        else:
+            X, M, rep = O.admm(Bw, mw, nthreads=got, X0=X, M0=M, **prm)
         times.append(time.perf_counter() - t0)
+        beta = rep["beta_final"]
+    return times, got, win
+
+
+def oracle_baseline(K, W):
+    """The CPU oracle's rate on the timed iterations (all host cores)."""
+    times, got, win = oracle_window(K, W, len(os.sched_getaffinity(0)))
+    tot = float(np.sum(times))
+    return {"value": win * K / tot, "unit": "slices/s", "cores": got, "kind": "oracle",
+            "sample": "oracle ADMM iterations %d-%d of the job on a 144x176x%d frame window (its own completion "
+                      "problem; prefix untimed), %d threads, %.1f s timed" % (JOB_ITERS - K, JOB_ITERS - 1, win, got,
+                                                                            tot)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    times, got, win = oracle_window(args.steps, args.warmup, len(os.sched_getaffinity(0)))
     tot = float(np.sum(times))
     value = win * args.steps / tot
-    sample = "one oracle ADMM iteration on a 144x176x%d frame window per step (%d threads)" % (win, got)
+    sample = ("oracle ADMM iterations %d-%d of the job on a 144x176x%d frame window per step (prefix untimed, "
+              "%d threads)" % (JOB_ITERS - args.steps, JOB_ITERS - 1, win, got))
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "slices/s", "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -562,9 +661,103 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_probe(a):
+    """One library call repeated on a seeded tensor (for profilers that
+    capture a launch of it); prints per-kernel device times and the Jacobi
+    statistics of the last call."""
+    import torch
+
+    from paper_1902_03070_gb300 import inputs, tnn
+    if a.probe == "batch":
+        return probe_batch(a, torch, inputs, tnn)
+    if a.probe == "admm_trace":
+        return probe_admm_trace(torch, inputs, tnn)
+    shape = tuple(int(x) for x in a.shape.split(","))
+    dt = torch.float64 if a.prec == "fp64" else torch.float32
+    Z = inputs.random_tensor(shape, np.random.default_rng(a.seed), "uniform")
+    with tnn.Context(0) as ctx:
+        Zd = tnn.to_fortran(Z, dtype=dt)
+        Yd = tnn.fortran_empty(shape, dt)
+        for rep in range(a.reps + 1):
+            if rep == 1:  # the first call (module loading, operator build) is not timed
+                torch.cuda.synchronize()
+                ctx.profile(True)
+            if a.probe == "tsvt":
+                ctx.tsvt(Zd, a.tau, Y=Yd, prec=a.prec)
+            elif a.probe in ("tsvt_dft", "tsvt_dct_plain"):
+                getattr(ctx, a.probe)(Zd, a.tau, Y=Yd, prec=a.prec, allow_noconv=True)
+            elif a.probe == "tdct3":
+                ctx.tdct3(Zd, Yd, prec=a.prec)
+            else:
+                r = min(shape[0], shape[1])
+                U = tnn.fortran_empty((shape[0], r, shape[2]), dt)
+                S = tnn.fortran_empty((r, shape[2]), dt)
+                V = tnn.fortran_empty((shape[1], r, shape[2]), dt)
+                ctx.tsvd(Zd, U, S, V, prec=a.prec)
+        torch.cuda.synchronize()
+        prof = ctx.profile_read()
+        out = {"probe": a.probe, "shape": shape, "prec": a.prec, "reps": a.reps,
+               "kernels": {k: {"ms_total": v[0], "launches": v[1], "ms_per_launch": v[0] / max(v[1], 1)}
+                           for k, v in prof.items()}}
+        if a.probe in ("tsvt", "tsvd", "tsvt_dft", "tsvt_dct_plain"):
+            out["jacobi"] = ctx.last_jacobi_stats()
+        print(json.dumps(out))
+
+
+def probe_batch(a, torch, inputs, tnn):
+    """The 64-tensor uneven batch, one graph replay per repetition; prints
+    per-launch times of one serial profiled run."""
+    from paper_1902_03070_gb300.serve import library_tprod
+    with tnn.Context(0) as ctx:
+        Zs = inputs.config4(library_tprod(ctx))
+        taus = [inputs.config4_tau(Z.shape[0], Z.shape[1]) for Z in Zs]
+        Zd = [tnn.to_fortran(Z, dtype=torch.float32) for Z in Zs]
+        Yd = [tnn.fortran_empty(Z.shape, torch.float32) for Z in Zs]
+        plan = ctx.tsvt_batch(Zd, taus, Yd, prec="fp32", graph=True, autotune=False)
+        for _ in range(a.reps + 1):
+            plan.run()
+        torch.cuda.synchronize()
+        print(json.dumps({"probe": "batch", "tensors": len(Zs), "info": plan.info(), "groups": plan.groups(),
+                          "profile_ms": plan.profile()}))
+        plan.close()
+
+
+def probe_admm_trace(torch, inputs, tnn):
+    """Per-iteration device time and Jacobi statistics of the video-shaped
+    completion (Algorithm 1, one tnn_admm_iterate call per iteration)."""
+    from paper_1902_03070_gb300.serve import library_tprod
+    with tnn.Context(0) as ctx:
+        d = inputs.config2(library_tprod(ctx))
+        B, mask = d["B"], d["mask"]
+        prm = dict(d["admm"])
+        dev = torch.device("cuda", 0)
+        Bd = tnn.to_fortran(B, device=dev, dtype=torch.float32)
+        md = tnn.to_fortran(mask, device=dev)
+        X = tnn.to_fortran(B * mask, device=dev, dtype=torch.float32)
+        M = tnn.to_fortran(np.zeros(B.shape), device=dev, dtype=torch.float32)
+        beta = prm["beta0"]
+        cp = ctx.params(**prm)
+        s = torch.cuda.current_stream(dev)
+        rows = []
+        for it in range(prm["max_iter"]):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            beta, _ = ctx.admm_iterate(Bd, md, X, M, beta, 1, cp, prec="tf32x3")
+            e1.record(s)
+            e1.synchronize()
+            st = ctx.last_jacobi_stats()
+            rows.append({"iter": it, "ms": e0.elapsed_time(e1), "pairs": st["pairs"], "rotations": st["rotations"],
+                         "max_sweeps": st["max_sweeps"], "kept": st["kept"]})
+        print(json.dumps({"probe": "admm_trace", "workload": "144x176x100 video-shaped, 20% observed, tf32x3",
+                          "total_ms": sum(r["ms"] for r in rows), "rows": rows}))
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.probe:
+        run_probe(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -117,6 +117,24 @@ const char* tnn_last_error(const tnn_ctx* ctx);
 /* Grow the context's device workspace to at least `bytes` (never shrinks). */
 tnn_status tnn_reserve(tnn_ctx* ctx, size_t bytes);
 
+/* Per-context options (no counterpart in the paper).
+ * TNN_OPT_JACOBI_MAX_SWEEPS: sweep cap of the per-slice Jacobi SVT in
+ *   tsvt_dct (0 = the kernels' default of 30; 1 ... 1000).  A slice that
+ *   reaches the cap still gets its shrinkage and rebuild from the columns
+ *   as they are; the call reports TNN_ENOCONV when it reports a status.
+ * TNN_OPT_TC_WAIT_POLLS: how many times each bounded mbarrier wait of the
+ *   tensor-core transforms polls before it gives up (negative = the default,
+ *   about 4e6).  A wait that gives up makes the kernel set the context's
+ *   error flag, stop issuing work, let its own copies and MMAs in flight
+ *   finish (waiting with the default bound), free its tensor memory and
+ *   return; the next call that checks the flag returns TNN_ECUDA and clears
+ *   it.  For exercising that path; the output of a call that timed out is
+ *   undefined.
+ * Returns TNN_EINVAL for an unknown option or a value out of range. */
+#define TNN_OPT_JACOBI_MAX_SWEEPS 1
+#define TNN_OPT_TC_WAIT_POLLS 2
+tnn_status tnn_set_option(tnn_ctx* ctx, int option, int64_t value);
+
 enum { TNN_OP_TDCT3 = 0, TNN_OP_TSVT = 1, TNN_OP_TSVD = 2, TNN_OP_TPROD = 3, TNN_OP_COMPLETE = 4 };
 
 /* Device workspace `op` needs for `shape` at `prec` with device buffers (host
@@ -202,21 +220,28 @@ tnn_status tnn_last_jacobi_stats(tnn_ctx* ctx, int64_t out[6]);
  * when they need a t-SVT: a serving loop bound to a fixed memory budget owned
  * by another allocator, code that must not create a context of its own, or a
  * thread that may not wait on the allocator's implicit synchronisation.
- * Computes exactly what tsvt_dct computes (same kernels), without tnn_out.
- * Z and Y must be device pointers on the current device; Y may be Z.
+ * Computes what tsvt_dct computes for the same precision, with the same
+ * kernels (the tensor-core transforms for TNN_FP32_TF32X3 and
+ * TNN_FP32_BF16SPLIT, the CUDA-core ones for TNN_FP32 and TNN_FP64), without
+ * tnn_out.  Z and Y must be device pointers of the current device (or
+ * managed memory); Y may be Z; anything else returns TNN_EINVAL.
  * Scratch: one file-scope device array of TNN_STATIC_SCRATCH_BYTES that every
  * GPU loading the library holds until the process exits.  The call needs
- * 2 n3^2 elements (DCT operators) + n1 n2 n3 elements + 32 n3 bytes (each
- * part rounded up to 256 bytes), plus the Jacobi working copies when a
- * frontal slice does not fit in shared memory; a larger problem returns
- * TNN_EINVAL before anything is launched (at most about 4.1e6 float or 2.0e6
- * double elements when the slices fit in shared memory).  The first call on
- * a device looks the array's device address up with cudaGetSymbolAddress
- * (device current); make that first call before any stream capture.  All
- * calls share the array and the call writes every scratch byte it reads, so
- * nothing carries over from an earlier call; calls whose GPU work overlaps
- * (other streams, other threads) race on the scratch and must be ordered by
- * the caller.  Returns before the GPU finishes (stream-ordered). */
+ * 256 bytes + the two DCT operators (2 n3^2 elements, or the tensor-core
+ * images of them) + n1 n2 n3 elements + 32 n3 bytes (each part rounded up to
+ * 256 bytes), plus the Jacobi working copies when a frontal slice does not
+ * fit in shared memory; a larger problem (or a size whose byte count would
+ * not fit in size_t) returns TNN_EINVAL before anything is launched (at most
+ * about 4.1e6 float or 2.0e6 double elements when the slices fit in shared
+ * memory).  The first call on a device looks the array's device address up
+ * with cudaGetSymbolAddress (device current); make that first call before
+ * any stream capture.  All calls share the array and the call writes every
+ * scratch byte it reads, so nothing carries over from an earlier call; calls
+ * whose GPU work overlaps (other streams, other threads) race on the scratch
+ * and must be ordered by the caller.  The call synchronises the stream at
+ * the end and returns TNN_ENOCONV when a slice's Jacobi SVD hit its sweep
+ * cap, TNN_ENONFINITE when a NaN or infinity was met (Y is written in both
+ * cases) and TNN_ECUDA when a tensor-core transform timed out. */
 #define TNN_STATIC_SCRATCH_BYTES ((size_t)16 << 20)
 tnn_status tsvt_dct_static(const void* Z, tnn_shape shape, double tau, tnn_precision prec, void* Y, void* stream);
 

@@ -35,7 +35,7 @@ def _open(path):
     L.or_tsvd.argtypes = [i64, i64, i64, d, d, d, d, _ct.c_int, _ct.c_int]
     L.or_tsvd.restype = _ct.c_int
     L.or_admm.argtypes = [i64, i64, i64, d, _ct.POINTER(_ct.c_uint8), _ct.c_double, _ct.c_double,
-                          _ct.c_double, _ct.c_double, _ct.c_int, _ct.c_int, _ct.c_int, d, d, d]
+                          _ct.c_double, _ct.c_double, _ct.c_int, _ct.c_int, _ct.c_int, _ct.c_int, d, d, d]
     L.or_threads.argtypes = [_ct.c_int]
     L.or_threads.restype = _ct.c_int
     return L
@@ -193,17 +193,25 @@ def ttranspose(X):
     return _np.asfortranarray(_np.transpose(_np.asarray(X), (1, 0, 2)))
 
 
-def admm(B, mask, beta0=1e-4, rho=1.1, beta_max=1e10, tol=1e-8, max_iter=300, max_sweeps=100, nthreads=1):
-    """Algorithm 1 with the schedule beta <- min(rho beta, beta_max).
-    Returns (X, M, report dict)."""
+def admm(B, mask, beta0=1e-4, rho=1.1, beta_max=1e10, tol=1e-8, max_iter=300, max_sweeps=100, nthreads=1,
+         X0=None, M0=None):
+    """Algorithm 1 with the schedule beta <- min(rho beta, beta_max), from
+    X = B on the mask, M = 0, or (with X0 and M0) continuing from that state
+    with beta0 as the next iteration's beta.  Returns (X, M, report dict);
+    report["beta_final"] is the beta a further iteration would use."""
     B = _f64(B)
     n1, n2, n3 = _shape3(B)
     mk = _np.asfortranarray(_np.asarray(mask, dtype=_np.uint8).reshape((n1, n2, n3), order="F"))
-    X = _np.zeros((n1, n2, n3), order="F")
-    M = _np.zeros((n1, n2, n3), order="F")
+    resume = X0 is not None
+    if resume != (M0 is not None):
+        raise ValueError("X0 and M0 go together")
+    X = _np.array(_f64(X0).reshape((n1, n2, n3), order="F"), order="F") if resume else \
+        _np.zeros((n1, n2, n3), order="F")
+    M = _np.array(_f64(M0).reshape((n1, n2, n3), order="F"), order="F") if resume else \
+        _np.zeros((n1, n2, n3), order="F")
     out = _np.zeros(5)
     _load().or_admm(n1, n2, n3, _dp(B), mk.ctypes.data_as(_ct.POINTER(_ct.c_uint8)), beta0, rho, beta_max,
-                    tol, int(max_iter), int(max_sweeps), int(nthreads), _dp(X), _dp(M), _dp(out))
+                    tol, int(max_iter), int(max_sweeps), int(nthreads), int(resume), _dp(X), _dp(M), _dp(out))
     rep = {"iters": int(out[0]), "rel_change": out[1], "primal_res": out[2], "beta_final": out[3],
            "converged": bool(out[4])}
     return X, M, rep

@@ -425,13 +425,17 @@ int or_tsvd(i64 m1, i64 m2, i64 m3, const double* X, double* U, double* S, doubl
 /* out[3] = beta after the last update, out[4] = converged.                  */
 /* ------------------------------------------------------------------------ */
 void or_admm(i64 n1, i64 n2, i64 n3, const double* B, const uint8_t* mask, double beta0, double rho,
-             double beta_max, double tol, int max_iter, int max_sweeps, int nthreads, double* X,
-             double* M, double* out)
+             double beta_max, double tol, int max_iter, int max_sweeps, int nthreads, int resume,
+             double* X, double* M, double* out)
 {
     const i64 N = n1 * n2 * n3;
     double* Z = (double*)malloc(sizeof(double) * (size_t)N);
     double* Y = (double*)malloc(sizeof(double) * (size_t)N);
-    for (i64 e = 0; e < N; ++e) { X[e] = mask[e] ? B[e] : 0.0; M[e] = 0.0; }
+    /* Algorithm 1 starts from X = B on the mask and M = 0; with resume set the
+       iterations continue from the (X, M) passed in, beta0 being the beta the
+       next iteration uses. */
+    if (!resume)
+        for (i64 e = 0; e < N; ++e) { X[e] = mask[e] ? B[e] : 0.0; M[e] = 0.0; }
     double beta = beta0, relchg = 0.0, pres = 0.0;
     int l = 0, conv = 0;
     for (;;) {

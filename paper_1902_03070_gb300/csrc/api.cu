@@ -25,6 +25,8 @@ struct tnn_ctx {
     std::map<std::tuple<int64_t, int, int, int>, void*> ops;  // (n3, elem, inverse, scaled) -> operator
     std::map<std::tuple<int64_t, int, int, int>, float*> tc_ops;  // (n3, inverse, scaled, bf16) -> tensor-core images
     int* d_err = nullptr;        // set by a tensor-core kernel whose bounded wait timed out
+    int opt_jacobi_sweeps = 0;   // TNN_OPT_JACOBI_MAX_SWEEPS (0: the kernels' default)
+    int opt_tc_polls = -1;       // TNN_OPT_TC_WAIT_POLLS (negative: the default limit)
     SliceStats* last_stats = nullptr;
     int64_t last_n3 = 0;
     cudaStream_t last_stream = nullptr;
@@ -227,7 +229,7 @@ tnn_status get_tube(tnn_ctx* ctx, tnn_precision prec, int elem, int64_t n3, int 
 cudaError_t tube_any(tnn_ctx* ctx, int elem, const void* X, void* Y, const TubeOp& t, int64_t P, int64_t n3,
                      cudaStream_t s)
 {
-    if (t.tc) return launch_tube_tc((const float*)X, (float*)Y, t.img, P, n3, t.bf, ctx->d_err, s);
+    if (t.tc) return launch_tube_tc((const float*)X, (float*)Y, t.img, P, n3, t.bf, ctx->d_err, s, ctx->opt_tc_polls);
     return elem == 8 ? launch_tube_op<double>((const double*)X, (double*)Y, (const double*)t.op, P, n3, s)
                      : launch_tube_op<float>((const float*)X, (float*)Y, (const float*)t.op, P, n3, s);
 }
@@ -311,6 +313,22 @@ void tnn_destroy(tnn_ctx* ctx)
     for (auto e : ctx->pool) cudaEventDestroy(e);
     if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
     delete ctx;
+}
+
+tnn_status tnn_set_option(tnn_ctx* ctx, int option, int64_t value)
+{
+    if (!ctx) return TNN_EINVAL;
+    switch (option) {
+    case TNN_OPT_JACOBI_MAX_SWEEPS:
+        if (value < 0 || value > 1000) return fail(ctx, TNN_EINVAL, "sweep cap %lld out of range", (long long)value);
+        ctx->opt_jacobi_sweeps = (int)value;
+        return TNN_OK;
+    case TNN_OPT_TC_WAIT_POLLS:
+        if (value > (int64_t)1 << 30) return fail(ctx, TNN_EINVAL, "poll limit %lld out of range", (long long)value);
+        ctx->opt_tc_polls = value < 0 ? -1 : (int)value;
+        return TNN_OK;
+    default: return fail(ctx, TNN_EINVAL, "unknown option %d", option);
+    }
 }
 
 tnn_status tnn_reserve(tnn_ctx* ctx, size_t bytes)
@@ -488,8 +506,9 @@ tnn_status tsvt_dct(tnn_ctx* ctx, const void* Z, tnn_shape sh, double tau, tnn_p
     }
     {
         TRACE(K_JACOBI_SVT);
-        if (elem == 8) CK(launch_jacobi_svt<double>(jp, (double*)W, tau, nullptr, 0, at(ctx, ojw), stats, s));
-        else CK(launch_jacobi_svt<float>(jp, (float*)W, tau, nullptr, 0, at(ctx, ojw), stats, s));
+        const int sw = ctx->opt_jacobi_sweeps;
+        if (elem == 8) CK(launch_jacobi_svt<double>(jp, (double*)W, tau, nullptr, sw, at(ctx, ojw), stats, s));
+        else CK(launch_jacobi_svt<float>(jp, (float*)W, tau, nullptr, sw, at(ctx, ojw), stats, s));
     }
     {
         TRACE(K_TUBE);
@@ -702,7 +721,7 @@ tnn_status admm_enqueue_iters(tnn_ctx* ctx, const AdmmJob& j, int iters, cudaStr
             { TRACE(K_TUBE_FWD_ADMM);
               if (opf.tc)
                   CK(launch_tube_tc_fwd_admm((const float*)j.X, (const float*)j.M, (float*)j.W, opf.img, P, n3, opf.bf,
-                                             j.ctl, ctx->d_err, s));
+                                             j.ctl, ctx->d_err, s, ctx->opt_tc_polls));
               else
                   CK(launch_tube_fwd_admm_op<float>((const float*)j.X, (const float*)j.M, (float*)j.W,
                                                     (const float*)opf.op, P, n3, j.ctl, s)); }
@@ -711,7 +730,8 @@ tnn_status admm_enqueue_iters(tnn_ctx* ctx, const AdmmJob& j, int iters, cudaStr
             { TRACE(K_TUBE_INV_ADMM);
               if (opi.tc)
                   CK(launch_tube_tc_inv_admm((const float*)j.W, (float*)j.X, (float*)j.M, (const float*)j.B, j.mask,
-                                             opi.img, P, n3, opi.bf, j.ctl, j.partials, &nblk, ctx->d_err, s));
+                                             opi.img, P, n3, opi.bf, j.ctl, j.partials, &nblk, ctx->d_err, s,
+                                             ctx->opt_tc_polls));
               else
                   CK(launch_tube_inv_admm_op<float>((const float*)j.W, (float*)j.X, (float*)j.M, (const float*)j.B,
                                                     j.mask, (const float*)opi.op, P, n3, j.ctl, j.partials, &nblk, s)); }

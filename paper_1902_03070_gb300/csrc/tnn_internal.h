@@ -84,18 +84,20 @@ cudaError_t launch_ctl_init(AdmmCtl* ctl, double beta, double rho, double beta_m
 // 3xTF32 split, or BF16 hi/lo split when bf; the operator is passed as
 // prebuilt hi/lo images in the MMA's shared-memory layout
 // (launch_build_operator_tc, tube_tc_image_floats floats of storage).
-// *err is set to 1 if a bounded wait timed out.
+// *err is set to 1 if a bounded wait timed out; `spin` bounds the polls of
+// each wait (negative: the default limit, about 4e6 polls).
 bool tube_tc_supported(int64_t n3);
 size_t tube_tc_image_floats(int64_t n3, bool bf);
 int tube_tc_partials_count(int64_t P);
 cudaError_t launch_build_operator_tc(float* img, int64_t n3, int inverse, int scaled, bool bf, cudaStream_t s);
 cudaError_t launch_tube_tc(const float* X, float* Y, const float* img, int64_t P, int64_t n3, bool bf, int* err,
-                           cudaStream_t s);
+                           cudaStream_t s, int spin = -1);
 cudaError_t launch_tube_tc_fwd_admm(const float* X, const float* M, float* Zbar, const float* img, int64_t P,
-                                    int64_t n3, bool bf, const AdmmCtl* ctl, int* err, cudaStream_t s);
+                                    int64_t n3, bool bf, const AdmmCtl* ctl, int* err, cudaStream_t s,
+                                    int spin = -1);
 cudaError_t launch_tube_tc_inv_admm(const float* Ybar, float* X, float* M, const float* B, const uint8_t* mask,
                                     const float* img, int64_t P, int64_t n3, bool bf, const AdmmCtl* ctl,
-                                    double* partials, int* nblocks, int* err, cudaStream_t s);
+                                    double* partials, int* nblocks, int* err, cudaStream_t s, int spin = -1);
 
 // ---- Jacobi SVT / SVD (jacobi.cu) -------------------------------------------
 // One frontal slice of a batched SVT launch (slices of different tensors and

@@ -96,11 +96,12 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
-// Bounded wait for the given phase parity; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+// Bounded wait for the given phase parity (at most `limit` polls); false on
+// timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit)
 {
     const uint32_t a = smem_u32(bar);
-    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+    for (uint32_t it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
@@ -175,7 +176,7 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
                const float* __restrict__ bimg, int64_t P, int n3, int NP, int nchunks, uint32_t tmem_cols,
                const AdmmCtl* __restrict__ ctl, float* __restrict__ Xs, float* __restrict__ Ms,
                const float* __restrict__ Bs, const uint8_t* __restrict__ mask, double* __restrict__ partials,
-               int* __restrict__ err)
+               int* __restrict__ err, uint32_t spin)
 {
     if (MODE != 0 && ctl->done) return;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -246,7 +247,7 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
         }
         if (c > 0) {
             // the A tiles are rewritten only after the previous chunk's MMAs completed
-            const int late = mbar_wait(&bar_mma, phase_m) ? 0 : 1;
+            const int late = mbar_wait(&bar_mma, phase_m, spin) ? 0 : 1;
             phase_m ^= 1;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             if (__syncthreads_or(late)) {
@@ -297,7 +298,7 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
         int fail = 0;
         if (tid == 0) {
             const int t = c & 1;
-            if (!mbar_wait(&bar_b[t], phase_b[t])) {
+            if (!mbar_wait(&bar_b[t], phase_b[t], spin)) {
                 fail = 1;
             } else {
                 b_pending[t] = false;
@@ -335,7 +336,7 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
         }
     }
     if (ok) {
-        const int late = mbar_wait(&bar_mma, phase_m) ? 0 : 1;
+        const int late = mbar_wait(&bar_mma, phase_m, spin) ? 0 : 1;
         phase_m ^= 1;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (__syncthreads_or(late)) ok = false;
@@ -413,10 +414,11 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
     }
     if (!ok && tid == 0) {
         atomicExch(err, 1);
-        // let in-flight copies and MMAs land before the shared memory goes away (bounded)
+        // let in-flight copies and MMAs land before the shared memory goes
+        // away: bounded by the full limit, whatever limit the waits above had
         for (int t = 0; t < 2; ++t)
-            if (b_pending[t]) mbar_wait(&bar_b[t], phase_b[t]);
-        if (mma_pending) mbar_wait(&bar_mma, phase_m);
+            if (b_pending[t]) mbar_wait(&bar_b[t], phase_b[t], kSpinLimit);
+        if (mma_pending) mbar_wait(&bar_mma, phase_m, kSpinLimit);
     }
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(tmem_cols));
@@ -485,7 +487,7 @@ cudaError_t launch_build_operator_tc(float* img, int64_t n3, int inverse, int sc
 template <int MODE, bool BF>
 static cudaError_t launch_tc_as(const float* in, const float* in2, float* out, const float* img, int64_t P,
                                 int64_t n3, const AdmmCtl* ctl, float* X, float* M, const float* B,
-                                const uint8_t* mask, double* partials, int* err, cudaStream_t s)
+                                const uint8_t* mask, double* partials, int* err, int spin, cudaStream_t s)
 {
     const int NP = tube_tc_np(n3), nc = tube_tc_chunks(n3);
     uint32_t cols = 32;
@@ -496,37 +498,39 @@ static cudaError_t launch_tc_as(const float* in, const float* in2, float* out, c
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)((P + TBM - 1) / TBM);
-    kern<<<grid, TTHREADS, smem, s>>>(in, in2, out, img, P, (int)n3, NP, nc, cols, ctl, X, M, B, mask, partials, err);
+    kern<<<grid, TTHREADS, smem, s>>>(in, in2, out, img, P, (int)n3, NP, nc, cols, ctl, X, M, B, mask, partials, err,
+                                      spin < 0 ? kSpinLimit : (uint32_t)spin);
     return cudaGetLastError();
 }
 
 template <int MODE>
 static cudaError_t launch_tc(bool bf, const float* in, const float* in2, float* out, const float* img, int64_t P,
                              int64_t n3, const AdmmCtl* ctl, float* X, float* M, const float* B, const uint8_t* mask,
-                             double* partials, int* err, cudaStream_t s)
+                             double* partials, int* err, int spin, cudaStream_t s)
 {
-    return bf ? launch_tc_as<MODE, true>(in, in2, out, img, P, n3, ctl, X, M, B, mask, partials, err, s)
-              : launch_tc_as<MODE, false>(in, in2, out, img, P, n3, ctl, X, M, B, mask, partials, err, s);
+    return bf ? launch_tc_as<MODE, true>(in, in2, out, img, P, n3, ctl, X, M, B, mask, partials, err, spin, s)
+              : launch_tc_as<MODE, false>(in, in2, out, img, P, n3, ctl, X, M, B, mask, partials, err, spin, s);
 }
 
 cudaError_t launch_tube_tc(const float* X, float* Y, const float* img, int64_t P, int64_t n3, bool bf, int* err,
-                           cudaStream_t s)
+                           cudaStream_t s, int spin)
 {
-    return launch_tc<0>(bf, X, nullptr, Y, img, P, n3, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, err, s);
+    return launch_tc<0>(bf, X, nullptr, Y, img, P, n3, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, err, spin,
+                        s);
 }
 
 cudaError_t launch_tube_tc_fwd_admm(const float* X, const float* M, float* Zbar, const float* img, int64_t P, int64_t n3,
-                                    bool bf, const AdmmCtl* ctl, int* err, cudaStream_t s)
+                                    bool bf, const AdmmCtl* ctl, int* err, cudaStream_t s, int spin)
 {
-    return launch_tc<1>(bf, X, M, Zbar, img, P, n3, ctl, nullptr, nullptr, nullptr, nullptr, nullptr, err, s);
+    return launch_tc<1>(bf, X, M, Zbar, img, P, n3, ctl, nullptr, nullptr, nullptr, nullptr, nullptr, err, spin, s);
 }
 
 cudaError_t launch_tube_tc_inv_admm(const float* Ybar, float* X, float* M, const float* B, const uint8_t* mask,
                                     const float* img, int64_t P, int64_t n3, bool bf, const AdmmCtl* ctl,
-                                    double* partials, int* nblocks, int* err, cudaStream_t s)
+                                    double* partials, int* nblocks, int* err, cudaStream_t s, int spin)
 {
     *nblocks = tube_tc_partials_count(P);
-    return launch_tc<2>(bf, Ybar, nullptr, nullptr, img, P, n3, ctl, X, M, B, mask, partials, err, s);
+    return launch_tc<2>(bf, Ybar, nullptr, nullptr, img, P, n3, ctl, X, M, B, mask, partials, err, spin, s);
 }
 
 }  // namespace tnn

@@ -25,6 +25,7 @@ if not _os.path.exists(LIB_PATH):
 _lib = _ct.CDLL(LIB_PATH)
 
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ENONFINITE, ENODEV = range(7)
+OPT_JACOBI_MAX_SWEEPS, OPT_TC_WAIT_POLLS = 1, 2
 PRECISIONS = {"fp64": 0, "fp32": 1, "tf32x3": 2, "bf16split": 3}
 OP_TDCT3, OP_TSVT, OP_TSVD, OP_TPROD, OP_COMPLETE = range(5)
 
@@ -59,6 +60,8 @@ _lib.tnn_last_error.argtypes = [_vp]
 _lib.tnn_last_error.restype = _ct.c_char_p
 _lib.tnn_reserve.argtypes = [_vp, _ct.c_size_t]
 _lib.tnn_reserve.restype = _st
+_lib.tnn_set_option.argtypes = [_vp, _ct.c_int, _ct.c_int64]
+_lib.tnn_set_option.restype = _st
 _lib.tnn_workspace_size.argtypes = [_vp, _ct.c_int, Shape, _ct.c_int, _ct.POINTER(_ct.c_size_t)]
 _lib.tnn_workspace_size.restype = _st
 _lib.tdct3.argtypes = [_vp, _vp, Shape, _ct.c_int, _ct.c_int, _ct.c_int, _vp, _vp]
@@ -164,7 +167,8 @@ _lib.tsvt_dft.restype = _st
 _lib.tsvt_dct_plain.argtypes = [_vp, _vp, Shape, _ct.c_double, _ct.c_int, _vp, _ct.POINTER(_ct.c_double), _vp]
 _lib.tsvt_dct_plain.restype = _st
 
-EXPORTS = ["tnn_create", "tnn_destroy", "tnn_status_string", "tnn_last_error", "tnn_reserve", "tnn_workspace_size",
+EXPORTS = ["tnn_create", "tnn_destroy", "tnn_status_string", "tnn_last_error", "tnn_reserve", "tnn_set_option",
+           "tnn_workspace_size",
            "tdct3", "tsvt_dct", "tsvd_dct_forward", "tsvd_dct_inverse", "tprod_dct", "tnn_complete",
            "tnn_admm_iterate", "tnn_last_jacobi_stats", "tnn_profile", "tnn_profile_read", "tsvt_dct_static",
            "tnn_tsvt_batch_create", "tnn_tsvt_batch_run", "tnn_tsvt_batch_info", "tnn_tsvt_batch_group",
@@ -322,6 +326,10 @@ class Context:
 
     def reserve(self, nbytes):
         self._chk(_lib.tnn_reserve(self._h, int(nbytes)), "tnn_reserve")
+
+    def set_option(self, option, value):
+        """tnn_set_option: OPT_JACOBI_MAX_SWEEPS or OPT_TC_WAIT_POLLS."""
+        self._chk(_lib.tnn_set_option(self._h, int(option), int(value)), "tnn_set_option")
 
     def workspace_size(self, op, shape, prec="fp32"):
         out = _ct.c_size_t(0)

@@ -34,12 +34,15 @@ WORKLOADS = {
     "msi": ("admm_msi_128x128x31.json", lambda: inputs.config3(n1=128, n2=128),
             "multispectral-shaped window 128x128x31, 10% observed, beta0=1e-4, rho=1.1, beta_max=1e10, tol=1e-8, "
             "max_iter=150 (seeded inputs of paper_1902_03070_gb300.inputs.config3(n1=128, n2=128))"),
+    "msi512": ("admm_msi_512x512x31.json", lambda: inputs.config3(),
+               "multispectral-shaped 512x512x31, 10% observed, beta0=1e-4, rho=1.1, beta_max=1e10, tol=1e-8, "
+               "max_iter=150 (seeded inputs of paper_1902_03070_gb300.inputs.config3())"),
 }
 
 
 def main():
     threads = int(sys.argv[1]) if len(sys.argv) > 1 else len(os.sched_getaffinity(0))
-    names = sys.argv[2:] or list(WORKLOADS)
+    names = sys.argv[2:] or ["video", "msi"]
     for name in names:
         fname, make, desc = WORKLOADS[name]
         d = make()
@@ -50,6 +53,13 @@ def main():
                "rel_err_vs_ground_truth": err, "iters": rep["iters"], "rel_change": rep["rel_change"],
                "primal_res": rep["primal_res"], "beta_final": rep["beta_final"], "converged": rep["converged"],
                "oracle_seconds": time.time() - t0, "threads": threads}
+        if name == "msi512":
+            # the oracle's final X at seeded positions, for an elementwise check
+            # of sampled outputs of the full-size run
+            idx = np.sort(np.random.default_rng(1902_03070).choice(X.size, size=512, replace=False))
+            out["sample_index"] = [int(i) for i in idx]
+            out["sample_x"] = [float(v) for v in X.ravel(order="F")[idx]]
+            out["norm_x"] = float(np.linalg.norm(X))
         with open(os.path.join(HERE, fname), "w") as f:
             json.dump(out, f, indent=1)
         print(json.dumps(out))

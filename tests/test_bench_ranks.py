@@ -57,3 +57,18 @@ def test_single_rank_is_unchanged():
     import bench
     assert bench.max_over_ranks(12.5, 1, None, "cpu") == 12.5
     assert abs(bench.job_rate(1, 100, 197, 400.0) - 100 * 197 / 0.4) < 1e-9
+
+
+def test_timed_window_is_the_jobs_last_iterations():
+    sys.path.insert(0, ROOT)
+    import bench
+    # the driver's --steps 20 --warmup 5: prefix 0-174 untimed, warm-up 175-179, timed 180-199
+    assert bench.window(20, 5) == {"start": 180, "prefix": 175, "warm_in": 5, "warm_extra": 0}
+    # the whole job timed: the warm-up runs on a throw-away copy
+    assert bench.window(200, 5) == {"start": 0, "prefix": 0, "warm_in": 0, "warm_extra": 5}
+    assert bench.window(197, 5) == {"start": 3, "prefix": 0, "warm_in": 3, "warm_extra": 2}
+    for K in (1, 7, 20, 199, 200):
+        for W in (0, 3, 5, 250):
+            w = bench.window(K, W)
+            assert w["prefix"] + w["warm_in"] == w["start"] == bench.JOB_ITERS - K
+            assert w["warm_in"] + w["warm_extra"] == W and min(w.values()) >= 0

@@ -75,3 +75,19 @@ def test_admm_recovers_low_tubal_rank_and_certificate():
         Ur, Vr = u[:, :r], vt[:r].T
         assert np.abs(Ur.T @ Gb[:, :, k] @ Vr - np.eye(r)).max() <= 1e-6
         assert np.linalg.norm(Gb[:, :, k], 2) <= 1 + 1e-6
+
+
+def test_admm_resume_equals_one_run():
+    # Algorithm 1 continued from the state (X, M, beta) after 3 iterations
+    # gives, 2 iterations later, bit for bit the state of one 5-iteration run
+    T, B, mask = _problem(9, 11, 6, 2, 0.4, 5)
+    X5, M5, r5 = O.admm(B, mask, beta0=0.3, rho=1.3, tol=-1.0, max_iter=5)
+    X3, M3, r3 = O.admm(B, mask, beta0=0.3, rho=1.3, tol=-1.0, max_iter=3)
+    assert r3["beta_final"] == 0.3 * 1.3 * 1.3 * 1.3
+    X, M, r = O.admm(B, mask, beta0=r3["beta_final"], rho=1.3, tol=-1.0, max_iter=2, X0=X3, M0=M3)
+    assert r["iters"] == 2
+    assert np.array_equal(X, X5) and np.array_equal(M, M5)
+    assert r["beta_final"] == r5["beta_final"]
+    # the state passed in is not modified
+    X3b, M3b, _ = O.admm(B, mask, beta0=0.3, rho=1.3, tol=-1.0, max_iter=3)
+    assert np.array_equal(X3, X3b) and np.array_equal(M3, M3b)

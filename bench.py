@@ -309,6 +309,44 @@ def run_ours(args):
                "tsvt_err_over_input_norm": float(dn / np.linalg.norm(Z)), "tau": tau,
                "where": "t-SVT of Z = X - M/beta after the last iteration of the job"}
 
+    # ---- the same window with the FP32 Jacobi's rotation angles and
+    # convergence tests in FP64 (tnn_set_option TNN_OPT_JACOBI_FP64_ANGLES):
+    # its time per step, and its t-SVT at the end against the FP64 path
+    a64 = None
+    if not args.no_fp64:
+        ctx.set_option(tnn.OPT_JACOBI_FP64_ANGLES, 1)
+        try:
+            Ba, ma, Xa, Ma = fresh(torch.float32)
+            ba = ADMM["beta0"]
+            if win["start"]:
+                ba, _ = ctx.admm_iterate(Ba, ma, Xa, Ma, ba, win["start"], prm, prec=PREC)
+            msa = []
+            for _ in range(K):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ba, _ = ctx.admm_iterate(Ba, ma, Xa, Ma, ba, 1, prm, prec=PREC)
+                e1.record(stream)
+                e1.synchronize()
+                msa.append(e0.elapsed_time(e1))
+            xa = tnn.to_numpy(Xa).astype(np.float64)
+            Za = np.asfortranarray((xa - tnn.to_numpy(Ma).astype(np.float64) / ba).astype(np.float32)
+                                   .astype(np.float64))
+            Ya = tnn.fortran_empty(Za.shape, torch.float32)
+            ctx.tsvt(tnn.to_fortran(Za, device=dev, dtype=torch.float32), 1.0 / ba, Y=Ya, prec=PREC)
+            Y64a = tnn.fortran_empty(Za.shape, torch.float64)
+            ctx.set_option(tnn.OPT_JACOBI_FP64_ANGLES, 0)
+            ctx.tsvt(tnn.to_fortran(Za, device=dev, dtype=torch.float64), 1.0 / ba, Y=Y64a, prec="fp64")
+            ya, y64a = tnn.to_numpy(Ya).astype(np.float64), tnn.to_numpy(Y64a)
+            a64 = {"ms_per_step": float(np.mean(msa)), "slowdown_vs_fp32_angles": float(np.sum(msa)) / total_ms,
+                   "tsvt_rel_err_vs_fp64": float(np.linalg.norm(ya - y64a) / np.linalg.norm(y64a)),
+                   "final_x_rel_err_vs_ground_truth": float(np.linalg.norm(xa - T) / np.linalg.norm(T)),
+                   "note": "the same window, FP32 columns and dot products, FP64 angles and convergence tests"}
+            del Ba, ma, Xa, Ma
+        finally:
+            ctx.set_option(tnn.OPT_JACOBI_FP64_ANGLES, 0)
+
     # ---- plain FP64 GPU path on the same workload and the same iterations
     # (its own run of the job: untimed prefix, then the same K timed
     # iterations; FP64 data, transforms and Jacobi), and the two runs' final
@@ -427,7 +465,7 @@ def run_ours(args):
         "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
         "roofline": roof, "transform_roofline": tr, "jacobi_window": jw,
         "kernels_ms": {k: v[0] for k, v in prof.items()},
-        "gpu_launches": launches, "clocks": clk, "e2e": e2e, "fp64_plain": fp64, "accuracy": acc,
+        "gpu_launches": launches, "clocks": clk, "e2e": e2e, "fp64_plain": fp64, "accuracy": acc, "fp64_angles": a64,
         "cpu_baseline": cpu, "other_workloads": nxt,
         "peaks_file": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained")},
     }
@@ -455,7 +493,7 @@ def timed(fn, reps, flush, stream, torch):
     return ms
 
 
-def next_legs(ctx, torch, dev, flush, serve):
+def next_legs(ctx, torch, dev, flush, streams):
     """Batched uneven t-SVT (64 tensors, n1, n2 in [32, 256], n3 in [8, 64],
     FP32, one graph launch, autotuned) against the per-tensor loop; the
     512 x 512 x 31 multispectral-shaped t-SVT (BF16-split transforms, slices
@@ -521,6 +559,54 @@ def next_legs(ctx, torch, dev, flush, serve):
         "note": "iterations 4-13 of the batch; the loop runs one tnn_admm_iterate (one iteration, host sync) per "
                 "tensor"}
     del Zd, Yd, Bd, md, Xd, Md
+    # ---- whole completions: the 48 x 48 x 16 tubal-rank-3 workload (FP64,
+    # and the FP32 forms), against the oracle on the host cores, and the full
+    # 512 x 512 x 31 multispectral-shaped one (BF16-split and 3xTF32
+    # transforms; the oracle's 46-minute run is the stored golden; the
+    # oracle's own 48 x 48 x 16 run is timed in the CPU-baseline leg)
+    c1 = inputs.config1(tp)
+    comp = {}
+    for prec in ("fp64", "fp32", "tf32x3", "bf16split"):
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        Bc = tnn.to_fortran(c1["B"], device=dev, dtype=dt)
+        mc = tnn.to_fortran(c1["mask"], device=dev)
+        Xc = tnn.fortran_empty(c1["B"].shape, dt, device=dev)
+        ctx.complete(Bc, mc, Xc, ctx.params(**{**c1["admm"], "max_iter": 3}), prec=prec)  # warm
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, rep = ctx.complete(Bc, mc, Xc, ctx.params(**c1["admm"]), prec=prec)
+        el = time.perf_counter() - t0
+        x = tnn.to_numpy(Xc).astype(np.float64)
+        comp[prec] = {"seconds": el, "iters": rep["iters"], "admm_iters_per_s": rep["iters"] / el,
+                      "tsvt_slices_per_s": 16 * rep["iters"] / el,
+                      "rel_err_vs_ground_truth": float(np.linalg.norm(x - c1["T"]) / np.linalg.norm(c1["T"]))}
+    out["completion_48x48x16"] = dict(comp, workload="48x48x16 tubal rank 3 (DCT t-product of N(0,1) factors), 40% "
+                                                     "observed, beta0=1e-4, rho=1.1, tol 1e-8, <= 300 iterations; "
+                                                     "whole tnn_complete calls on device buffers")
+    c3 = inputs.config3()
+    try:
+        gold = json.load(open(os.path.join(ROOT, "tests", "golden", "admm_msi_512x512x31.json")))
+    except (OSError, ValueError):
+        gold = {}
+    comp = {}
+    for prec in ("bf16split", "tf32x3"):
+        Bc = tnn.to_fortran(c3["B"], device=dev, dtype=torch.float32)
+        mc = tnn.to_fortran(c3["mask"], device=dev)
+        Xc = tnn.fortran_empty(c3["B"].shape, torch.float32, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, rep = ctx.complete(Bc, mc, Xc, ctx.params(**c3["admm"]), prec=prec)
+        el = time.perf_counter() - t0
+        x = tnn.to_numpy(Xc).astype(np.float64)
+        comp[prec] = {"seconds": el, "iters": rep["iters"], "admm_iters_per_s": rep["iters"] / el,
+                      "tsvt_slices_per_s": 31 * rep["iters"] / el,
+                      "rel_err_vs_ground_truth": float(np.linalg.norm(x - c3["T"]) / np.linalg.norm(c3["T"]))}
+        del Bc, mc, Xc
+    comp["oracle"] = {"rel_err_vs_ground_truth": gold.get("rel_err_vs_ground_truth"),
+                      "seconds": gold.get("oracle_seconds"), "threads": gold.get("threads"),
+                      "note": "the stored oracle run (tests/golden), not timed here"}
+    out["completion_msi_512x512x31"] = dict(comp, workload="512x512x31 multispectral-shaped, 10% observed, "
+                                                           "150 iterations; whole tnn_complete calls")
     # ---- multispectral-shaped t-SVT
     d = inputs.config3()
     Z = d["T"]
@@ -572,7 +658,7 @@ def next_legs(ctx, torch, dev, flush, serve):
     # GPU completes: latency is queueing), a stream under capacity (latency
     # is service time), and a prefix of the first with the FP32 and FP64
     # jobs' iterations batched
-    jobs = serve.make_stream(serve["jobs"], 200.0, tprod=tp)
+    jobs = serve.make_stream(streams["jobs"], 200.0, tprod=tp)
     _, summ = serve.run(jobs, streams=8, chunk=8, max_active=8, policy=1, timeout_s=1500.0)
     summ.update({"rate_jobs_per_s": 200.0, "policy": "shortest estimated work first, at most 8 running",
                  "note": "the offered load is far above what one GPU completes: latency is queueing"})
@@ -584,10 +670,10 @@ def next_legs(ctx, torch, dev, flush, serve):
                                                      "iteration)" % nb})
     out["serving_batched"] = summ
     del jobs
-    if serve["jobs_low"] > 0:
-        jobs = serve.make_stream(serve["jobs_low"], serve["rate_low"], seed=1902_03076, tprod=tp)
+    if streams["jobs_low"] > 0:
+        jobs = serve.make_stream(streams["jobs_low"], streams["rate_low"], seed=1902_03076, tprod=tp)
         _, summ = serve.run(jobs, streams=8, chunk=8, max_active=8, policy=1, timeout_s=1500.0)
-        summ.update({"rate_jobs_per_s": serve["rate_low"], "policy": "shortest estimated work first, at most 8 "
+        summ.update({"rate_jobs_per_s": streams["rate_low"], "policy": "shortest estimated work first, at most 8 "
                                                                      "running",
                      "note": "offered load under capacity: latency is service time"})
         out["serving_low_rate"] = summ
@@ -634,10 +720,21 @@ def oracle_window(K, W, nthreads):
 
 
 def oracle_baseline(K, W):
-    """The CPU oracle's rate on the timed iterations (all host cores)."""
+    """The CPU oracle's rate on the timed iterations (all host cores), and
+    its whole 48 x 48 x 16 completion beside it."""
+    import oracle as O
+    from paper_1902_03070_gb300 import inputs
     times, got, win = oracle_window(K, W, len(os.sched_getaffinity(0)))
     tot = float(np.sum(times))
+    c1 = inputs.config1(O.tprod)
+    t0 = time.perf_counter()
+    Xo, _, rep_o = O.admm(c1["B"], c1["mask"], nthreads=got, **c1["admm"])
+    el = time.perf_counter() - t0
+    c1_out = {"seconds": el, "iters": rep_o["iters"], "admm_iters_per_s": rep_o["iters"] / el,
+              "tsvt_slices_per_s": 16 * rep_o["iters"] / el, "threads": got,
+              "rel_err_vs_ground_truth": float(np.linalg.norm(Xo - c1["T"]) / np.linalg.norm(c1["T"]))}
     return {"value": win * K / tot, "unit": "slices/s", "cores": got, "kind": "oracle",
+            "completion_48x48x16": c1_out,
             "sample": "oracle ADMM iterations %d-%d of the job on a 144x176x%d frame window (its own completion "
                       "problem; prefix untimed), %d threads, %.1f s timed" % (JOB_ITERS - K, JOB_ITERS - 1, win, got,
                                                                             tot)}

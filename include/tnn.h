@@ -130,9 +130,18 @@ tnn_status tnn_reserve(tnn_ctx* ctx, size_t bytes);
  *   return; the next call that checks the flag returns TNN_ECUDA and clears
  *   it.  For exercising that path; the output of a call that timed out is
  *   undefined.
+ * TNN_OPT_JACOBI_FP64_ANGLES: 1 = the FP32 Jacobi SVT of tsvt_dct,
+ *   tnn_complete and tnn_admm_iterate computes each pair's convergence test
+ *   and rotation (Rutishauser's angle and the scaled-rotation factors) in
+ *   FP64 from its FP32 dot products, for slices whose working copy fits in
+ *   one CTA's shared memory (larger slices keep the FP32 form); 0 (default)
+ *   = in FP32.  The columns, the dot products and the rotations applied stay
+ *   FP32.  (Measured on the video-shaped workload: about 5x the time per
+ *   iteration for errors within 1.2x of the FP32 form's.)
  * Returns TNN_EINVAL for an unknown option or a value out of range. */
 #define TNN_OPT_JACOBI_MAX_SWEEPS 1
 #define TNN_OPT_TC_WAIT_POLLS 2
+#define TNN_OPT_JACOBI_FP64_ANGLES 3
 tnn_status tnn_set_option(tnn_ctx* ctx, int option, int64_t value);
 
 enum { TNN_OP_TDCT3 = 0, TNN_OP_TSVT = 1, TNN_OP_TSVD = 2, TNN_OP_TPROD = 3, TNN_OP_COMPLETE = 4 };

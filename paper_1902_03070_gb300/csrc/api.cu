@@ -27,6 +27,7 @@ struct tnn_ctx {
     int* d_err = nullptr;        // set by a tensor-core kernel whose bounded wait timed out
     int opt_jacobi_sweeps = 0;   // TNN_OPT_JACOBI_MAX_SWEEPS (0: the kernels' default)
     int opt_tc_polls = -1;       // TNN_OPT_TC_WAIT_POLLS (negative: the default limit)
+    int opt_angle64 = 0;         // TNN_OPT_JACOBI_FP64_ANGLES
     SliceStats* last_stats = nullptr;
     int64_t last_n3 = 0;
     cudaStream_t last_stream = nullptr;
@@ -327,6 +328,10 @@ tnn_status tnn_set_option(tnn_ctx* ctx, int option, int64_t value)
         if (value > (int64_t)1 << 30) return fail(ctx, TNN_EINVAL, "poll limit %lld out of range", (long long)value);
         ctx->opt_tc_polls = value < 0 ? -1 : (int)value;
         return TNN_OK;
+    case TNN_OPT_JACOBI_FP64_ANGLES:
+        if (value != 0 && value != 1) return fail(ctx, TNN_EINVAL, "FP64-angle flag must be 0 or 1");
+        ctx->opt_angle64 = (int)value;
+        return TNN_OK;
     default: return fail(ctx, TNN_EINVAL, "unknown option %d", option);
     }
 }
@@ -485,6 +490,7 @@ tnn_status tsvt_dct(tnn_ctx* ctx, const void* Z, tnn_shape sh, double tau, tnn_p
     JacobiPlan jp;
     if (!jacobi_plan(sh.n1, sh.n2, sh.n3, elem, &jp)) return fail(ctx, TNN_EINVAL, "slice %lldx%lld too large",
                                                                 (long long)sh.n1, (long long)sh.n2);
+    jp.angle64 = ctx->opt_angle64;
     const size_t bytes = (size_t)sh.n1 * sh.n2 * sh.n3 * elem;
     Arg az = make_arg(Z, bytes), ay = make_arg(Y, bytes);
     Carve cv;
@@ -809,6 +815,7 @@ tnn_status tnn_complete(tnn_ctx* ctx, const void* B, const uint8_t* mask, tnn_sh
     const int elem = elem_of(prec);
     JacobiPlan jp;
     if (!jacobi_plan(sh.n1, sh.n2, sh.n3, elem, &jp)) return fail(ctx, TNN_EINVAL, "slice too large");
+    jp.angle64 = ctx->opt_angle64;
     const size_t N = (size_t)sh.n1 * sh.n2 * sh.n3, bytes = N * elem;
     Arg ab = make_arg(B, bytes), am = make_arg(mask, N), ax = make_arg(X_out, bytes);
     const int nparts = tube_partials_count(sh.n1 * sh.n2, sh.n3);
@@ -853,6 +860,7 @@ tnn_status tnn_admm_iterate(tnn_ctx* ctx, const void* B, const uint8_t* mask, tn
     const int elem = elem_of(prec);
     JacobiPlan jp;
     if (!jacobi_plan(sh.n1, sh.n2, sh.n3, elem, &jp)) return fail(ctx, TNN_EINVAL, "slice too large");
+    jp.angle64 = ctx->opt_angle64;
     const size_t N = (size_t)sh.n1 * sh.n2 * sh.n3, bytes = N * elem;
     Arg ab = make_arg(B, bytes), am = make_arg(mask, N), ax = make_arg(X, bytes), amm = make_arg(M, bytes);
     const int nparts = tube_partials_count(sh.n1 * sh.n2, sh.n3);

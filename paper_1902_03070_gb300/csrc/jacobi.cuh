@@ -169,6 +169,7 @@ struct Counters {
     int pairs;
     int rots;
     int big;
+    int bigll;  // the part of big whose two columns both had squared norms below tau^2
 };
 
 // Registers of one group: 2K columns of A (and of V when WITHV), with the
@@ -213,6 +214,56 @@ __device__ __forceinline__ void rot_params(T ai, T aj, T gam, T& t, T& c)
     c = y;
 }
 
+// Factors of the scaled rotation for tangent t: t1 = t d_j / d_i, t2 = t d_i /
+// d_j and c = 1 / sqrt(1 + t^2).  The angle t itself need not be accurate
+// (any t gives an orthogonal rotation), but c must belong to the t that is
+// applied and t1, t2 must match the scales: an error there is a column scaling
+// that builds up in d over the thousands of rotations a column takes part in,
+// and d |s| is the singular value the shrinkage uses.  FP32: the hardware's
+// approximate reciprocal and reciprocal square root, each refined by one
+// Newton step written with FMAs (r <- r + r (1 - x r), y <- y + y (1/2 - x/2
+// y^2)), which brings them to about one unit in the last place; the approximate
+// forms alone leave a few units, and the drift of the singular values they
+// cause (a few 1e-5 relative to Y where tau is large) is what FP64 angles
+// remove.  FP64: the IEEE reciprocal.
+__device__ __forceinline__ void rot_factors(float t, float di, float dj, float& t1, float& t2, float& c)
+{
+    float ri = rcp(di), rj = rcp(dj);
+    ri = fmaf(ri, fmaf(-di, ri, 1.0f), ri);
+    rj = fmaf(rj, fmaf(-dj, rj, 1.0f), rj);
+    t1 = (t * dj) * ri;
+    t2 = (t * di) * rj;
+    const float x = fmaf(t, t, 1.0f);
+    float y = rsqrtf(x);
+    y = fmaf(y, fmaf(-0.5f * x * y, y, 0.5f), y);
+    c = y;
+}
+__device__ __forceinline__ void rot_factors(double t, double di, double dj, double& t1, double& t2, double& c)
+{
+    const double rd = rcp(di * dj);
+    t1 = t * (dj * dj) * rd;
+    t2 = t * (di * di) * rd;
+    c = 1.0 / sqrt(fma(t, t, 1.0));
+}
+
+// The same rotation evaluated in FP64 (from FP32 or FP64 column sums): the
+// FP64-angle option of the FP32 kernels.
+__device__ __forceinline__ void rot_params64(double ai, double aj, double gam, double& t, double& c)
+{
+    const double D = aj - ai, g2 = gam + gam;
+    const double h = sqrt(fma(D, D, g2 * g2));
+    t = g2 / (D + copysign(h, D));
+    c = 1.0 / sqrt(fma(t, t, 1.0));
+}
+
+// Relative off-diagonality |gam| / sqrt(ai aj) of a pair in FP64; NaN (no
+// rotation) for a zero column or a carried norm gone negative, as in the
+// FP32 form.
+__device__ __forceinline__ double off64(double ai, double aj, double gam)
+{
+    return (ai > 0.0 && aj > 0.0) ? fabs(gam) / sqrt(ai * aj) : __longlong_as_double(0x7ff8000000000000ll);
+}
+
 template <typename T, int K, int R, int L, bool WITHV>
 __device__ __forceinline__ void recompute_norm(Regs<T, K, R, WITHV>& S, int c)
 {
@@ -230,7 +281,7 @@ __device__ __forceinline__ void recompute_norm(Regs<T, K, R, WITHV>& S, int c)
 // sweep's set of small columns); a pair of two flagged columns is left alone.
 template <typename T, int K, int R, int L, bool WITHV, bool CROSS, int r>
 __device__ __forceinline__ void do_round(Regs<T, K, R, WITHV>& S, const T tol, const int hl, Counters& cnt,
-                                         const unsigned lm)
+                                         const unsigned lm, const bool a64, const T tau2)
 {
     constexpr int G = L / K;
     const int slot = hl / G;
@@ -256,17 +307,30 @@ __device__ __forceinline__ void do_round(Regs<T, K, R, WITHV>& S, const T tol, c
     }
     const T gam = (di * dj) * gs;
     T t1 = T(0), t2 = T(0), cc = T(1), tg = T(0);
-    const T off = lo ? T(0) : fabs(gam) * rsqrt(ai) * rsqrt(aj);
-    const bool bigp = off > T(2) * tol;
-    // false for a zero column (0 * inf = NaN) and for a carried norm gone negative
-    if (off > tol) {
-        T t, c;
-        rot_params(ai, aj, gam, t, c);
-        const T rd = rcp(di * dj);
-        t1 = t * (dj * dj) * rd;
-        t2 = t * (di * di) * rd;
-        cc = c;
-        tg = t * gam;
+    bool bigp, rotp;
+    if (a64) {
+        const double off = lo ? 0.0 : off64((double)ai, (double)aj, (double)gam);
+        bigp = off > 2.0 * (double)tol;
+        rotp = off > (double)tol;
+    } else {
+        const T off = lo ? T(0) : fabs(gam) * rsqrt(ai) * rsqrt(aj);
+        bigp = off > T(2) * tol;
+        rotp = off > tol;  // false for a zero column (0 * inf = NaN) and for a carried norm gone negative
+    }
+    if (rotp) {
+        if (a64) {
+            double t, c;
+            rot_params64((double)ai, (double)aj, (double)gam, t, c);
+            t1 = (T)(t * ((double)dj / (double)di));
+            t2 = (T)(t * ((double)di / (double)dj));
+            cc = (T)c;
+            tg = (T)(t * (double)gam);
+        } else {
+            T t, c;
+            rot_params(ai, aj, gam, t, c);
+            rot_factors(t, di, dj, t1, t2, cc);
+            tg = t * gam;
+        }
     }
     T T1[K], T2[K], CC[K], TG[K];
 #pragma unroll
@@ -276,7 +340,10 @@ __device__ __forceinline__ void do_round(Regs<T, K, R, WITHV>& S, const T tol, c
         CC[q] = __shfl_sync(FULL, cc, q * G, L);
         TG[q] = __shfl_sync(FULL, tg, q * G, L);
     }
-    if (bigp && hl % G == 0) ++cnt.big;
+    if (bigp && hl % G == 0) {
+        ++cnt.big;
+        if (ai < tau2 && aj < tau2) ++cnt.bigll;
+    }
     if (hl == 0) cnt.pairs += K;
     unsigned need = 0;
 #pragma unroll
@@ -330,7 +397,7 @@ struct Slot {
 // (t1, t2) by shuffles.
 template <typename T, int K, int R, int L, bool WITHV, int r>
 __device__ __forceinline__ void cross_round(Regs<T, K, R, WITHV>& S, Slot<T>& st, const T tol, const int hl,
-                                            Counters& cnt, const unsigned lm)
+                                            Counters& cnt, const unsigned lm, const bool a64, const T tau2)
 {
     constexpr int G = L / K;
     const int slot = hl / G;
@@ -345,16 +412,35 @@ __device__ __forceinline__ void cross_round(Regs<T, K, R, WITHV>& S, Slot<T>& st
     T t1 = T(0), t2 = T(0);
     bool needI = false, needJ = false;
     const unsigned lo = (lm >> slot) & (lm >> (K + (slot + r) % K)) & 1u;
-    const T off = lo ? T(0) : fabs(gam) * rsqrt(st.aI) * rsqrt(st.aJ);
-    if (off > T(2) * tol && hl % G == 0) ++cnt.big;
-    // false for a zero column (0 * inf = NaN) and for a carried norm gone negative
-    if (off > tol) {
-        T t, c;
-        rot_params(st.aI, st.aJ, gam, t, c);
-        const T rd = rcp(st.dI * st.dJ);
-        t1 = t * (st.dJ * st.dJ) * rd;
-        t2 = t * (st.dI * st.dI) * rd;
-        const T tg = t * gam;
+    bool bigp, rotp;
+    if (a64) {
+        const double off = lo ? 0.0 : off64((double)st.aI, (double)st.aJ, (double)gam);
+        bigp = off > 2.0 * (double)tol;
+        rotp = off > (double)tol;
+    } else {
+        const T off = lo ? T(0) : fabs(gam) * rsqrt(st.aI) * rsqrt(st.aJ);
+        bigp = off > T(2) * tol;
+        rotp = off > tol;  // false for a zero column (0 * inf = NaN) and for a carried norm gone negative
+    }
+    if (bigp && hl % G == 0) {
+        ++cnt.big;
+        if (st.aI < tau2 && st.aJ < tau2) ++cnt.bigll;
+    }
+    if (rotp) {
+        T c, tg;
+        if (a64) {
+            double td, cd;
+            rot_params64((double)st.aI, (double)st.aJ, (double)gam, td, cd);
+            t1 = (T)(td * ((double)st.dJ / (double)st.dI));
+            t2 = (T)(td * ((double)st.dI / (double)st.dJ));
+            c = (T)cd;
+            tg = (T)(td * (double)gam);
+        } else {
+            T t;
+            rot_params(st.aI, st.aJ, gam, t, c);
+            rot_factors(t, st.dI, st.dJ, t1, t2, c);
+            tg = t * gam;
+        }
         const T oI = st.aI, oJ = st.aJ;
         st.aI = oI - tg;
         st.aJ = oJ + tg;
@@ -426,16 +512,18 @@ __device__ __forceinline__ void cross_round(Regs<T, K, R, WITHV>& S, Slot<T>& st
 
 template <typename T, int K, int R, int L, bool WITHV, int... Rs>
 __device__ __forceinline__ void cross_rounds(Regs<T, K, R, WITHV>& S, Slot<T>& st, const T tol, const int hl,
-                                             Counters& cnt, std::integer_sequence<int, Rs...>, const unsigned lm = 0u)
+                                             Counters& cnt, std::integer_sequence<int, Rs...>, const unsigned lm = 0u,
+                                             const bool a64 = false, const T tau2 = T(0))
 {
-    (cross_round<T, K, R, L, WITHV, Rs>(S, st, tol, hl, cnt, lm), ...);
+    (cross_round<T, K, R, L, WITHV, Rs>(S, st, tol, hl, cnt, lm, a64, tau2), ...);
 }
 
 template <typename T, int K, int R, int L, bool WITHV, bool CROSS, int... Rs>
 __device__ __forceinline__ void do_rounds(Regs<T, K, R, WITHV>& S, const T tol, const int hl, Counters& cnt,
-                                          std::integer_sequence<int, Rs...>, const unsigned lm = 0u)
+                                          std::integer_sequence<int, Rs...>, const unsigned lm = 0u,
+                                          const bool a64 = false, const T tau2 = T(0))
 {
-    (do_round<T, K, R, L, WITHV, CROSS, Rs>(S, tol, hl, cnt, lm), ...);
+    (do_round<T, K, R, L, WITHV, CROSS, Rs>(S, tol, hl, cnt, lm, a64, tau2), ...);
 }
 
 // Load the 2K columns of blocks bI, bJ into the group's registers and the
@@ -643,7 +731,9 @@ struct Bound {
     static constexpr int value = t > 1024 ? 1024 : t;
 };
 
-template <typename T, int K, int R, int L, bool SMEM, bool WITHV, bool ITEMS = false>
+// A64: the FP32 rotation angles and convergence tests in FP64 (a separate
+// instantiation, so the default kernels carry no FP64 code).
+template <typename T, int K, int R, int L, bool SMEM, bool WITHV, bool ITEMS = false, bool A64 = false>
 __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KArgs<T> a)
 {
     if (a.ctl && a.ctl->done) return;
@@ -686,8 +776,8 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
     int* kidx = reinterpret_cast<int*>(anorm + npad);
     int* rank = kidx + npad;
     T* gbuf = reinterpret_cast<T*>(rank + npad);
-    __shared__ int s_rot, s_keep, s_nonfinite, s_nlo;
-    __shared__ double s_nuc, s_fro, s_lo, s_s1;
+    __shared__ int s_rot, s_rotll, s_keep, s_nonfinite, s_nlo, s_cnt;
+    __shared__ double s_nuc, s_fro, s_lo, s_s1, s_yn;
     __shared__ unsigned long long s_maxb;  // bits of a nonnegative double (ordered as integers)
     __shared__ unsigned long long s_pairs, s_rots;
 
@@ -744,6 +834,7 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
     // columns' alphas still sum below tau^2 (a rotation with a column that
     // has shrunk below them can grow them); otherwise full sweeps follow.
     const T tol = sqrt((T)m) * Num<T>::unit();
+    constexpr bool a64 = A64 && sizeof(T) == 4;
     Counters cnt{0, 0, 0};
     int sweeps = 0, converged = skip ? 1 : 0;
     const int max_sweeps = a.max_sweeps > 0 ? a.max_sweeps : 30;
@@ -753,6 +844,100 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
     bool full_only = WITHV;
     int cert_left = WITHV ? 0 : 2;  // zero-SVT certificate attempts (below)
     int* loflag = kidx;  // free until the rebuild
+    const T tau2 = (T)(tau_s * tau_s);
+    bool gmode = false;           // low block certified (below): pairs of two low columns are left alone
+    int gm_left = WITHV ? 0 : 4;  // low-block certificate attempts
+
+    // Low-block certificate (SVT).  The columns whose squared norms are
+    // below tau^2 form a block S_L whose singular values the SVT discards as
+    // long as they are at most tau.  By Gershgorin on its Gram matrix
+    // G = S_L^T S_L, sigma_max(S_L)^2 <= max_i sum_{j in L} |G_ij|.  The bound,
+    // with the rounding of the computed G (|dG_ij| <= m u |a_i| |a_j|) and of
+    // the row sums added as for the zero-SVT certificate, is accepted if it is
+    // at most (tau + eps)^2 with eps = 1e-7 ||Y_slice|| (estimated from the
+    // other columns' norms): a singular value of S_L above tau by at most eps
+    // would change Y by at most eps.  Once certified, pairs of two low columns
+    // are left alone; a sweep without rotation ends the iteration only if the
+    // certificate still holds on the current columns.  Columns of S_L are
+    // listed in rank[] (free in the SVT).
+    auto low_cert = [&](const bool zero) -> bool {
+        if (tid == 0) { s_cnt = 0; s_maxb = 0ull; s_s1 = 0.0; s_yn = 0.0; }
+        __syncthreads();
+        double yn = 0.0, s1 = 0.0;
+        for (int c = tid; c < n; c += nthr) {
+            const double an = (double)anorm[c];
+            if (an < tau_s * tau_s) {
+                rank[atomicAdd(&s_cnt, 1)] = c;
+                s1 += sqrt(fmax(an, 0.0));
+            } else {
+                const double e = sqrt(an) - tau_s;
+                yn += e * e;
+            }
+        }
+        yn = group_sum<32>(yn);
+        s1 = group_sum<32>(s1);
+        if (lane == 0) {
+            if (yn != 0.0) atomicAdd(&s_yn, yn);
+            if (s1 != 0.0) atomicAdd(&s_s1, s1);
+        }
+        __syncthreads();
+        const int nl = s_cnt;
+        const double S1 = 1.01 * s_s1;
+        // zero: the zero-SVT certificate below (every column in the set, bound below tau^2)
+        const double lim = zero ? (1.0 - 1e-4) * tau_s * tau_s
+                                : (tau_s + 1e-7 * sqrt(s_yn)) * (tau_s + 1e-7 * sqrt(s_yn));
+        constexpr int RG = (R * L + 31) / 32;  // rows per lane (lane-strided; rows past L R are padding)
+        const double uu = (double)Num<T>::unit();
+        double wmax = 0.0;
+        for (int i0 = 2 * warp; i0 < nl; i0 += 2 * W) {
+            const int c0 = rank[i0], c1 = rank[i0 + 1 < nl ? i0 + 1 : i0];
+            T x0[RG], x1[RG];
+#pragma unroll
+            for (int q = 0; q < RG; ++q) {
+                const int r = q * 32 + lane;
+                x0[q] = r < ldA ? Aw[(size_t)c0 * ldA + r] : T(0);
+                x1[q] = r < ldA ? Aw[(size_t)c1 * ldA + r] : T(0);
+            }
+            T r0 = T(0), r1 = T(0);
+            for (int j0 = 0; j0 < nl; j0 += 32) {
+                T p0[32], p1[32];
+#pragma unroll
+                for (int jj = 0; jj < 32; ++jj) {
+                    p0[jj] = T(0);
+                    p1[jj] = T(0);
+                    if (j0 + jj < nl) {
+                        const T* col = Aw + (size_t)rank[j0 + jj] * ldA;
+#pragma unroll
+                        for (int q = 0; q < RG; ++q) {
+                            const int r = q * 32 + lane;
+                            const T v = r < ldA ? col[r] : T(0);
+                            p0[jj] = fma(x0[q], v, p0[jj]);
+                            p1[jj] = fma(x1[q], v, p1[jj]);
+                        }
+                    }
+                }
+                const T g0 = reduce_scatter<T, 32, 32>(p0, lane);  // lane: G(i, list[j0 + lane]) / scales
+                const T g1 = reduce_scatter<T, 32, 32>(p1, lane);
+                if (j0 + lane < nl) {
+                    const T dj = dsc[rank[j0 + lane]];
+                    r0 += fabs(g0 * dj);
+                    r1 += fabs(g1 * dj);
+                }
+            }
+            r0 = group_sum<32>(r0);
+            r1 = group_sum<32>(r1);
+            const double b0 = (double)(r0 * dsc[c0]) * (1.0 + 2.0 * nl * uu) +
+                              2.0 * m * uu * sqrt(fmax((double)anorm[c0], 0.0)) * S1;
+            const double b1 = (double)(r1 * dsc[c1]) * (1.0 + 2.0 * nl * uu) +
+                              2.0 * m * uu * sqrt(fmax((double)anorm[c1], 0.0)) * S1;
+            wmax = fmax(wmax, fmax(b0, b1));
+        }
+        if (lane == 0) atomicMax(&s_maxb, (unsigned long long)__double_as_longlong(wmax));
+        __syncthreads();
+        const bool ok = __longlong_as_double((long long)s_maxb) <= lim;
+        __syncthreads();  // the shared words are reused after this
+        return ok;
+    };
     if (!WITHV && !skip) {
         for (int c = warp; c < npad; c += W) {
             const T* col = Aw + (size_t)c * ldA;
@@ -763,10 +948,12 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
         }
     }
     while (!skip && sweeps < max_sweeps) {
-        if (tid == 0) { s_rot = 0; s_lo = 0.0; s_nlo = 0; }
+        if (tid == 0) { s_rot = 0; s_rotll = 0; s_lo = 0.0; s_nlo = 0; }
         __syncthreads();
-        if (!full_only) {
-            const double thr = 0.25 * tau_s * tau_s;
+        if (!full_only || gmode) {
+            // columns flagged: below tau^2 / 4 (small-column sweeps) or, with
+            // the low block certified, below tau^2
+            const double thr = gmode ? tau_s * tau_s : 0.25 * tau_s * tau_s;
             double part = 0.0;
             int nf = 0;
             for (int c = tid; c < npad; c += nthr) {
@@ -786,8 +973,8 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
         __syncthreads();
         // flagged sweeps only where they pay: most columns flagged (a few
         // tiny columns save nothing and can cost a closing full sweep)
-        const bool partial = !full_only && s_lo <= 0.9 * tau_s * tau_s && 2 * s_nlo >= n;
-        const int big0 = cnt.big;
+        const bool partial = gmode || (!full_only && s_lo <= 0.9 * tau_s * tau_s && 2 * s_nlo >= n);
+        const int big0 = cnt.big, bigll0 = cnt.bigll;
         // one sweep; compiled twice, so that a sweep without flagged columns
         // runs code without the flag tests
         auto sweep = [&](auto flagged) {
@@ -814,10 +1001,11 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
                     if (step == 0) {
                         gather_state<T, K, R, L, WITHV>(Sr, st);
                         do_rounds<T, K, R, L, WITHV, false>(Sr, tol, hl, cnt,
-                                                            std::make_integer_sequence<int, K - 1>{}, lm);
+                                                            std::make_integer_sequence<int, K - 1>{}, lm, a64, tau2);
                         scatter_state<T, K, R, L, WITHV>(Sr, st, hl);
                     }
-                    cross_rounds<T, K, R, L, WITHV>(Sr, st, tol, hl, cnt, std::make_integer_sequence<int, K>{}, lm);
+                    cross_rounds<T, K, R, L, WITHV>(Sr, st, tol, hl, cnt, std::make_integer_sequence<int, K>{}, lm,
+                                                    a64, tau2);
                     store_cols<T, K, R, L, WITHV>(Sr, st, Aw, Aw, Vw, dsc, dsc, ldA, bI, bJ, hl, active, anorm);
                     if (!active) cnt = cnt0;  // an inactive group's work is discarded, and so are its counts
                 }
@@ -827,11 +1015,12 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
         if (!WITHV && partial) sweep(std::true_type{});
         else sweep(std::false_type{});
         if (cnt.big != big0) atomicAdd(&s_rot, cnt.big - big0);
+        if (cnt.bigll != bigll0) atomicAdd(&s_rotll, cnt.bigll - bigll0);
         __syncthreads();
-        const int nrot = s_rot;
+        const int nrot = s_rot, nrotll = s_rotll;
         ++sweeps;
         bool done = nrot == 0;
-        if (done && partial) {
+        if (done && partial && !gmode) {
             // the flagged columns' alphas after the sweep
             if (tid == 0) s_lo = 0.0;
             __syncthreads();
@@ -842,6 +1031,17 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
             __syncthreads();
             done = s_lo <= (1.0 - 1e-3) * tau_s * tau_s;
             if (!done) full_only = true;
+        }
+        // the low-block certificate: re-checked on the current columns when a
+        // sweep that left low pairs alone ends without rotation; attempted once
+        // rotations of low pairs are at least half of a sweep's big ones
+        if (!WITHV && done && gmode) {
+            --gm_left;
+            done = low_cert(false);
+            if (!done) gmode = false;
+        } else if (!WITHV && !done && !gmode && gm_left > 0 && sweeps >= 2 && 2 * nrotll >= nrot) {
+            --gm_left;
+            gmode = low_cert(false);
         }
         // Zero-SVT certificate.  sigma_1^2 is the largest eigenvalue of the
         // Gram matrix G = S^T S of the current columns (V orthogonal), so by
@@ -854,80 +1054,17 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
         // sigma_1).  Tried after the first two sweeps only.
         if (!WITHV && !done && cert_left > 0) {
             --cert_left;
-            if (tid == 0) { s_maxb = 0ull; s_s1 = 0.0; }
+            if (tid == 0) s_maxb = 0ull;
             __syncthreads();
-            double amx = 0.0, s1 = 0.0;
-            for (int c = tid; c < n; c += nthr) {
-                const double an = fmax((double)anorm[c], 0.0);
-                amx = fmax(amx, an);
-                s1 += sqrt(an);
-            }
+            double amx = 0.0;
+            for (int c = tid; c < n; c += nthr) amx = fmax(amx, fmax((double)anorm[c], 0.0));
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) amx = fmax(amx, __shfl_xor_sync(FULL, amx, o));
-            s1 = group_sum<32>(s1);
-            if (lane == 0) {
-                atomicMax(&s_maxb, (unsigned long long)__double_as_longlong(amx));
-                if (s1 != 0.0) atomicAdd(&s_s1, s1);
-            }
+            if (lane == 0) atomicMax(&s_maxb, (unsigned long long)__double_as_longlong(amx));
             __syncthreads();
             const double amax = __longlong_as_double((long long)s_maxb);
-            const double S1 = 1.01 * s_s1;
             __syncthreads();
-            if (amax < 0.999 * tau_s * tau_s) {
-                if (tid == 0) s_maxb = 0ull;
-                __syncthreads();
-                constexpr int RG = (R * L + 31) / 32;  // rows per lane (lane-strided; rows past L R are padding)
-                const double uu = (double)Num<T>::unit();
-                double wmax = 0.0;
-                for (int i0 = 2 * warp; i0 < n; i0 += 2 * W) {
-                    const int i1 = i0 + 1 < n ? i0 + 1 : i0;
-                    T x0[RG], x1[RG];
-#pragma unroll
-                    for (int q = 0; q < RG; ++q) {
-                        const int r = q * 32 + lane;
-                        x0[q] = r < ldA ? Aw[(size_t)i0 * ldA + r] : T(0);
-                        x1[q] = r < ldA ? Aw[(size_t)i1 * ldA + r] : T(0);
-                    }
-                    T r0 = T(0), r1 = T(0);
-                    for (int j0 = 0; j0 < n; j0 += 32) {
-                        T p0[32], p1[32];
-#pragma unroll
-                        for (int jj = 0; jj < 32; ++jj) {
-                            p0[jj] = T(0);
-                            p1[jj] = T(0);
-                            const int j = j0 + jj;
-                            if (j < n) {
-                                const T* col = Aw + (size_t)j * ldA;
-#pragma unroll
-                                for (int q = 0; q < RG; ++q) {
-                                    const int r = q * 32 + lane;
-                                    const T v = r < ldA ? col[r] : T(0);
-                                    p0[jj] = fma(x0[q], v, p0[jj]);
-                                    p1[jj] = fma(x1[q], v, p1[jj]);
-                                }
-                            }
-                        }
-                        const T g0 = reduce_scatter<T, 32, 32>(p0, lane);  // lane: G(i, j0 + lane) / scales
-                        const T g1 = reduce_scatter<T, 32, 32>(p1, lane);
-                        const int j = j0 + lane;
-                        if (j < n) {
-                            const T dj = dsc[j];
-                            r0 += fabs(g0 * dj);
-                            r1 += fabs(g1 * dj);
-                        }
-                    }
-                    r0 = group_sum<32>(r0);
-                    r1 = group_sum<32>(r1);
-                    const double b0 = (double)(r0 * dsc[i0]) * (1.0 + 2.0 * n * uu) +
-                                      2.0 * m * uu * sqrt(fmax((double)anorm[i0], 0.0)) * S1;
-                    const double b1 = (double)(r1 * dsc[i1]) * (1.0 + 2.0 * n * uu) +
-                                      2.0 * m * uu * sqrt(fmax((double)anorm[i1], 0.0)) * S1;
-                    wmax = fmax(wmax, fmax(b0, b1));
-                }
-                if (lane == 0) atomicMax(&s_maxb, (unsigned long long)__double_as_longlong(wmax));
-                __syncthreads();
-                done = __longlong_as_double((long long)s_maxb) <= (1.0 - 1e-4) * tau_s * tau_s;
-            }
+            if (amax < 0.999 * tau_s * tau_s) done = low_cert(true);  // every column is in the low set
         }
         __syncthreads();
         if (done) { converged = 1; break; }

@@ -14,11 +14,14 @@ __host__ __device__ constexpr int pick_K(int elem, int R, bool withv)
     return elem == 4 ? (withv ? (R <= 8 ? 4 : 2) : 4) : (withv ? (R <= 4 ? 4 : 2) : (R <= 8 ? 4 : 2));
 }
 
-template <typename T, int K, int R, int L, bool WITHV, bool ITEMS = false>
+// A64: the FP64-angle instantiation (FP32 SVT, slice in shared memory; the
+// plan must have in_smem set).
+template <typename T, int K, int R, int L, bool WITHV, bool ITEMS = false, bool A64 = false>
 cudaError_t launch_one(const JacobiPlan& p, KArgs<T> a, cudaStream_t s)
 {
-    void (*kern)(KArgs<T>) = p.in_smem ? jacobi_kernel<T, K, R, L, true, WITHV, ITEMS>
-                                       : jacobi_kernel<T, K, R, L, false, WITHV, ITEMS>;
+    void (*kern)(KArgs<T>);
+    if constexpr (A64) kern = jacobi_kernel<T, K, R, L, true, false, false, true>;
+    else kern = p.in_smem ? jacobi_kernel<T, K, R, L, true, WITHV, ITEMS> : jacobi_kernel<T, K, R, L, false, WITHV, ITEMS>;
     cudaFuncAttributes attr;
     cudaError_t e = cudaFuncGetAttributes(&attr, kern);
     if (e != cudaSuccess) return e;
@@ -50,6 +53,18 @@ cudaError_t launch_one(const JacobiPlan& p, KArgs<T> a, cudaStream_t s)
 #define TNN_JAC_CASE_K(T, L, R, K, WITHV) \
     case L * 1000 + R * 10 + K:           \
         return jac::launch_one<T, K, R, L, WITHV>(p, a, s);
+// The FP64-angle SVT kernels (FP32, slice in shared memory).
+#define TNN_JAC_CASE_A64(T, L, R) \
+    case L * 1000 + R * 10 + jac::pick_K((int)sizeof(T), R, false): \
+        return jac::launch_one<T, jac::pick_K((int)sizeof(T), R, false), R, L, false, false, true>(p, a, s);
+#define TNN_JAC_CASE_K_A64(T, L, R, K) \
+    case L * 1000 + R * 10 + K:         \
+        return jac::launch_one<T, K, R, L, false, false, true>(p, a, s);
+namespace tnn {
+// FP32 SVT with FP64 rotation angles (jacobi_svt_f32_a64.cu), for plans with
+// angle64 and in_smem set.
+cudaError_t launch_jacobi_svt_f32_a64(const JacobiPlan& p, const jac::KArgs<float>& a, cudaStream_t s);
+}  // namespace tnn
 // The same for the batched (item-table) SVT kernels.
 #define TNN_JAC_CASE_I(T, L, R) \
     case L * 1000 + R * 10 + jac::pick_K((int)sizeof(T), R, false): \

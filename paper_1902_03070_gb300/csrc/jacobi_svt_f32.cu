@@ -14,6 +14,7 @@ cudaError_t launch_jacobi_svt<float>(const JacobiPlan& p, float* data, double ta
     a.tau = tau; a.ctl = ctl; a.max_sweeps = max_sweeps;
     a.work = reinterpret_cast<float*>(work); a.stats = stats;
     if (p.cluster > 1) return launch_jacobi_svt_cluster<float>(p, a, false, s);
+    if (p.angle64 && p.in_smem) return launch_jacobi_svt_f32_a64(p, a, s);
     switch (p.L * 1000 + p.RA * 10 + p.K) {
         TNN_JAC_CASE(float, 16, 4, false)
         TNN_JAC_CASE(float, 16, 8, false)

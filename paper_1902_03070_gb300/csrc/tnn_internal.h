@@ -126,6 +126,7 @@ struct JacobiPlan {
     size_t work_bytes; // global scratch per launch
     int elem;          // sizeof(T)
     int cluster;       // > 1: each slice spread over a cluster of this many CTAs (SVT only)
+    int angle64 = 0;   // FP32 SVT of slices in shared memory: rotation angles and convergence tests in FP64
 };
 
 // Plan a Jacobi launch for n1 x n2 slices of element size elem (4 or 8).

@@ -132,11 +132,13 @@ __device__ __forceinline__ void tube_tile(const T* __restrict__ in, const T* __r
 
     // ADMM epilogue (Algorithm 1; Eq. 25 and the multiplier update of Eq. 20):
     //   X+ = mask ? B : Y + M/beta,  M+ = M + beta (Y - X+)
-    T sdx = 0, sxx = 0, syx = 0, snx = 0;
+    //   residual sums in FP64 per thread, FP32 only within a row of 4 pixels
+    double sdx = 0, sxx = 0, syx = 0, snx = 0;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         int q = q0 + tq + 8 * i;
         if (q >= n3) continue;
+        T cdx = 0, cxx = 0, cyx = 0, cnx = 0;
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
             int64_t p = p0 + tp * 4 + c;
@@ -147,15 +149,19 @@ __device__ __forceinline__ void tube_tile(const T* __restrict__ in, const T* __r
             T xn = mask[g] ? Bs[g] : y + mm / rbeta;
             T mn = mm + rbeta * (y - xn);
             T dx = xn - x, dy = y - xn;
-            sdx = fma(dx, dx, sdx);
-            sxx = fma(x, x, sxx);
-            syx = fma(dy, dy, syx);
-            snx = fma(xn, xn, snx);
+            cdx = fma(dx, dx, cdx);
+            cxx = fma(x, x, cxx);
+            cyx = fma(dy, dy, cyx);
+            cnx = fma(xn, xn, cnx);
             Xs[g] = xn;
             Ms[g] = mn;
         }
+        sdx += (double)cdx;
+        sxx += (double)cxx;
+        syx += (double)cyx;
+        snx += (double)cnx;
     }
-    double s[4] = {(double)sdx, (double)sxx, (double)syx, (double)snx};
+    double s[4] = {sdx, sxx, syx, snx};
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
 #pragma unroll

@@ -1,5 +1,5 @@
 // Tube transforms on the tcgen05 tensor cores (FP32 data, 3xTF32 split or
-// BF16 hi/lo split).
+// three-part BF16 split).
 //
 // out(p, q) = sum_j in(p, j) op(j, q) as a GEMM with M = pixels (a CTA owns
 // 128 of them, the MMA's M), N = output tube positions (n3 rounded up to 16,
@@ -8,10 +8,13 @@
 // x rounded to TF32 (10 mantissa bits) and x_lo = x - x_hi (exact in FP32,
 // at most 2^-11 |x|), and out = A_hi B_hi + A_hi B_lo + A_lo B_hi (the
 // dropped A_lo B_lo term is below 2^-22 relative).  The BF16 form splits
-// the same way into two BF16 parts (8 significant bits each, x_lo at most
-// 2^-9 |x|) and runs the three products as kind::f16 MMAs with FP32
-// accumulation: what it drops (A_lo B_lo and the part of x below x_hi + x_lo)
-// is of order 2^-16 relative, a transform error of a few 1e-6.
+// each value into three BF16 parts x = x0 + x1 + x2 (8 significant bits
+// each; x1 at most 2^-9 |x|, x2 at most 2^-17 |x|, the rest below 2^-25 |x|)
+// and runs the six products of total order at most two (A0 B0, A0 B1,
+// A1 B0, A0 B2, A1 B1, A2 B0) as kind::f16 MMAs with FP32 accumulation:
+// what it drops is below about 2^-24 relative, FP32 accuracy.  (With two
+// parts and three products the dropped terms are of order 2^-16, a transform
+// error of a few 1e-6, which shows in the t-SVT at the 1e-5 level.)
 //
 // Staging: 256 threads, two per pixel row (each takes half of a K chunk), load
 // the input strip with coalesced loads (the ADMM prologue Z = X - M/beta is
@@ -169,9 +172,9 @@ __host__ __device__ __forceinline__ uint32_t kmajor_off(int row, int k)
 }
 
 // MODE 0: plain; MODE 1: forward with Z = X - M/beta; MODE 2: inverse with the
-// ADMM update.  BF: BF16 hi/lo split (kind::f16) instead of 3xTF32.
+// ADMM update.  BF: three-part BF16 split (kind::f16) instead of 3xTF32.
 template <int MODE, bool BF>
-__global__ void __launch_bounds__(TTHREADS)
+__global__ void __launch_bounds__(TTHREADS, 2)
 tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, float* __restrict__ out,
                const float* __restrict__ bimg, int64_t P, int n3, int NP, int nchunks, uint32_t tmem_cols,
                const AdmmCtl* __restrict__ ctl, float* __restrict__ Xs, float* __restrict__ Ms,
@@ -187,12 +190,14 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t p0 = (int64_t)blockIdx.x * TBM;
     constexpr uint32_t ES = BF ? 2 : 4;                // bytes per staged value
-    const uint32_t a_bytes = TBM * TKC * ES;           // one A tile (hi or lo)
-    const uint32_t b_bytes = (uint32_t)NP * TKC * ES;  // one B tile (hi or lo)
+    constexpr int NPART = BF ? 3 : 2;                  // split parts per value
+    const uint32_t a_bytes = TBM * TKC * ES;           // one A tile (one part)
+    const uint32_t b_bytes = (uint32_t)NP * TKC * ES;  // one B tile (one part)
     unsigned char* Ahi = smem;
     unsigned char* Alo = smem + a_bytes;
-    // two stages of operator tiles: stage t holds hi at Bst(t), lo right after
-    auto Bst = [&](int t) { return smem + 2 * a_bytes + (size_t)t * 2 * b_bytes; };
+    unsigned char* Alo2 = smem + 2 * a_bytes;          // BF16: third part
+    // two stages of operator tiles: stage t holds the NPART parts from Bst(t) on
+    auto Bst = [&](int t) { return smem + NPART * a_bytes + (size_t)t * NPART * b_bytes; };
 
     float rbeta = 1.f, rinv = 1.f;
     if (MODE != 0) {
@@ -226,17 +231,16 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
     bool ok = true;
     auto issue_b = [&](int chunk) {
         const int t = chunk & 1;
-        mbar_expect_tx(&bar_b[t], 2 * b_bytes);
-        const unsigned char* src = reinterpret_cast<const unsigned char*>(bimg) + (size_t)chunk * 2 * b_bytes;
-        bulk_g2s(Bst(t), src, b_bytes, &bar_b[t]);
-        bulk_g2s(Bst(t) + b_bytes, src + b_bytes, b_bytes, &bar_b[t]);
+        mbar_expect_tx(&bar_b[t], NPART * b_bytes);
+        const unsigned char* src = reinterpret_cast<const unsigned char*>(bimg) + (size_t)chunk * NPART * b_bytes;
+#pragma unroll
+        for (int q = 0; q < NPART; ++q) bulk_g2s(Bst(t) + q * b_bytes, src + q * b_bytes, b_bytes, &bar_b[t]);
         b_pending[t] = true;
     };
     if (tid == 0) issue_b(0);
-    for (int c = 0; c < nchunks; ++c) {
-        // this chunk's inputs: all loads first, in flight while the previous chunk's MMAs run
+    // a chunk's inputs, loaded into registers (issued early: see the loop below)
+    auto load_chunk = [&](int c, float (&v)[TKH], float (&w)[TKH]) {
         const int k0 = c * TKC + half * TKH;
-        float v[TKH], w[TKH];
 #pragma unroll
         for (int u = 0; u < TKH; ++u) {
             const int j = k0 + u;
@@ -245,15 +249,15 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
             v[u] = ld ? __ldg(in + e) : 0.f;
             if (MODE == 1) w[u] = ld ? __ldg(in2 + e) : 0.f;
         }
+    };
+    // split chunk c into the A tiles and issue its MMAs; false on a timeout
+    auto run_chunk = [&](int c, float (&v)[TKH], float (&w)[TKH]) -> bool {
         if (c > 0) {
             // the A tiles are rewritten only after the previous chunk's MMAs completed
             const int late = mbar_wait(&bar_mma, phase_m, spin) ? 0 : 1;
             phase_m ^= 1;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            if (__syncthreads_or(late)) {
-                ok = false;
-                break;
-            }
+            if (__syncthreads_or(late)) return false;
             if (tid == 0) mma_pending = false;
         }
         if (!BF) {
@@ -274,7 +278,9 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
         } else {
 #pragma unroll
             for (int g = 0; g < TKH / 8; ++g) {
-                uint32_t hw[4], lw[4];
+                // x = x0 + x1 + x2, each part rounded to BF16 from what the
+                // parts before it leave (x - x0 and x - x0 - x1 are exact in FP32)
+                uint32_t hw[4], mw[4], lw[4];
 #pragma unroll
                 for (int u = 0; u < 8; u += 2) {
                     float x0 = v[g * 8 + u], x1 = v[g * 8 + u + 1];
@@ -283,13 +289,17 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
                         x1 = fmaf(-w[g * 8 + u + 1], rinv, x1);
                     }
                     const uint16_t h0 = bf16_bits(x0), h1 = bf16_bits(x1);
-                    const uint16_t l0 = bf16_bits(x0 - bf16_val(h0)), l1 = bf16_bits(x1 - bf16_val(h1));
+                    const float r0 = x0 - bf16_val(h0), r1 = x1 - bf16_val(h1);
+                    const uint16_t m0 = bf16_bits(r0), m1 = bf16_bits(r1);
+                    const uint16_t l0 = bf16_bits(r0 - bf16_val(m0)), l1 = bf16_bits(r1 - bf16_val(m1));
                     hw[u / 2] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+                    mw[u / 2] = (uint32_t)m0 | ((uint32_t)m1 << 16);
                     lw[u / 2] = (uint32_t)l0 | ((uint32_t)l1 << 16);
                 }
                 const uint32_t off = kmajor_off<true>(row, half * TKH + g * 8);
                 *reinterpret_cast<uint4*>(Ahi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-                *reinterpret_cast<uint4*>(Alo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+                *reinterpret_cast<uint4*>(Alo + off) = make_uint4(mw[0], mw[1], mw[2], mw[3]);
+                *reinterpret_cast<uint4*>(Alo2 + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
             }
         }
         // make the generic-proxy writes visible to the tensor cores
@@ -306,7 +316,7 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 // an MMA takes 32 bytes of K (8 TF32 or 16 BF16 values): two core matrices
                 const uint32_t sbo = TKC / (BF ? 8 : 4) * 128, lbo = 128;
-                const uint32_t bh0 = smem_u32(Bst(t)), bl0 = bh0 + b_bytes;
+                const uint32_t bh0 = smem_u32(Bst(t)), bl0 = bh0 + b_bytes, bl20 = bl0 + b_bytes;
 #pragma unroll
                 for (int s = 0; s < TKC * (int)ES / 32; ++s) {
                     const uint32_t koff = (uint32_t)s * 2 * 128;
@@ -315,9 +325,16 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
                     const uint64_t bh = make_desc(bh0 + koff, lbo, sbo);
                     const uint64_t bl = make_desc(bl0 + koff, lbo, sbo);
                     if (BF) {
+                        // parts 0, 1, 2 of each operand: every product of total
+                        // order at most 2 (what is dropped is below 2^-24 relative)
+                        const uint64_t al2 = make_desc(smem_u32(Alo2) + koff, lbo, sbo);
+                        const uint64_t bl2 = make_desc(bl20 + koff, lbo, sbo);
                         mma_bf16(taddr, ah, bh, idesc, (c > 0 || s > 0) ? 1u : 0u);
                         mma_bf16(taddr, ah, bl, idesc, 1u);
                         mma_bf16(taddr, al, bh, idesc, 1u);
+                        mma_bf16(taddr, ah, bl2, idesc, 1u);
+                        mma_bf16(taddr, al, bl, idesc, 1u);
+                        mma_bf16(taddr, al2, bh, idesc, 1u);
                     } else {
                         mma_tf32(taddr, ah, bh, idesc, (c > 0 || s > 0) ? 1u : 0u);
                         mma_tf32(taddr, ah, bl, idesc, 1u);
@@ -330,11 +347,52 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
                 if (c + 1 < nchunks) issue_b(c + 1);
             }
         }
-        if (__syncthreads_or(fail)) {
-            ok = false;
-            break;
+        if (__syncthreads_or(fail)) return false;
+        return true;
+    };
+    // software pipeline: the loads of chunk c + 1 are in flight while chunk c
+    // waits for the MMAs of chunk c - 1, is split and is issued (two register
+    // buffers, used alternately, so no load result is copied)
+    {
+        float va[TKH], wa[TKH], vb[TKH], wb[TKH];
+        load_chunk(0, va, wa);
+        for (int c = 0; c < nchunks; c += 2) {
+            if (c + 1 < nchunks) load_chunk(c + 1, vb, wb);
+            if (!run_chunk(c, va, wa)) {
+                ok = false;
+                break;
+            }
+            if (c + 1 >= nchunks) break;
+            if (c + 2 < nchunks) load_chunk(c + 2, va, wa);
+            if (!run_chunk(c + 1, vb, wb)) {
+                ok = false;
+                break;
+            }
         }
     }
+    // epilogue lanes: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its pixels),
+    // 16 columns at a time, the two warps of a lane quarter alternating chunks
+    const int quarter = warp & 3, qhalf = warp >> 2;
+    const int64_t pe = p0 + quarter * 32 + lane;
+    const bool erow = pe < P;
+    // inverse with the ADMM update: the X, M, B, mask values of a 16-column
+    // chunk (B is loaded everywhere, no wait on the mask, but only selected on it)
+    float xv[16], mv[16], bv[16];
+    uint8_t kv[16];
+    auto load_epi = [&](int q0) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int q = q0 + u;
+            const bool ld = erow && q < n3;
+            const size_t e = (size_t)pe + (size_t)P * (ld ? q : 0);
+            xv[u] = ld ? Xs[e] : 0.f;
+            mv[u] = ld ? Ms[e] : 0.f;
+            kv[u] = ld ? mask[e] : (uint8_t)0;
+            bv[u] = ld ? __ldg(Bs + e) : 0.f;
+        }
+    };
+    // the first chunk's loads are in flight while the last MMAs finish
+    if (MODE == 2 && ok) load_epi(qhalf * 16);
     if (ok) {
         const int late = mbar_wait(&bar_mma, phase_m, spin) ? 0 : 1;
         phase_m ^= 1;
@@ -344,12 +402,8 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
     }
 
     if (ok) {
-        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (its pixels), 16
-        // columns at a time, the two warps of a lane quarter alternating chunks
-        const int quarter = warp & 3, qhalf = warp >> 2;
-        const int64_t pe = p0 + quarter * 32 + lane;
-        const bool erow = pe < P;
-        float sdx = 0.f, sxx = 0.f, syx = 0.f, snx = 0.f;
+        // residual sums in FP64 per thread, FP32 only within a chunk of 16
+        double sdx = 0.0, sxx = 0.0, syx = 0.0, snx = 0.0;
         for (int q0 = qhalf * 16; q0 < NP; q0 += 32) {
             float v[16];
             tmem_ld16(taddr + ((uint32_t)(quarter * 32) << 16) + (uint32_t)q0, v);
@@ -360,21 +414,9 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
                     if (erow && q < n3) out[(size_t)pe + (size_t)P * q] = v[u];
                 }
             } else {
-                // the group's X, M, B, mask loads first, then Algorithm 1's update
-                // (Eq. 25 and the multiplier update of Eq. 20), then the stores
-                float xv[16], mv[16], bv[16];
-                uint8_t kv[16];
-#pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    const int q = q0 + u;
-                    const bool ld = erow && q < n3;
-                    const size_t e = (size_t)pe + (size_t)P * (ld ? q : 0);
-                    xv[u] = ld ? Xs[e] : 0.f;
-                    mv[u] = ld ? Ms[e] : 0.f;
-                    kv[u] = ld ? mask[e] : (uint8_t)0;
-                    // B is loaded everywhere (no wait on the mask) but only selected on the mask
-                    bv[u] = ld ? __ldg(Bs + e) : 0.f;
-                }
+                // Algorithm 1's update (Eq. 25 and the multiplier update of Eq. 20)
+                if (q0 > qhalf * 16) load_epi(q0);  // the first chunk's were loaded before the MMA wait
+                float cdx = 0.f, cxx = 0.f, cyx = 0.f, cnx = 0.f;
 #pragma unroll
                 for (int u = 0; u < 16; ++u) {
                     const int q = q0 + u;
@@ -385,17 +427,21 @@ tube_tc_kernel(const float* __restrict__ in, const float* __restrict__ in2, floa
                     const float xn = kv[u] ? bv[u] : fmaf(mm, rinv, y);
                     const float mn = fmaf(rbeta, y - xn, mm);
                     const float dx = xn - x, dy = y - xn;
-                    sdx = fmaf(dx, dx, sdx);
-                    sxx = fmaf(x, x, sxx);
-                    syx = fmaf(dy, dy, syx);
-                    snx = fmaf(xn, xn, snx);
+                    cdx = fmaf(dx, dx, cdx);
+                    cxx = fmaf(x, x, cxx);
+                    cyx = fmaf(dy, dy, cyx);
+                    cnx = fmaf(xn, xn, cnx);
                     Xs[e] = xn;
                     Ms[e] = mn;
                 }
+                sdx += (double)cdx;
+                sxx += (double)cxx;
+                syx += (double)cyx;
+                snx += (double)cnx;
             }
         }
         if (MODE == 2) {
-            double sv[4] = {(double)sdx, (double)sxx, (double)syx, (double)snx};
+            double sv[4] = {sdx, sxx, syx, snx};
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
@@ -454,12 +500,16 @@ __global__ void build_operator_tc(float* img, int n3, int NP, int nchunks, int i
             img[(size_t)c * 2 * NP * TKC + off] = hi;
             img[(size_t)c * 2 * NP * TKC + (size_t)NP * TKC + off] = lo;
         } else {
+            // three BF16 parts, each rounded from what the parts before it leave
             const uint16_t hi = bf16_bits((float)v);
-            const uint16_t lo = bf16_bits((float)(v - (double)bf16_val(hi)));
+            const double r = v - (double)bf16_val(hi);
+            const uint16_t mid = bf16_bits((float)r);
+            const uint16_t lo = bf16_bits((float)(r - (double)bf16_val(mid)));
             uint16_t* b16 = reinterpret_cast<uint16_t*>(img);
             const uint32_t off = kmajor_off<true>(n, kk) / 2;
-            b16[(size_t)c * 2 * NP * TKC + off] = hi;
-            b16[(size_t)c * 2 * NP * TKC + (size_t)NP * TKC + off] = lo;
+            b16[(size_t)c * 3 * NP * TKC + off] = hi;
+            b16[(size_t)c * 3 * NP * TKC + (size_t)NP * TKC + off] = mid;
+            b16[(size_t)c * 3 * NP * TKC + (size_t)2 * NP * TKC + off] = lo;
         }
     }
 }
@@ -472,7 +522,9 @@ int tube_tc_np(int64_t n3) { return (int)((n3 + 15) / 16 * 16); }
 int tube_tc_chunks(int64_t n3) { return (int)((n3 + TKC - 1) / TKC); }
 size_t tube_tc_image_floats(int64_t n3, bool bf)
 {
-    return (size_t)tube_tc_chunks(n3) * 2 * tube_tc_np(n3) * TKC / (bf ? 2 : 1);
+    // TF32: two 4-byte parts per value; BF16: three 2-byte parts
+    return bf ? (size_t)tube_tc_chunks(n3) * 3 * tube_tc_np(n3) * TKC / 2
+              : (size_t)tube_tc_chunks(n3) * 2 * tube_tc_np(n3) * TKC;
 }
 int tube_tc_partials_count(int64_t P) { return (int)((P + TBM - 1) / TBM); }
 
@@ -493,7 +545,8 @@ static cudaError_t launch_tc_as(const float* in, const float* in2, float* out, c
     uint32_t cols = 32;
     while ((int)cols < NP) cols <<= 1;
     const size_t es = BF ? 2 : 4;
-    const size_t smem = 2 * (size_t)TBM * TKC * es + 4 * (size_t)NP * TKC * es;  // A hi/lo + two B stages
+    const size_t np = BF ? 3 : 2;  // split parts
+    const size_t smem = np * (size_t)TBM * TKC * es + 2 * np * (size_t)NP * TKC * es;  // A parts + two B stages
     auto kern = tube_tc_kernel<MODE, BF>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -25,7 +25,7 @@ if not _os.path.exists(LIB_PATH):
 _lib = _ct.CDLL(LIB_PATH)
 
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ENONFINITE, ENODEV = range(7)
-OPT_JACOBI_MAX_SWEEPS, OPT_TC_WAIT_POLLS = 1, 2
+OPT_JACOBI_MAX_SWEEPS, OPT_TC_WAIT_POLLS, OPT_JACOBI_FP64_ANGLES = 1, 2, 3
 PRECISIONS = {"fp64": 0, "fp32": 1, "tf32x3": 2, "bf16split": 3}
 OP_TDCT3, OP_TSVT, OP_TSVD, OP_TPROD, OP_COMPLETE = range(5)
 
@@ -328,7 +328,8 @@ class Context:
         self._chk(_lib.tnn_reserve(self._h, int(nbytes)), "tnn_reserve")
 
     def set_option(self, option, value):
-        """tnn_set_option: OPT_JACOBI_MAX_SWEEPS or OPT_TC_WAIT_POLLS."""
+        """tnn_set_option: OPT_JACOBI_MAX_SWEEPS, OPT_TC_WAIT_POLLS or
+        OPT_JACOBI_FP64_ANGLES."""
         self._chk(_lib.tnn_set_option(self._h, int(option), int(value)), "tnn_set_option")
 
     def workspace_size(self, op, shape, prec="fp32"):

@@ -4,13 +4,14 @@ FP64 oracle.
 FP64 path: ||Y - Y_oracle||_F <= 1e-12 ||Y_oracle||_F (||Z||_F when the
 oracle's Y is below 1e-6 ||Z||_F).
 
-FP32 path: ||Y - Y_oracle||_F <= 1e-5 ||Z||_F on every case.  The t-SVT is
-1-Lipschitz in Z, so FP32 rounding of size u ||Z|| (u = 2^-24) bounds what an
-FP32 computation can reach; relative to ||Y|| the same error grows by
-||Z|| / ||Y||.  The error relative to ||Y_oracle|| is also held to 1e-5 on the
-completion-shaped tensors and where the threshold keeps most of the energy
-(Gaussian slices, tau at the 30th-percentile singular value); with tau at the
-80th percentile (||Y|| about 0.13 ||Z||) it is held to 1e-4."""
+FP32 forms (CUDA-core, 3xTF32 and BF16-split transforms; FP32 Jacobi):
+||Y - Y_oracle||_F <= 1e-5 ||Y_oracle||_F and <= 1e-5 ||Z||_F on every case
+held by one CTA, the Gaussian stress cases with tau at the 80th-percentile
+singular value (||Y|| about 0.13 ||Z||) included.  Gaussian slices spread
+over thread-block clusters (several hundred rows and columns, dense spectra)
+are held to 2 sqrt(m n) u ||Z|| (u = 2^-24): one-sided Jacobi leaves each
+column pair orthogonal only to its threshold sqrt(m) u, and on such spectra
+the rebuilt slice carries an error of that order."""
 import numpy as np
 import pytest
 import scipy.fft
@@ -22,9 +23,9 @@ from paper_1902_03070_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-12, "fp32": 1e-5, "tf32x3": 1e-5,
-       # BF16 hi/lo transforms: about 2^-16 relative each way (the Jacobi
-       # stage is FP32 as in the other FP32 forms)
-       "bf16split": 2.0 ** -15}
+       # three-part BF16 transforms: FP32 accuracy (the Jacobi stage is FP32
+       # as in the other FP32 forms)
+       "bf16split": 1e-5}
 
 SHAPES = [
     (48, 48, 16),    # the 48 x 48 x 16 completion workload
@@ -72,7 +73,7 @@ def test_tsvt_matches_oracle(ctx, prec, shape, q):
     else:
         err_z = np.linalg.norm(Y - ref) / np.linalg.norm(Z)
         assert err_z <= TOL[prec], (err_z, err_y)
-        assert err_y <= (TOL[prec] if q <= 0.5 else 1e-4), (err_z, err_y)
+        assert err_y <= TOL[prec], (err_z, err_y)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "bf16split"])
@@ -113,7 +114,7 @@ def test_tsvt_special_cases(ctx, prec):
     Z = inputs.random_tensor((20, 12, 6), rng)
     if prec != "fp64":
         Z = Z.astype(np.float32).astype(np.float64)
-    tol = {"fp64": 1e-13, "bf16split": 2.0 ** -15}.get(prec, 2e-6)
+    tol = {"fp64": 1e-13}.get(prec, 2e-6)
     # tau = 0: Y = Z
     Y = _run(ctx, Z, 0.0, prec)
     assert np.linalg.norm(Y - Z) <= tol * np.linalg.norm(Z)
@@ -200,6 +201,8 @@ def test_tsvt_cluster_slices(ctx, prec, shape, q):
     else:
         m, n = max(shape[:2]), min(shape[:2])
         assert err_z <= 2.0 * np.sqrt(m * n) * U32, (err_z, err_y)
+        if q <= 0.5:  # tau keeps most of the energy: within 1e-5 of Y as everywhere else
+            assert err_y <= TOL[prec], (err_z, err_y)
 
 
 @pytest.mark.parametrize("C", ["2", "4", "8"])
@@ -319,3 +322,31 @@ def test_tsvt_top_singular_value_near_tau(ctx, prec, shape, s1):
         assert np.count_nonzero(ref) == 0 or np.abs(ref).max() == 0.0
         assert np.abs(Y).max() == 0.0
     assert err_z <= (TOL["fp64"] if prec == "fp64" else TOL["fp32"]), err_z
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32x3"])
+@pytest.mark.parametrize("shape", [(48, 48, 16), (130, 100, 3), (33, 65, 5)])
+def test_tsvt_fp64_angles(ctx, prec, shape):
+    """TNN_OPT_JACOBI_FP64_ANGLES: the FP32 Jacobi with its rotation angles
+    and convergence tests in FP64 meets the same gates as the FP32 form on the
+    hardest cases of the suite (Gaussian slices, tau at the 80th-percentile
+    singular value, ||Y|| about 0.13 ||Z||); both errors are logged, for the
+    comparison of the two forms."""
+    from paper_1902_03070_gb300 import tnn
+    rng = np.random.default_rng(shape[0] * 1000 + shape[1] * 10 + shape[2])
+    Z = inputs.random_tensor(shape, rng).astype(np.float32).astype(np.float64)
+    tau = tau_at_quantile(Z, 0.8)
+    ref = O.tsvt(Z, tau, nthreads=THREADS)
+    errs = {}
+    try:
+        for a64 in (0, 1):
+            ctx.set_option(tnn.OPT_JACOBI_FP64_ANGLES, a64)
+            Y = _run(ctx, Z, tau, prec)
+            errs[a64] = (rel_err(Y, ref, Z), np.linalg.norm(Y - ref) / np.linalg.norm(Z))
+    finally:
+        ctx.set_option(tnn.OPT_JACOBI_FP64_ANGLES, 0)
+    log_err("tsvt angles %s %s q=0.8" % (prec, shape), err_y_fp32_angles=errs[0][0], err_y_fp64_angles=errs[1][0],
+            err_z_fp32_angles=errs[0][1], err_z_fp64_angles=errs[1][1])
+    for a64 in (0, 1):
+        assert errs[a64][1] <= TOL[prec], errs
+        assert errs[a64][0] <= TOL[prec], errs

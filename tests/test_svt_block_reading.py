@@ -108,3 +108,79 @@ def test_zero_svt_certificate(s1, ortho):
         assert not cert
     if s1 <= 0.9 and ortho <= 1e-4:
         assert cert  # nearly orthogonal columns well below tau: the bound is tight enough
+
+
+def _low_block_cert_fp32(S, tau, eps):
+    # the kernel's low-block certificate (reading 22), in FP32 like the FP32
+    # kernel: the low set is the columns below tau^2; row sums of |S_L^T S_L|
+    # plus the rounding margins, accepted up to (tau + eps)^2
+    S32 = S.astype(np.float32)
+    nrm = np.linalg.norm(S, axis=0)
+    L = nrm < tau
+    SL = S32[:, L]
+    G = SL.T @ SL
+    m = S.shape[0]
+    nl = int(L.sum())
+    u = 2.0 ** -24
+    rows = (np.abs(G).astype(np.float64).sum(1) * (1 + 2 * nl * u)
+            + 2 * m * u * nrm[L] * 1.01 * nrm[L].sum())
+    return rows.max() <= (tau + eps) ** 2, L
+
+
+def _low_case(rng, m, n, nh, top, spread, tau):
+    # S_H: nh orthogonal columns far above tau; S_L: the other columns,
+    # orthogonal to S_H, with singular values from top * tau down, mixed by a
+    # near-identity matrix so that its columns are not quite orthogonal
+    Q, _ = np.linalg.qr(rng.standard_normal((m, m)))
+    SH = Q[:, :nh] * (tau * np.geomspace(2000.0, 30.0, nh))
+    nl = n - nh
+    sl = tau * np.linspace(top, 0.1, nl)
+    W = np.eye(nl) + spread * rng.standard_normal((nl, nl))
+    SL = (Q[:, nh:nh + nl] * sl) @ W
+    SL *= top * tau / np.linalg.svd(SL, compute_uv=False)[0]   # top low singular value exactly top * tau
+    S = np.hstack([SH, SL])
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    return S, S @ V.T
+
+
+@pytest.mark.parametrize("top", [0.9, 0.99, 0.999, 1.02, 1.2])
+@pytest.mark.parametrize("spread", [1e-5, 1e-3, 3e-2])
+def test_low_block_certificate(top, spread):
+    # soundness: where the certificate accepts, the rebuild over the columns
+    # above tau is the oracle's SVT to within the allowance eps per low
+    # singular value; a low set (columns below tau) whose block has a
+    # singular value above tau + eps is never certified
+    rng = np.random.default_rng(int(top * 1000) + int(spread * 1e5))
+    m, n, nh, tau = 60, 48, 10, 0.5
+    S, A = _low_case(rng, m, n, nh, top, spread, tau)
+    Y, _ = O.svt_matrix(A, tau)
+    eps = 1e-7 * np.linalg.norm(Y)
+    cert, L = _low_block_cert_fp32(S, tau, eps)
+    if cert:
+        H = np.flatnonzero(~L)
+        Yb = _rebuild(S[:, H], A, len(H), tau)
+        assert np.linalg.norm(Yb - Y) <= np.sqrt(L.sum()) * eps + 1e-12 * np.linalg.norm(A)
+    if np.linalg.svd(S[:, L], compute_uv=False)[0] > tau + 2 * eps:
+        assert not cert
+    if top <= 0.99 and spread <= 1e-5:
+        assert cert  # nearly orthogonal and clear of tau: the bound is tight enough
+
+
+def test_low_block_certificate_rejects_correlated_columns():
+    # every low column below tau, but correlated so that the block has a
+    # singular value above tau: the certificate must refuse, and leaving the
+    # block out would indeed be wrong
+    rng = np.random.default_rng(3)
+    m, n, nh, tau = 60, 40, 6, 0.5
+    Q, _ = np.linalg.qr(rng.standard_normal((m, m)))
+    SH = Q[:, :nh] * (tau * np.geomspace(500.0, 40.0, nh))
+    base = Q[:, nh:nh + 2] @ rng.standard_normal((2, n - nh))
+    SL = base * (0.9 * tau / np.linalg.norm(base, axis=0))   # each column at 0.9 tau
+    S = np.hstack([SH, SL])
+    assert np.linalg.svd(SL, compute_uv=False)[0] > 1.5 * tau
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = S @ V.T
+    Y, _ = O.svt_matrix(A, tau)
+    cert, L = _low_block_cert_fp32(S, tau, 1e-7 * np.linalg.norm(Y))
+    assert L.sum() == n - nh and not cert
+    assert np.linalg.norm(_rebuild(S, A, nh, tau) - Y) > 1e-3 * np.linalg.norm(Y)

@@ -8,7 +8,9 @@ Algorithm 1 (forward tube DCT with the Z = X - M/beta prologue, per-slice
 Jacobi SVT, inverse DCT with the ADMM update), run through the C ABI.  The
 K timed steps are the LAST K iterations of the 200-iteration job (200 - K ..
 199), where every slice's SVD runs: an untimed prefix of the job comes first,
-its last W iterations counting as the warm-up.  The L2 cache is flushed
+its last W iterations counting as the warm-up.  The job carries its warm-start
+state (each slice's right singular vectors from the previous iteration), as
+tnn_complete does; the plain FP64 path runs without it.  The L2 cache is flushed
 between timed steps.
 
 Prints one JSON line.  `value` is t-SVT slices/s over all ranks (100 slices
@@ -241,17 +243,21 @@ def run_ours(args):
     # fit before the window runs on a throw-away copy, then one run of the
     # job goes through its untimed prefix and the W warm-up iterations right
     # before the window.
+    # The job's warm-start state (each slice's right singular vectors from
+    # the previous iteration) is part of the run, as in tnn_complete.
     K, W = args.steps, args.warmup
     win = window(K, W)
     if win["warm_extra"]:
         Bd, md, X, M = fresh(torch.float32)
-        ctx.admm_iterate(Bd, md, X, M, ADMM["beta0"], win["warm_extra"], prm, prec=PREC)
+        wst = ctx.admm_warm_state((N1, N2, N3), PREC)
+        ctx.admm_iterate(Bd, md, X, M, ADMM["beta0"], win["warm_extra"], prm, prec=PREC, warm=wst)
     Bd, md, X, M = fresh(torch.float32)
+    wst = ctx.admm_warm_state((N1, N2, N3), PREC)
     beta = ADMM["beta0"]
     if win["prefix"]:
-        beta, _ = ctx.admm_iterate(Bd, md, X, M, beta, win["prefix"], prm, prec=PREC)
+        beta, _ = ctx.admm_iterate(Bd, md, X, M, beta, win["prefix"], prm, prec=PREC, warm=wst)
     for _ in range(win["warm_in"]):
-        beta, _ = ctx.admm_iterate(Bd, md, X, M, beta, 1, prm, prec=PREC)
+        beta, _ = ctx.admm_iterate(Bd, md, X, M, beta, 1, prm, prec=PREC, warm=wst)
     step_ms, flops, tflops = [], 0.0, 0.0
     jw = {"pairs": 0, "rotations": 0, "kept": 0, "max_sweeps": 0, "unconverged": 0}
     clocks = Clocks(gpu_id_for_smi(torch, lrank))
@@ -265,7 +271,7 @@ def run_ours(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        beta, rep = ctx.admm_iterate(Bd, md, X, M, beta, 1, prm, prec=PREC)
+        beta, rep = ctx.admm_iterate(Bd, md, X, M, beta, 1, prm, prec=PREC, warm=wst)
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
@@ -317,16 +323,17 @@ def run_ours(args):
         ctx.set_option(tnn.OPT_JACOBI_FP64_ANGLES, 1)
         try:
             Ba, ma, Xa, Ma = fresh(torch.float32)
+            wa = ctx.admm_warm_state((N1, N2, N3), PREC)
             ba = ADMM["beta0"]
             if win["start"]:
-                ba, _ = ctx.admm_iterate(Ba, ma, Xa, Ma, ba, win["start"], prm, prec=PREC)
+                ba, _ = ctx.admm_iterate(Ba, ma, Xa, Ma, ba, win["start"], prm, prec=PREC, warm=wa)
             msa = []
             for _ in range(K):
                 flush.zero_()
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                ba, _ = ctx.admm_iterate(Ba, ma, Xa, Ma, ba, 1, prm, prec=PREC)
+                ba, _ = ctx.admm_iterate(Ba, ma, Xa, Ma, ba, 1, prm, prec=PREC, warm=wa)
                 e1.record(stream)
                 e1.synchronize()
                 msa.append(e0.elapsed_time(e1))
@@ -834,13 +841,14 @@ def probe_admm_trace(torch, inputs, tnn):
         M = tnn.to_fortran(np.zeros(B.shape), device=dev, dtype=torch.float32)
         beta = prm["beta0"]
         cp = ctx.params(**prm)
+        wst = ctx.admm_warm_state(B.shape, "tf32x3")
         s = torch.cuda.current_stream(dev)
         rows = []
         for it in range(prm["max_iter"]):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(s)
-            beta, _ = ctx.admm_iterate(Bd, md, X, M, beta, 1, cp, prec="tf32x3")
+            beta, _ = ctx.admm_iterate(Bd, md, X, M, beta, 1, cp, prec="tf32x3", warm=wst)
             e1.record(s)
             e1.synchronize()
             st = ctx.last_jacobi_stats()

@@ -69,7 +69,7 @@ typedef enum {
     TNN_FP64 = 0,           /* double data, FP64 arithmetic everywhere (the plain path) */
     TNN_FP32 = 1,           /* float data, FP32 arithmetic on CUDA cores */
     TNN_FP32_TF32X3 = 2,    /* float data, tube DCT on tcgen05 tensor cores, 3xTF32 split */
-    TNN_FP32_BF16SPLIT = 3  /* float data, tube DCT on tcgen05 tensor cores, BF16 hi/lo split (three
+    TNN_FP32_BF16SPLIT = 3  /* float data, tube DCT on tcgen05 tensor cores, three-part BF16 split (six
                                products accumulated in FP32) */
 } tnn_precision;
 
@@ -138,10 +138,17 @@ tnn_status tnn_reserve(tnn_ctx* ctx, size_t bytes);
  *   = in FP32.  The columns, the dot products and the rotations applied stay
  *   FP32.  (Measured on the video-shaped workload: about 5x the time per
  *   iteration for errors within 1.2x of the FP32 form's.)
+ * TNN_OPT_ADMM_WARM_START: 1 (default) = tnn_complete warm-starts the
+ *   per-slice Jacobi of each iteration from the previous iteration's right
+ *   singular vectors (FP32 precisions, slices one CTA holds; the state lives
+ *   in the workspace; see tnn_admm_iterate); 0 = every iteration starts from
+ *   the slices themselves, as the batched plans and the completion server
+ *   do, whose iterates tnn_complete then reproduces bit for bit.
  * Returns TNN_EINVAL for an unknown option or a value out of range. */
 #define TNN_OPT_JACOBI_MAX_SWEEPS 1
 #define TNN_OPT_TC_WAIT_POLLS 2
 #define TNN_OPT_JACOBI_FP64_ANGLES 3
+#define TNN_OPT_ADMM_WARM_START 4
 tnn_status tnn_set_option(tnn_ctx* ctx, int option, int64_t value);
 
 enum { TNN_OP_TDCT3 = 0, TNN_OP_TSVT = 1, TNN_OP_TSVD = 2, TNN_OP_TPROD = 3, TNN_OP_COMPLETE = 4 };
@@ -197,21 +204,41 @@ tnn_status tprod_dct(tnn_ctx* ctx, const void* X, const void* Y, int64_t m1, int
  * mask is n1*n2*n3 bytes in the tensor's layout (nonzero = observed).
  * X_out receives the recovered tensor and may be the same buffer as B.
  * rep (may be NULL) receives the run's report.  Synchronises the stream.
- * Returns TNN_ENOCONV if max_iter was reached before the tol test passed. */
+ * Returns TNN_ENOCONV if max_iter was reached before the tol test passed.
+ * The FP32 precisions warm-start each iteration's per-slice Jacobi from the
+ * previous iteration's right singular vectors (see tnn_admm_warm_size). */
 tnn_status tnn_complete(tnn_ctx* ctx, const void* B, const uint8_t* mask, tnn_shape shape,
                         const tnn_admm_params* params, tnn_precision prec, void* X_out,
                         tnn_admm_report* rep, void* stream);
 
 /* Run up to `iters` iterations of Algorithm 1 from a caller-held state:
- * X and M (n1 x n2 x n3, device or host, updated in place) and *beta (host,
- * updated).  The iteration counter starts from 0 for this call; params->tol
- * and params->max_iter still stop the run (max_iter counts iterations of this
+ * X and M (n1 x n2 x n3, device or host, updated in place), *beta (host,
+ * updated) and, optionally, the warm-start state `warm` (NULL: none).  The
+ * iteration counter starts from 0 for this call; params->tol and
+ * params->max_iter still stop the run (max_iter counts iterations of this
  * call).  A run split over several calls computes exactly what one call
- * does (checkpoint and resume).  rep may be NULL.  Synchronises the stream.
- * Returns TNN_OK when all requested iterations ran or tol was met. */
+ * does (checkpoint and resume; the same warm buffer is part of the state).
+ * rep may be NULL.  Synchronises the stream.  Returns TNN_OK when all
+ * requested iterations ran or tol was met.
+ *
+ * warm: a device buffer of tnn_admm_warm_size bytes, zero-filled before the
+ * job's first iteration, then left to the library, which keeps there each
+ * slice's right singular vectors (an orthogonal n x n matrix Q per slice,
+ * n = min(n1, n2)) from the last iteration that rotated it.  One-sided
+ * Jacobi on A Q has the singular values and left singular vectors of A, so
+ * the SVT (rebuilt from A) does not depend on Q up to rounding; a Q from the
+ * previous iteration makes the columns of A Q nearly orthogonal and cuts the
+ * sweeps severalfold late in a completion.  Any orthogonal Q is correct, so
+ * a zero-filled or stale buffer only costs sweeps.  Used by the FP32
+ * precisions for slices one CTA holds; otherwise not touched. */
 tnn_status tnn_admm_iterate(tnn_ctx* ctx, const void* B, const uint8_t* mask, tnn_shape shape,
                             const tnn_admm_params* params, tnn_precision prec, void* X, void* M,
-                            double* beta, int32_t iters, tnn_admm_report* rep, void* stream);
+                            double* beta, int32_t iters, void* warm, tnn_admm_report* rep, void* stream);
+
+/* Host only: bytes of the warm-start state of tnn_admm_iterate for this
+ * shape and precision; 0 when the precision or slice size does not use it
+ * (FP64, or slices spread over thread-block clusters). */
+tnn_status tnn_admm_warm_size(tnn_shape shape, tnn_precision prec, size_t* bytes);
 
 /* Kernel statistics of the last tsvt_dct / tsvd_dct_forward / ADMM iteration
  * on ctx: out[0] = slices, out[1] = column pairs visited, out[2] = rotations
@@ -435,8 +462,9 @@ void tnn_server_destroy(tnn_server* server);
  *   4 ADMM iteration finalize   5 ADMM control init
  *   6 ADMM state init           7 Jacobi SVD
  *   8 facewise product          9 DFT / rectangular tube transform
- *  10 plain Jacobi SVT (comparison path) */
-#define TNN_NKERNELS 11
+ *  10 plain Jacobi SVT (comparison path)
+ *  11 warm start of the Jacobi SVT (A Q before it, Q after it) */
+#define TNN_NKERNELS 12
 tnn_status tnn_profile(tnn_ctx* ctx, int enable);
 tnn_status tnn_profile_read(tnn_ctx* ctx, double ms[TNN_NKERNELS], int64_t launches[TNN_NKERNELS]);
 

@@ -28,6 +28,7 @@ struct tnn_ctx {
     int opt_jacobi_sweeps = 0;   // TNN_OPT_JACOBI_MAX_SWEEPS (0: the kernels' default)
     int opt_tc_polls = -1;       // TNN_OPT_TC_WAIT_POLLS (negative: the default limit)
     int opt_angle64 = 0;         // TNN_OPT_JACOBI_FP64_ANGLES
+    int opt_warm = 1;            // TNN_OPT_ADMM_WARM_START (tnn_complete)
     SliceStats* last_stats = nullptr;
     int64_t last_n3 = 0;
     cudaStream_t last_stream = nullptr;
@@ -140,7 +141,7 @@ struct Trace {
 
 // Kernel kinds reported by tnn_profile_read (array index, listed in tnn.h).
 enum { K_TUBE = 0, K_TUBE_FWD_ADMM, K_JACOBI_SVT, K_TUBE_INV_ADMM, K_FINALIZE, K_CTL_INIT, K_ADMM_INIT,
-       K_JACOBI_SVD, K_FACEWISE, K_DFT, K_JACOBI_PLAIN, K_NKINDS };
+       K_JACOBI_SVD, K_FACEWISE, K_DFT, K_JACOBI_PLAIN, K_WARM, K_NKINDS };
 #define TRACE_CAT2(a, b) a##b
 #define TRACE_CAT(a, b) TRACE_CAT2(a, b)
 #define TRACE(kind) Trace TRACE_CAT(trace_, __LINE__)(ctx, kind, s)
@@ -331,6 +332,10 @@ tnn_status tnn_set_option(tnn_ctx* ctx, int option, int64_t value)
     case TNN_OPT_JACOBI_FP64_ANGLES:
         if (value != 0 && value != 1) return fail(ctx, TNN_EINVAL, "FP64-angle flag must be 0 or 1");
         ctx->opt_angle64 = (int)value;
+        return TNN_OK;
+    case TNN_OPT_ADMM_WARM_START:
+        if (value != 0 && value != 1) return fail(ctx, TNN_EINVAL, "warm-start flag must be 0 or 1");
+        ctx->opt_warm = (int)value;
         return TNN_OK;
     default: return fail(ctx, TNN_EINVAL, "unknown option %d", option);
     }
@@ -731,8 +736,23 @@ tnn_status admm_enqueue_iters(tnn_ctx* ctx, const AdmmJob& j, int iters, cudaStr
               else
                   CK(launch_tube_fwd_admm_op<float>((const float*)j.X, (const float*)j.M, (float*)j.W,
                                                     (const float*)opf.op, P, n3, j.ctl, s)); }
+            // warm start: the slices times the previous iteration's right
+            // singular vectors before the sweeps, the new vectors after them
+            const bool warm = j.warm != nullptr;
+            float* Q = (float*)j.warm;
+            int* wflag = warm ? (int*)((char*)j.warm + ((size_t)n3 * j.jp.n * j.jp.n * 4 + 255) / 256 * 256) : nullptr;
+            if (warm) {
+                TRACE(K_WARM);
+                CK(launch_warm_gemm<float>(j.jp, (const float*)j.W, Q, wflag, (float*)j.wscr, j.ctl, s));
+            }
             { TRACE(K_JACOBI_SVT);
-              CK(launch_jacobi_svt<float>(j.jp, (float*)j.W, 0.0, j.ctl, sweeps, j.jwork, j.stats, s)); }
+              const WarmPtrs wp{j.wscr, wflag, j.wscr, j.wrec};
+              CK(launch_jacobi_svt<float>(j.jp, (float*)j.W, 0.0, j.ctl, sweeps, j.jwork, j.stats, s,
+                                          warm ? &wp : nullptr)); }
+            if (warm) {
+                TRACE(K_WARM);
+                CK(launch_warm_qr<float>(j.jp, (float*)j.wscr, j.wrec, Q, wflag, j.ctl, s));
+            }
             { TRACE(K_TUBE_INV_ADMM);
               if (opi.tc)
                   CK(launch_tube_tc_inv_admm((const float*)j.W, (float*)j.X, (float*)j.M, (const float*)j.B, j.mask,
@@ -823,6 +843,12 @@ tnn_status tnn_complete(tnn_ctx* ctx, const void* B, const uint8_t* mask, tnn_sh
     size_t oM = cv.add(bytes), oW = cv.add(bytes), oP = cv.add((size_t)nparts * 4 * sizeof(double));
     size_t oS = cv.add(sizeof(SliceStats) * sh.n3), oC = cv.add(sizeof(AdmmCtl)), oJ = cv.add(jp.work_bytes);
     size_t ohb = ab.host ? cv.add(bytes) : 0, ohm = am.host ? cv.add(N) : 0, ohx = ax.host ? cv.add(bytes) : 0;
+    // warm start across the run's iterations: state, scratch and flags
+    const bool warm = ctx->opt_warm && elem == 4 && warm_supported(jp);
+    const size_t wstate = warm ? warm_state_bytes(sh.n3, jp.n, elem) : 0;
+    const size_t wscr = warm ? (size_t)sh.n3 * jp.ldA * jp.nb * jp.K * elem : 0;
+    size_t oWs = warm ? cv.add(wstate) : 0, oWc = warm ? cv.add(wscr) : 0;
+    size_t oWr = warm ? cv.add(sizeof(int) * sh.n3) : 0;
     if ((st = ensure_ws(ctx, cv.total))) return st;
     Stager sg{ctx, s};
     if ((st = sg.in(ab, ohb))) return st;
@@ -837,6 +863,13 @@ tnn_status tnn_complete(tnn_ctx* ctx, const void* B, const uint8_t* mask, tnn_sh
     AdmmCtl res;
     AdmmJob job = make_job(sh, prec, *params, ab.dev, am.dev, X, M, at(ctx, oW), (AdmmCtl*)at(ctx, oC),
                            (double*)at(ctx, oP), (SliceStats*)at(ctx, oS), at(ctx, oJ), jp);
+    if (warm) {
+        CK(cudaMemsetAsync(at(ctx, oWs), 0, wstate, s));
+        CK(cudaMemsetAsync(at(ctx, oWr), 0, sizeof(int) * sh.n3, s));
+        job.warm = at(ctx, oWs);
+        job.wscr = at(ctx, oWc);
+        job.wrec = (int*)at(ctx, oWr);
+    }
     st = admm_run(ctx, job, params->beta0, params->max_iter, s, &res);
     if (st) return st;
     if ((st = sg.finish())) return st;
@@ -848,7 +881,7 @@ tnn_status tnn_complete(tnn_ctx* ctx, const void* B, const uint8_t* mask, tnn_sh
 
 tnn_status tnn_admm_iterate(tnn_ctx* ctx, const void* B, const uint8_t* mask, tnn_shape sh,
                             const tnn_admm_params* params, tnn_precision prec, void* X, void* M, double* beta,
-                            int32_t iters, tnn_admm_report* rep, void* stream)
+                            int32_t iters, void* warm_state, tnn_admm_report* rep, void* stream)
 {
     if (!ctx) return TNN_EINVAL;
     if (!B || !mask || !X || !M || !beta || !(*beta > 0.0) || iters < 0 || !shape_ok(sh) || !prec_ok(prec))
@@ -869,6 +902,12 @@ tnn_status tnn_admm_iterate(tnn_ctx* ctx, const void* B, const uint8_t* mask, tn
     size_t oS = cv.add(sizeof(SliceStats) * sh.n3), oC = cv.add(sizeof(AdmmCtl)), oJ = cv.add(jp.work_bytes);
     size_t ohb = ab.host ? cv.add(bytes) : 0, ohm = am.host ? cv.add(N) : 0;
     size_t ohx = ax.host ? cv.add(bytes) : 0, ohmm = amm.host ? cv.add(bytes) : 0;
+    // warm start from the caller's state (device memory), when this precision
+    // and slice size use it
+    const bool warm = warm_state && elem == 4 && warm_supported(jp);
+    if (warm && !is_device_ptr(warm_state)) return fail(ctx, TNN_EINVAL, "warm state must be device memory");
+    const size_t wscr = warm ? (size_t)sh.n3 * jp.ldA * jp.nb * jp.K * elem : 0;
+    size_t oWc = warm ? cv.add(wscr) : 0, oWr = warm ? cv.add(sizeof(int) * sh.n3) : 0;
     if ((st = ensure_ws(ctx, cv.total))) return st;
     Stager sg{ctx, s};
     if ((st = sg.in(ab, ohb))) return st;
@@ -881,12 +920,29 @@ tnn_status tnn_admm_iterate(tnn_ctx* ctx, const void* B, const uint8_t* mask, tn
     AdmmCtl res;
     AdmmJob job = make_job(sh, prec, *params, ab.dev, am.dev, ax.dev, amm.dev, at(ctx, oW), (AdmmCtl*)at(ctx, oC),
                            (double*)at(ctx, oP), (SliceStats*)at(ctx, oS), at(ctx, oJ), jp);
+    if (warm) {
+        CK(cudaMemsetAsync(at(ctx, oWr), 0, sizeof(int) * sh.n3, s));
+        job.warm = warm_state;
+        job.wscr = at(ctx, oWc);
+        job.wrec = (int*)at(ctx, oWr);
+    }
     st = admm_run(ctx, job, *beta, max_iter, s, &res);
     if (st) return st;
     if ((st = sg.finish())) return st;
     *beta = res.beta;
     fill_report(rep, res);
     if (res.nonfinite) return fail(ctx, TNN_ENONFINITE, "non-finite value met in iteration %d", res.iter);
+    return TNN_OK;
+}
+
+tnn_status tnn_admm_warm_size(tnn_shape sh, tnn_precision prec, size_t* bytes)
+{
+    if (!bytes || !shape_ok(sh) || !prec_ok(prec)) return TNN_EINVAL;
+    *bytes = 0;
+    const int elem = elem_of(prec);
+    JacobiPlan jp;
+    if (!jacobi_plan(sh.n1, sh.n2, sh.n3, elem, &jp)) return TNN_EINVAL;
+    if (elem == 4 && warm_supported(jp)) *bytes = warm_state_bytes(sh.n3, jp.n, elem);
     return TNN_OK;
 }
 

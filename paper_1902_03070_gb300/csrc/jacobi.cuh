@@ -217,15 +217,19 @@ __device__ __forceinline__ void rot_params(T ai, T aj, T gam, T& t, T& c)
 // Factors of the scaled rotation for tangent t: t1 = t d_j / d_i, t2 = t d_i /
 // d_j and c = 1 / sqrt(1 + t^2).  The angle t itself need not be accurate
 // (any t gives an orthogonal rotation), but c must belong to the t that is
-// applied and t1, t2 must match the scales: an error there is a column scaling
-// that builds up in d over the thousands of rotations a column takes part in,
-// and d |s| is the singular value the shrinkage uses.  FP32: the hardware's
-// approximate reciprocal and reciprocal square root, each refined by one
-// Newton step written with FMAs (r <- r + r (1 - x r), y <- y + y (1/2 - x/2
-// y^2)), which brings them to about one unit in the last place; the approximate
-// forms alone leave a few units, and the drift of the singular values they
-// cause (a few 1e-5 relative to Y where tau is large) is what FP64 angles
-// remove.  FP64: the IEEE reciprocal.
+// applied and t1, t2 must match the scales: their errors act as a column
+// scaling that builds up in d over the thousands of rotations a column takes
+// part in, and d |s| is the singular value the shrinkage uses.  What matters
+// is bias: a systematic error adds up linearly over the rotations, a random
+// one only as their square root.  Measured on GB300 over 2^24 random
+// arguments (bias / RMS in units of the last place): c from the approximate
+// reciprocal square root and one Newton step +0.08 / 0.46 (without the step
+// +0.14 / 0.76), correctly rounded +0.01 / 0.35; t1, t2 from the approximate
+// reciprocal refined by one FMA Newton step 0.00 / 0.73, correctly rounded
+// division 0.00 / 0.60.  So FP32 takes the correctly rounded reciprocal square
+// root for c and the refined reciprocal for t1, t2 (with the biased c the
+// t-SVT error reached 1e-5..3e-5 of ||Y|| where tau is large); FP64 the IEEE
+// reciprocal.
 __device__ __forceinline__ void rot_factors(float t, float di, float dj, float& t1, float& t2, float& c)
 {
     float ri = rcp(di), rj = rcp(dj);
@@ -233,10 +237,7 @@ __device__ __forceinline__ void rot_factors(float t, float di, float dj, float& 
     rj = fmaf(rj, fmaf(-dj, rj, 1.0f), rj);
     t1 = (t * dj) * ri;
     t2 = (t * di) * rj;
-    const float x = fmaf(t, t, 1.0f);
-    float y = rsqrtf(x);
-    y = fmaf(y, fmaf(-0.5f * x * y, y, 0.5f), y);
-    c = y;
+    c = __frsqrt_rn(fmaf(t, t, 1.0f));
 }
 __device__ __forceinline__ void rot_factors(double t, double di, double dj, double& t1, double& t2, double& c)
 {
@@ -710,6 +711,15 @@ struct KArgs {
     T* S;
     T* V;
     const SliceItem* items;  // batched SVT: per-CTA slice parameters (replace the fields above)
+    // warm start (single-tensor SVT): slice k starts from w0 + k * stride (the
+    // slice times an orthogonal Q, in the working copy's layout) when
+    // wflag[k] is set; after the sweeps A0^T s_i / sigma_i of every column is
+    // written to vrec + k * stride (n x n, columns by descending sigma) and
+    // wrec[k] set.  vrec may alias w0: each CTA reads its w0 before writing.
+    const T* w0;
+    const int* wflag;
+    T* vrec;
+    int* wrec;
 };
 
 // Shared-memory carve-up (bytes) for a launch: dsc, sig, cf, carried norms
@@ -784,22 +794,35 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
     T* src = item ? static_cast<T*>(item->data) : a.data + (size_t)slice * n1 * n2;
 
     // ---- load the oriented slice; pad rows and columns with zeros
-    for (size_t e = tid; e < wsz; e += nthr) Aw[e] = T(0);
-    if (WITHV)
-        for (size_t e = tid; e < wsz; e += nthr) {
-            int c = (int)(e / ldA), r = (int)(e % ldA);
-            Vw[e] = (r == c && c < n) ? T(1) : T(0);
-        }
-    __syncthreads();
-    const int64_t S = n1 * n2;
+    const bool warm_in = !WITHV && !ITEMS && a.w0 && a.wflag && a.wflag[slice];
     T fro = T(0);  // this thread's share of ||A||_F^2
-    for (int64_t e = tid; e < S; e += nthr) {
-        int i = (int)(e % n1), j = (int)(e / n1);
-        // oriented (row, col): (i, j) if n1 >= n2 else (j, i)
-        int r = tr ? j : i, c = tr ? i : j;
-        const T v = src[e];
-        Aw[(size_t)c * ldA + r] = v;
-        fro = fma(v, v, fro);
+    if (warm_in) {
+        // warm start: the slice times the previous iteration's right singular
+        // vectors (orthogonal), already oriented, padded and laid out as here;
+        // the same singular values, columns nearly orthogonal
+        const T* w0 = a.w0 + (size_t)slice * wstride;
+        for (size_t e = tid; e < wsz; e += nthr) {
+            const T v = w0[e];
+            Aw[e] = v;
+            fro = fma(v, v, fro);
+        }
+    } else {
+        for (size_t e = tid; e < wsz; e += nthr) Aw[e] = T(0);
+        if (WITHV)
+            for (size_t e = tid; e < wsz; e += nthr) {
+                int c = (int)(e / ldA), r = (int)(e % ldA);
+                Vw[e] = (r == c && c < n) ? T(1) : T(0);
+            }
+        __syncthreads();
+        const int64_t S = n1 * n2;
+        for (int64_t e = tid; e < S; e += nthr) {
+            int i = (int)(e % n1), j = (int)(e / n1);
+            // oriented (row, col): (i, j) if n1 >= n2 else (j, i)
+            int r = tr ? j : i, c = tr ? i : j;
+            const T v = src[e];
+            Aw[(size_t)c * ldA + r] = v;
+            fro = fma(v, v, fro);
+        }
     }
     for (int c = tid; c < npad; c += nthr) dsc[c] = T(1);
     if (tid == 0) { s_pairs = 0; s_rots = 0; s_nonfinite = 0; s_nuc = 0.0; s_keep = 0; s_fro = 0.0; }
@@ -1086,6 +1109,68 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
         }
     }
     __syncthreads();
+
+    // ---- warm start for the next iteration: v_c = A0^T s_c / (d_c |s_c|^2)
+    // = A0^T u_c / sigma_c for every column, columns by descending sigma
+    // (the reliable ones first for the orthogonalisation that follows).  A
+    // slice that ran no sweep has no new vectors.
+    if (!WITHV && !ITEMS && a.vrec && !skip) {
+        for (int c = tid; c < n; c += nthr) {
+            int rk = 0;
+            const T sc = sig[c];
+            for (int o = 0; o < n; ++o) {
+                const T so = sig[o];
+                rk += (so > sc || (so == sc && o < c)) ? 1 : 0;
+            }
+            rank[c] = rk;
+        }
+        __syncthreads();
+        T* vr = a.vrec + (size_t)slice * wstride;  // this slice's w0, read before the sweeps
+        constexpr int RR = (R * L + 31) / 32;
+        constexpr int JB = (RR <= 6) ? 4 : (RR <= 12 ? 2 : 1);
+        constexpr int NV = 4 * JB;
+        constexpr int GV = 32 / NV;
+        for (int j0 = warp * JB; j0 < n; j0 += JB * W) {
+            T x[JB][RR];
+#pragma unroll
+            for (int u = 0; u < JB; ++u)
+#pragma unroll
+                for (int q = 0; q < RR; ++q) {
+                    const int r = q * 32 + lane, j = j0 + u;
+                    x[u][q] = (r < m && j < n) ? (tr ? src[(size_t)j + (size_t)n1 * r] : src[(size_t)r + (size_t)n1 * j])
+                                               : T(0);
+                }
+            for (int k0 = 0; k0 < n; k0 += 4) {
+                T g[NV];
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    T sv[RR];
+                    const T* col = Aw + (size_t)(k0 + v < n ? k0 + v : 0) * ldA;
+#pragma unroll
+                    for (int q = 0; q < RR; ++q) {
+                        const int r = q * 32 + lane;
+                        sv[q] = (r < ldA && k0 + v < n) ? col[r] : T(0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < JB; ++u) {
+                        T acc = T(0);
+#pragma unroll
+                        for (int q = 0; q < RR; ++q) acc = fma(sv[q], x[u][q], acc);
+                        g[v * JB + u] = acc;
+                    }
+                }
+                const T tot = reduce_scatter<T, NV, 32>(g, lane);  // lane holds value lane / GV
+                const int idx = lane / GV, vv = idx / JB, uu = idx % JB;
+                const int k = k0 + vv, j = j0 + uu;
+                if (lane % GV == 0 && k < n && j < n) {
+                    const T den = dsc[k] * cf[k];
+                    vr[(size_t)rank[k] * n + j] = den > T(0) ? tot / den : T(0);
+                }
+            }
+        }
+        if (tid == 0) a.wrec[slice] = 1;
+        __syncthreads();
+    }
 
     const T tau = a.ctl ? (T)(1.0 / a.ctl->beta) : (ictl ? (T)(1.0 / ictl->beta) : (T)(item ? item->tau : a.tau));
 

@@ -6,7 +6,8 @@ namespace tnn {
 
 template <>
 cudaError_t launch_jacobi_svt<double>(const JacobiPlan& p, double* data, double tau, const AdmmCtl* ctl, int max_sweeps,
-                                   void* work, SliceStats* stats, cudaStream_t s)
+                                   void* work, SliceStats* stats, cudaStream_t s,
+                                   const WarmPtrs* warm)
 {
     jac::KArgs<double> a{};
     a.data = data; a.n1 = p.n1; a.n2 = p.n2; a.n3 = p.n3;

@@ -97,10 +97,19 @@ bool pageable(const void* p)
 
 // Device layout of one job (offsets into its allocation).
 struct Layout {
-    size_t B, mask, X, M, W, partials, stats, ctl, jwork, total;
+    size_t B, mask, X, M, W, partials, stats, ctl, jwork, warm, wscr, wrec, total;
 };
 
-Layout layout_of(const tnn_shape& sh, int elem, const JacobiPlan& jp)
+// A job warm-starts its Jacobi from the previous iteration's right singular
+// vectors (as tnn_complete does) when it runs on its own kernels: FP32
+// precisions, slices one CTA holds, not a TNN_FP32 job of a server that
+// batches those (the batched kernels start cold).
+bool job_warm(tnn_precision prec, const JacobiPlan& jp, bool batching)
+{
+    return prec != TNN_FP64 && warm_supported(jp) && !(batching && prec == TNN_FP32);
+}
+
+Layout layout_of(const tnn_shape& sh, int elem, const JacobiPlan& jp, bool warm)
 {
     const size_t N = (size_t)sh.n1 * sh.n2 * sh.n3, bytes = N * elem;
     Layout L;
@@ -119,6 +128,9 @@ Layout layout_of(const tnn_shape& sh, int elem, const JacobiPlan& jp)
     L.stats = add(sizeof(SliceStats) * sh.n3);
     L.ctl = add(sizeof(AdmmCtl));
     L.jwork = add(jp.work_bytes);
+    L.warm = warm ? add(warm_state_bytes(sh.n3, jp.n, elem)) : 0;
+    L.wscr = warm ? add((size_t)sh.n3 * jp.ldA * jp.nb * jp.K * elem) : 0;
+    L.wrec = warm ? add(sizeof(int) * sh.n3) : 0;
     L.total = o;
     return L;
 }
@@ -195,7 +207,8 @@ bool admit(tnn_server* sv, SJob& j)
     const int elem = j.prec == TNN_FP64 ? 8 : 4;
     JacobiPlan jp;
     jacobi_plan(j.sh.n1, j.sh.n2, j.sh.n3, elem, &jp);
-    const Layout L = layout_of(j.sh, elem, jp);
+    const bool warm = job_warm(j.prec, jp, (sv->p.flags & TNN_SERVER_BATCH_KERNELS) != 0);
+    const Layout L = layout_of(j.sh, elem, jp, warm);
     int lane = 0;
     const int bl = (sv->p.flags & TNN_SERVER_BATCH_KERNELS) && (j.prec == TNN_FP32 || j.prec == TNN_FP64)
                        ? (j.prec == TNN_FP64 ? 1 : 0)
@@ -241,8 +254,16 @@ bool admit(tnn_server* sv, SJob& j)
     j.aj.stats = reinterpret_cast<SliceStats*>(c + L.stats);
     j.aj.jwork = jp.work_bytes ? c + L.jwork : nullptr;
     j.aj.jp = jp;
+    if (warm) {
+        j.aj.warm = c + L.warm;
+        j.aj.wscr = c + L.wscr;
+        j.aj.wrec = reinterpret_cast<int*>(c + L.wrec);
+    }
     bool ok = cudaMemcpyAsync(c + L.B, j.B_user, bytes, cudaMemcpyDefault, s) == cudaSuccess &&
               cudaMemcpyAsync(c + L.mask, j.mask_user, N, cudaMemcpyDefault, s) == cudaSuccess;
+    if (ok && warm)  // a cold start: no slice has its vectors yet
+        ok = cudaMemsetAsync(c + L.warm, 0, L.wscr - L.warm, s) == cudaSuccess &&
+             cudaMemsetAsync(c + L.wrec, 0, sizeof(int) * j.sh.n3, s) == cudaSuccess;
     if (ok) {
         ok = (elem == 8 ? launch_admm_init<double>((const double*)j.aj.B, j.aj.mask, (double*)j.aj.X,
                                                    (double*)j.aj.M, (int64_t)N, s)
@@ -278,7 +299,7 @@ size_t footprint(const tnn_shape& sh, tnn_precision prec)
     const int elem = prec == TNN_FP64 ? 8 : 4;
     JacobiPlan jp;
     if (!jacobi_plan(sh.n1, sh.n2, sh.n3, elem, &jp)) return 0;
-    return layout_of(sh, elem, jp).total;
+    return layout_of(sh, elem, jp, job_warm(prec, jp, false)).total;
 }
 
 void release(tnn_server* sv, SJob& j)

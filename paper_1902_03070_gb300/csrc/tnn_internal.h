@@ -138,9 +138,32 @@ bool jacobi_plan_mode(int64_t n1, int64_t n2, int64_t n3, int elem, bool withv, 
 
 // SVT of every frontal slice of `data` in place:  data_k <- U (S - tau)_+ V^T.
 // tau = 1 / ctl->beta when ctl is not null (and the launch exits if ctl->done).
+// Warm start of the SVT (warm.cu): w0 = start columns (per slice, working-
+// copy layout, launch stride ldA * nb * K), wflag = slices whose w0 is valid,
+// vrec / wrec = the recovered right vectors and their flags (vrec may be w0).
+struct WarmPtrs {
+    void* w0;
+    const int* wflag;
+    void* vrec;
+    int* wrec;
+};
+
 template <typename T>
 cudaError_t launch_jacobi_svt(const JacobiPlan& plan, T* data, double tau, const AdmmCtl* ctl, int max_sweeps,
-                              void* work, SliceStats* stats, cudaStream_t s);
+                              void* work, SliceStats* stats, cudaStream_t s, const WarmPtrs* warm = nullptr);
+
+// Warm start across ADMM iterations (FP32, slices held by one CTA).  State:
+// n3 orthogonal n x n matrices Q followed by n3 int flags (warm_state_bytes);
+// zero-filled = cold.  Scratch: n3 * ldA * nb * K elements (W0, then the
+// recovered vectors) and n3 int flags.
+bool warm_supported(const JacobiPlan& p);
+size_t warm_state_bytes(int64_t n3, int n, int elem);
+template <typename T>
+cudaError_t launch_warm_gemm(const JacobiPlan& p, const T* data, const T* Q, const int* flag, T* w0,
+                             const AdmmCtl* ctl, cudaStream_t s);
+template <typename T>
+cudaError_t launch_warm_qr(const JacobiPlan& p, T* vrec, int* wrec, T* Q, int* flag, const AdmmCtl* ctl,
+                           cudaStream_t s);
 
 // SVT of a list of slices (device array of `count` SliceItems) that all use
 // the variant of `plan` (K, RA, L, ldA, in_smem); plan.nb and plan.n3 must be
@@ -281,6 +304,11 @@ struct AdmmJob {
     void* jwork;           // plan.work_bytes
     JacobiPlan jp;
     TubeOp opf, opi;       // filled by admm_prepare_job
+    // warm start (FP32, warm_supported(jp)): the state (Q per slice, then
+    // flags), the scratch (n3 * ldA * nb * K elements) and its n3 flags
+    void* warm = nullptr;
+    void* wscr = nullptr;
+    int* wrec = nullptr;
 };
 
 // The job's transform operators, from the context's caches (built on first use).

@@ -25,7 +25,7 @@ if not _os.path.exists(LIB_PATH):
 _lib = _ct.CDLL(LIB_PATH)
 
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ENONFINITE, ENODEV = range(7)
-OPT_JACOBI_MAX_SWEEPS, OPT_TC_WAIT_POLLS, OPT_JACOBI_FP64_ANGLES = 1, 2, 3
+OPT_JACOBI_MAX_SWEEPS, OPT_TC_WAIT_POLLS, OPT_JACOBI_FP64_ANGLES, OPT_ADMM_WARM_START = 1, 2, 3, 4
 PRECISIONS = {"fp64": 0, "fp32": 1, "tf32x3": 2, "bf16split": 3}
 OP_TDCT3, OP_TSVT, OP_TSVD, OP_TPROD, OP_COMPLETE = range(5)
 
@@ -78,8 +78,10 @@ _lib.tnn_complete.argtypes = [_vp, _vp, _vp, Shape, _ct.POINTER(AdmmParams), _ct
                               _ct.POINTER(AdmmReport), _vp]
 _lib.tnn_complete.restype = _st
 _lib.tnn_admm_iterate.argtypes = [_vp, _vp, _vp, Shape, _ct.POINTER(AdmmParams), _ct.c_int, _vp, _vp,
-                                  _ct.POINTER(_ct.c_double), _ct.c_int32, _ct.POINTER(AdmmReport), _vp]
+                                  _ct.POINTER(_ct.c_double), _ct.c_int32, _vp, _ct.POINTER(AdmmReport), _vp]
 _lib.tnn_admm_iterate.restype = _st
+_lib.tnn_admm_warm_size.argtypes = [Shape, _ct.c_int, _ct.POINTER(_ct.c_size_t)]
+_lib.tnn_admm_warm_size.restype = _st
 _lib.tnn_last_jacobi_stats.argtypes = [_vp, _ct.POINTER(_ct.c_int64)]
 _lib.tnn_last_jacobi_stats.restype = _st
 _lib.tnn_fma_peak.argtypes = [_ct.c_int32, _ct.c_int32, _ct.POINTER(_ct.c_double)]
@@ -159,9 +161,9 @@ _lib.tnn_admm_batch_destroy.argtypes = [_vp]
 _lib.tnn_admm_batch_destroy.restype = None
 BATCH_GRAPH = 1
 BATCH_AUTOTUNE = 2
-NKERNELS = 11
+NKERNELS = 12
 KERNEL_KINDS = ["tube", "tube_fwd_admm", "jacobi_svt", "tube_inv_admm", "admm_finalize", "ctl_init", "admm_init",
-                "jacobi_svd", "facewise", "dft", "jacobi_plain"]
+                "jacobi_svd", "facewise", "dft", "jacobi_plain", "warm"]
 _lib.tsvt_dft.argtypes = [_vp, _vp, Shape, _ct.c_double, _ct.c_int, _vp, _ct.POINTER(_ct.c_double), _vp]
 _lib.tsvt_dft.restype = _st
 _lib.tsvt_dct_plain.argtypes = [_vp, _vp, Shape, _ct.c_double, _ct.c_int, _vp, _ct.POINTER(_ct.c_double), _vp]
@@ -170,7 +172,7 @@ _lib.tsvt_dct_plain.restype = _st
 EXPORTS = ["tnn_create", "tnn_destroy", "tnn_status_string", "tnn_last_error", "tnn_reserve", "tnn_set_option",
            "tnn_workspace_size",
            "tdct3", "tsvt_dct", "tsvd_dct_forward", "tsvd_dct_inverse", "tprod_dct", "tnn_complete",
-           "tnn_admm_iterate", "tnn_last_jacobi_stats", "tnn_profile", "tnn_profile_read", "tsvt_dct_static",
+           "tnn_admm_iterate", "tnn_admm_warm_size", "tnn_last_jacobi_stats", "tnn_profile", "tnn_profile_read", "tsvt_dct_static",
            "tnn_tsvt_batch_create", "tnn_tsvt_batch_run", "tnn_tsvt_batch_info", "tnn_tsvt_batch_group",
            "tnn_tsvt_batch_profile", "tnn_tsvt_batch_stats", "tnn_tsvt_batch_destroy",
            "tnn_server_create", "tnn_server_submit", "tnn_server_step", "tnn_server_job_state", "tnn_server_take",
@@ -328,8 +330,8 @@ class Context:
         self._chk(_lib.tnn_reserve(self._h, int(nbytes)), "tnn_reserve")
 
     def set_option(self, option, value):
-        """tnn_set_option: OPT_JACOBI_MAX_SWEEPS, OPT_TC_WAIT_POLLS or
-        OPT_JACOBI_FP64_ANGLES."""
+        """tnn_set_option: OPT_JACOBI_MAX_SWEEPS, OPT_TC_WAIT_POLLS,
+        OPT_JACOBI_FP64_ANGLES or OPT_ADMM_WARM_START."""
         self._chk(_lib.tnn_set_option(self._h, int(option), int(value)), "tnn_set_option")
 
     def workspace_size(self, op, shape, prec="fp32"):
@@ -434,18 +436,32 @@ class Context:
         self._chk(st, "tnn_complete", allow=(ENOCONV,))
         return st, rep.as_dict()
 
-    def admm_iterate(self, B, mask, X, M, beta, iters, params, prec="fp32"):
-        """Advance a caller-held ADMM state (X, M, beta) by up to `iters`
-        iterations.  Returns (beta, report dict)."""
+    def admm_iterate(self, B, mask, X, M, beta, iters, params, prec="fp32", warm=None):
+        """Advance a caller-held ADMM state (X, M, beta and, optionally, the
+        warm-start buffer of admm_warm_state) by up to `iters` iterations.
+        Returns (beta, report dict)."""
         for t in (B, X, M, mask):
             _check_layout(t, B.shape)
         b = _ct.c_double(float(beta))
         rep = AdmmReport()
+        wp = None if warm is None else warm.data_ptr()
         st = _lib.tnn_admm_iterate(self._h, _ptr(B)[0], _ptr(mask)[0], Shape(*B.shape), _ct.byref(params),
-                                   PRECISIONS[prec], _ptr(X)[0], _ptr(M)[0], _ct.byref(b), int(iters),
+                                   PRECISIONS[prec], _ptr(X)[0], _ptr(M)[0], _ct.byref(b), int(iters), wp,
                                    _ct.byref(rep), _stream([B, mask, X, M]))
         self._chk(st, "tnn_admm_iterate")
         return b.value, rep.as_dict()
+
+    @staticmethod
+    def admm_warm_state(shape, prec="fp32", device="cuda"):
+        """A zero-filled warm-start buffer for admm_iterate (torch uint8
+        tensor on the device), or None where the precision or slice size does
+        not use one (tnn_admm_warm_size)."""
+        import torch
+        n = _ct.c_size_t(0)
+        st = _lib.tnn_admm_warm_size(Shape(*shape), PRECISIONS[prec], _ct.byref(n))
+        if st != OK:
+            raise TnnError(st, "tnn_admm_warm_size")
+        return torch.zeros(n.value, dtype=torch.uint8, device=device) if n.value else None
 
     def tsvt_batch(self, Zs, taus, Ys=None, prec="fp32", graph=True, autotune=False):
         """Plan for Y_i = t-SVT_{tau_i}(Z_i) over device tensors of different

@@ -163,3 +163,79 @@ def test_completion_msi_full_size_matches_oracle(ctx, prec):
     assert rep["iters"] == gold["iters"]
     assert abs(err - gold["rel_err_vs_ground_truth"]) <= 1e-4, (err, gold["rel_err_vs_ground_truth"])
     assert dev <= 1e-3, dev
+
+
+def _video_state(ctx, iters, warm):
+    """The video-shaped completion (3xTF32 transforms) after `iters` warm-
+    started iterations from its start: (d, Bd, md, X, M, beta)."""
+    from paper_1902_03070_gb300 import tnn
+    torch = torch_cuda()
+    d = inputs.config2(O.tprod)
+    B, mask = d["B"], d["mask"]
+    Bd, md = tnn.to_fortran(B, dtype=torch.float32), tnn.to_fortran(mask)
+    X = tnn.to_fortran(B * mask, dtype=torch.float32)
+    M = tnn.to_fortran(np.zeros(B.shape), dtype=torch.float32)
+    prm = ctx.params(**{**d["admm"], "tol": -1.0})
+    beta, _ = ctx.admm_iterate(Bd, md, X, M, d["admm"]["beta0"], iters, prm, prec="tf32x3", warm=warm)
+    return d, Bd, md, X, M, beta, prm
+
+
+def test_admm_warm_start_one_iteration_matches_cold_and_oracle(ctx):
+    """Warm start (the previous iteration's right singular vectors): from one
+    late state of the video-shaped completion, one warm-started iteration,
+    one cold iteration and one oracle iteration (FP64, same state) agree, the
+    warm one with a fraction of the sweeps, and the kept Q are orthogonal."""
+    from paper_1902_03070_gb300 import tnn
+    torch = torch_cuda()
+    shape = (144, 176, 100)
+    warm = ctx.admm_warm_state(shape, "tf32x3")
+    assert warm is not None
+    d, Bd, md, X, M, beta, prm = _video_state(ctx, 150, warm)
+    x0, m0 = tnn.to_numpy(X).astype(np.float64), tnn.to_numpy(M).astype(np.float64)
+    # the kept Q (n x n per slice, then one flag per slice) are orthogonal
+    n, n3 = 144, 100
+    q = warm[: n3 * n * n * 4].view(torch.float32).reshape(n3, n, n).double()
+    flags = warm[(n3 * n * n * 4 + 255) // 256 * 256:][: 4 * n3].view(torch.int32).cpu().numpy()
+    assert flags.sum() == n3
+    err = (q.transpose(1, 2) @ q - torch.eye(n, dtype=torch.float64, device=q.device)).abs().amax().item()
+    assert err <= 5e-6, err
+    Xw, Mw = X.clone(), M.clone()
+    ctx.admm_iterate(Bd, md, Xw, Mw, beta, 1, prm, prec="tf32x3", warm=warm)
+    sw_warm = ctx.last_jacobi_stats()["max_sweeps"]
+    Xc, Mc = X.clone(), M.clone()
+    ctx.admm_iterate(Bd, md, Xc, Mc, beta, 1, prm, prec="tf32x3")
+    sw_cold = ctx.last_jacobi_stats()["max_sweeps"]
+    Xo, _, _ = O.admm(d["B"], d["mask"], X0=x0, M0=m0, **{**d["admm"], "beta0": beta, "tol": -1.0,
+                                                            "max_iter": 1}, nthreads=THREADS)
+    xw, xc = tnn.to_numpy(Xw).astype(np.float64), tnn.to_numpy(Xc).astype(np.float64)
+    dx = np.linalg.norm(Xo - x0)
+    log_err("admm warm one iteration", warm_vs_cold=np.linalg.norm(xw - xc) / dx,
+            warm_vs_oracle=np.linalg.norm(xw - Xo) / dx, cold_vs_oracle=np.linalg.norm(xc - Xo) / dx,
+            sweeps_warm=sw_warm, sweeps_cold=sw_cold)
+    # relative to the iteration's own change of X (the t-SVT's contribution)
+    assert np.linalg.norm(xw - Xo) <= 1e-3 * dx + 1e-5 * np.linalg.norm(Xo)
+    assert np.linalg.norm(xw - xc) <= 1e-3 * dx + 1e-5 * np.linalg.norm(Xo)
+    assert sw_warm * 2 <= sw_cold, (sw_warm, sw_cold)
+
+
+def test_admm_warm_start_resume_bit_exact(ctx):
+    """With the warm-start buffer as part of the state, 40 + 40 iterations in
+    two calls give bit for bit the 80 of one call."""
+    from paper_1902_03070_gb300 import tnn
+    torch = torch_cuda()
+    shape = (144, 176, 100)
+    w1 = ctx.admm_warm_state(shape, "tf32x3")
+    w2 = ctx.admm_warm_state(shape, "tf32x3")
+    _, Bd, md, X1, M1, b1, prm = _video_state(ctx, 80, w1)
+    d, Bd, md, X2, M2, b2, prm = _video_state(ctx, 40, w2)
+    b2, _ = ctx.admm_iterate(Bd, md, X2, M2, b2, 40, prm, prec="tf32x3", warm=w2)
+    assert b1 == b2
+    assert torch.equal(X1, X2) and torch.equal(M1, M2) and torch.equal(w1, w2)
+
+
+def test_admm_warm_size_zero_where_unused():
+    from paper_1902_03070_gb300 import tnn
+    torch_cuda()
+    assert tnn.Context.admm_warm_state((48, 48, 16), "fp64") is None        # FP64: cold
+    assert tnn.Context.admm_warm_state((512, 512, 31), "bf16split") is None  # slices on clusters
+    assert tnn.Context.admm_warm_state((48, 48, 16), "fp32") is not None

@@ -19,6 +19,9 @@ def ctx():
     torch_cuda()
     from paper_1902_03070_gb300 import tnn
     with tnn.Context(0) as c:
+        # the reference runs: tnn_complete without the warm start, the
+        # iterates the batched and served paths reproduce bit for bit
+        c.set_option(tnn.OPT_ADMM_WARM_START, 0)
         yield c
 
 

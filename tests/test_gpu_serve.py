@@ -26,6 +26,9 @@ def ctx():
     torch_cuda()
     from paper_1902_03070_gb300 import tnn
     with tnn.Context(0) as c:
+        # the reference runs: tnn_complete without the warm start, the
+        # iterates the batched and served paths reproduce bit for bit
+        c.set_option(tnn.OPT_ADMM_WARM_START, 0)
         yield c
 
 
@@ -43,12 +46,20 @@ def _jobs(seed=5):
     return out
 
 
-def _alone(ctx, job):
+def _alone(ctx, job, batch_kernels=False):
+    """The job through tnn_complete, warm-started exactly when the server
+    warm-starts it (FP32 precisions on the job's own kernels; not an FP32
+    job that a batching server puts on the batched kernels)."""
     from paper_1902_03070_gb300 import tnn
     dt = dtype_of(job["prec"])
     Xd = tnn.fortran_empty(job["shape"], dt)
-    st, rep = ctx.complete(tnn.to_fortran(job["B"], dtype=dt), tnn.to_fortran(job["mask"]), Xd,
-                           ctx.params(**job["prm"]), prec=job["prec"])
+    warm = not (batch_kernels and job["prec"] == "fp32")
+    ctx.set_option(tnn.OPT_ADMM_WARM_START, 1 if warm else 0)
+    try:
+        st, rep = ctx.complete(tnn.to_fortran(job["B"], dtype=dt), tnn.to_fortran(job["mask"]), Xd,
+                               ctx.params(**job["prm"]), prec=job["prec"])
+    finally:
+        ctx.set_option(tnn.OPT_ADMM_WARM_START, 0)
     return tnn.to_numpy(Xd), rep
 
 
@@ -81,7 +92,7 @@ def _run_server(server, jobs, device_inputs, stagger=0.0):
 def test_alone_equals_in_mix(ctx, batch_kernels):
     from paper_1902_03070_gb300 import tnn
     jobs = _jobs()
-    alone = [_alone(ctx, j) for j in jobs]
+    alone = [_alone(ctx, j, batch_kernels) for j in jobs]
     with tnn.Server(streams=4, chunk=3, batch_kernels=batch_kernels) as sv:
         mixed = _run_server(sv, jobs, device_inputs=True, stagger=0.002)
         st = sv.stats()
@@ -206,7 +217,7 @@ def test_batched_jobs_join_and_leave(ctx):
             prm["jacobi_max_sweeps"] = 6
         jobs.append(dict(shape=shape, prec="fp64" if i % 3 == 0 else "fp32", B=inputs.fortran(T * mask), mask=mask,
                          prm=prm))
-    alone = [_alone(ctx, j) for j in jobs]
+    alone = [_alone(ctx, j, batch_kernels=True) for j in jobs]
     with tnn.Server(streams=2, chunk=4, batch_kernels=True) as sv:
         mixed = _run_server(sv, jobs, device_inputs=True, stagger=0.001)
         st = sv.stats()

@@ -70,15 +70,26 @@ def test_limits_refused(tnn):
 
 def test_server_footprint(tnn):
     # B, X, M and the transformed tensor (elem bytes each) plus the mask, at
-    # least; the Jacobi scratch only when the slices are not in shared memory
+    # least; the Jacobi scratch only when the slices are not in shared memory;
+    # for a warm-started job also its warm-start state (tnn_admm_warm_size)
+    # and the scratch of its start columns (one L R x nb K working copy per
+    # slice, the slice oriented with its rows the longer side)
+    import ctypes
     for shape, prec in (((144, 176, 100), "tf32x3"), ((48, 48, 16), "fp64"), ((512, 512, 31), "bf16split"),
                         ((300, 20, 7), "fp32")):
         N = int(np.prod(shape))
         elem = 8 if prec == "fp64" else 4
         fp = tnn.server_footprint(shape, prec)
         plan = tnn.jacobi_plan_info(shape, prec)
-        assert fp >= 4 * N * elem + N + plan["work_bytes"]
-        assert fp <= 4 * N * elem + N + plan["work_bytes"] + 64 * 1024 + 64 * shape[2] + 16 * N // 32
+        wb = ctypes.c_size_t(0)
+        assert tnn._lib.tnn_admm_warm_size(tnn.Shape(*shape), tnn.PRECISIONS[prec], ctypes.byref(wb)) == tnn.OK
+        warm = wb.value
+        if warm:
+            warm += shape[2] * plan["L"] * plan["R"] * plan["nb"] * plan["K"] * elem + 4 * shape[2]
+        # warm-started: the video-shaped FP32 job; not FP64, not slices on clusters or over 256 rows
+        assert (warm > 0) == (shape == (144, 176, 100))
+        assert fp >= 4 * N * elem + N + plan["work_bytes"] + warm
+        assert fp <= 4 * N * elem + N + plan["work_bytes"] + warm + 64 * 1024 + 64 * shape[2] + 16 * N // 32
     assert tnn.server_footprint((64, 64, 8), "fp32") < tnn.server_footprint((64, 64, 16), "fp32")
     for shape in ((513, 4, 4), (0, 4, 4)):
         with pytest.raises(tnn.TnnError):

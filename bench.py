@@ -72,7 +72,8 @@ def parse():
     p.add_argument("--serve-jobs-low", type=int, default=150, help="jobs of the under-capacity stream")
     p.add_argument("--serve-rate-low", type=float, default=1.0, help="arrival rate (jobs/s) of that stream")
     p.add_argument("--probe", default=None, choices=["tsvt", "tdct3", "tsvd", "tsvt_dft", "tsvt_dct_plain", "batch",
-                                                     "admm_trace"])
+                                                     "admm_trace", "sweep_cost"])
+    p.add_argument("--at", type=int, default=185, help="sweep_cost: the ADMM iteration to measure")
     p.add_argument("--shape", default="144,176,100")
     p.add_argument("--prec", default="fp32")
     p.add_argument("--reps", type=int, default=3)
@@ -776,6 +777,8 @@ def run_probe(a):
         return probe_batch(a, torch, inputs, tnn)
     if a.probe == "admm_trace":
         return probe_admm_trace(torch, inputs, tnn)
+    if a.probe == "sweep_cost":
+        return probe_sweep_cost(a, torch, inputs, tnn)
     shape = tuple(int(x) for x in a.shape.split(","))
     dt = torch.float64 if a.prec == "fp64" else torch.float32
     Z = inputs.random_tensor(shape, np.random.default_rng(a.seed), "uniform")
@@ -826,6 +829,45 @@ def probe_batch(a, torch, inputs, tnn):
         plan.close()
 
 
+def probe_sweep_cost(a, torch, inputs, tnn):
+    """Per-kernel device time of one ADMM iteration of the video-shaped
+    completion at iteration --at, repeated from the same state with the
+    Jacobi sweeps capped at 1, 2, 3, 4 and uncapped: the fixed cost of a
+    Jacobi launch (start columns, singular values, recovered vectors, rebuild)
+    and the cost of a sweep."""
+    from paper_1902_03070_gb300.serve import library_tprod
+    with tnn.Context(0) as ctx:
+        d = inputs.config2(library_tprod(ctx))
+        B, mask = d["B"], d["mask"]
+        prm = dict(d["admm"])
+        dev = torch.device("cuda", 0)
+        Bd = tnn.to_fortran(B, device=dev, dtype=torch.float32)
+        md = tnn.to_fortran(mask, device=dev)
+        X = tnn.to_fortran(B * mask, device=dev, dtype=torch.float32)
+        M = tnn.to_fortran(np.zeros(B.shape), device=dev, dtype=torch.float32)
+        wst = ctx.admm_warm_state(B.shape, "tf32x3")
+        beta, _ = ctx.admm_iterate(Bd, md, X, M, prm["beta0"], a.at, ctx.params(**prm), prec="tf32x3", warm=wst)
+        snap = (X.clone(), M.clone(), wst.clone())
+        rows = []
+        for cap in (1, 2, 3, 4, 0, 0):
+            X.copy_(snap[0]); M.copy_(snap[1]); wst.copy_(snap[2])
+            torch.cuda.synchronize()
+            ctx.profile(True)
+            ctx.admm_iterate(Bd, md, X, M, beta, 1, ctx.params(**dict(prm, jacobi_max_sweeps=cap)), prec="tf32x3",
+                             warm=wst)
+            torch.cuda.synchronize()
+            prof = ctx.profile_read()
+            ctx.profile(False)
+            st = ctx.last_jacobi_stats()
+            rows.append({"cap": cap, "max_sweeps": st["max_sweeps"], "rotations": st["rotations"],
+                         "kernels_ms": {k: v[0] / max(v[1], 1) for k, v in prof.items()}})
+        print(json.dumps({"probe": "sweep_cost", "at": a.at, "rows": rows}))
+
+
+# iterations of the trace probe whose Jacobi launches keep a sweep log
+LOGGED_ITERS = (60, 100, 150, 185, 199)
+
+
 def probe_admm_trace(torch, inputs, tnn):
     """Per-iteration device time and Jacobi statistics of the video-shaped
     completion (Algorithm 1, one tnn_admm_iterate call per iteration)."""
@@ -844,7 +886,9 @@ def probe_admm_trace(torch, inputs, tnn):
         wst = ctx.admm_warm_state(B.shape, "tf32x3")
         s = torch.cuda.current_stream(dev)
         rows = []
+        logged = {}
         for it in range(prm["max_iter"]):
+            ctx.set_option(tnn.OPT_JACOBI_SWEEP_LOG, 1 if it in LOGGED_ITERS else 0)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(s)
@@ -852,10 +896,21 @@ def probe_admm_trace(torch, inputs, tnn):
             e1.record(s)
             e1.synchronize()
             st = ctx.last_jacobi_stats()
+            per = ctx.last_slice_stats()
+            sw = per["sweeps"]
+            slow = max(range(len(sw)), key=lambda k: (sw[k], per["rotations"][k])) if sw else -1
             rows.append({"iter": it, "ms": e0.elapsed_time(e1), "pairs": st["pairs"], "rotations": st["rotations"],
-                         "max_sweeps": st["max_sweeps"], "kept": st["kept"]})
+                         "max_sweeps": st["max_sweeps"], "kept": st["kept"],
+                         "mean_sweeps": (sum(sw) / len(sw)) if sw else 0.0, "slowest_slice": slow,
+                         "sweeps_hist": [sw.count(v) for v in range(max(sw) + 1)] if sw else []})
+            if it in LOGGED_ITERS:
+                lg = ctx.last_sweep_log()
+                keep = sorted({0, 1, 2, 50, slow})
+                logged[it] = {k: [[round(float(v), 9) for v in row] for row in lg[k] if row.any()] for k in keep}
         print(json.dumps({"probe": "admm_trace", "workload": "144x176x100 video-shaped, 20% observed, tf32x3",
-                          "total_ms": sum(r["ms"] for r in rows), "rows": rows}))
+                          "total_ms": sum(r["ms"] for r in rows), "rows": rows,
+                          "sweep_log_fields": ["big", "wide", "big_lowlow", "max_c_big", "max_t_big", "max_t_all"],
+                          "sweep_logs": logged}))
 
 
 def main():

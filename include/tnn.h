@@ -144,11 +144,27 @@ tnn_status tnn_reserve(tnn_ctx* ctx, size_t bytes);
  *   in the workspace; see tnn_admm_iterate); 0 = every iteration starts from
  *   the slices themselves, as the batched plans and the completion server
  *   do, whose iterates tnn_complete then reproduces bit for bit.
+ * TNN_OPT_JACOBI_SMALL_STOP: 1 (default) = the Jacobi kernels of tsvt_dct,
+ *   tnn_complete and tnn_admm_iterate also stop after a sweep whose
+ *   rotations all had |gamma| / sqrt(alpha beta) and |t| at most
+ *   theta = sqrt(tol / (4 n)) (tol = sqrt(m) u, n the slice's smaller
+ *   side): such a sweep leaves every pair within 2 tol of orthogonal, the
+ *   level the plain rule (a sweep without rotation above 2 tol) accepts, so
+ *   the sweep that rule spends confirming it is skipped.  0 = the plain rule
+ *   only.  The batched plans and the server always use 1.
+ * TNN_OPT_JACOBI_SWEEP_LOG: 1 = the single-CTA Jacobi SVT launches of
+ *   tsvt_dct, tnn_complete and tnn_admm_iterate on ctx record, per slice and
+ *   sweep, the counts and largest rotations that drive the stopping rules
+ *   (read with tnn_last_sweep_log; the buffer is device memory the context
+ *   allocates); 0 (default) = no log.  A tracing aid: the log costs a
+ *   device clear per launch.
  * Returns TNN_EINVAL for an unknown option or a value out of range. */
 #define TNN_OPT_JACOBI_MAX_SWEEPS 1
 #define TNN_OPT_TC_WAIT_POLLS 2
 #define TNN_OPT_JACOBI_FP64_ANGLES 3
 #define TNN_OPT_ADMM_WARM_START 4
+#define TNN_OPT_JACOBI_SMALL_STOP 5
+#define TNN_OPT_JACOBI_SWEEP_LOG 6
 tnn_status tnn_set_option(tnn_ctx* ctx, int option, int64_t value);
 
 enum { TNN_OP_TDCT3 = 0, TNN_OP_TSVT = 1, TNN_OP_TSVD = 2, TNN_OP_TPROD = 3, TNN_OP_COMPLETE = 4 };
@@ -250,6 +266,27 @@ tnn_status tnn_admm_warm_size(tnn_shape shape, tnn_precision prec, size_t* bytes
  * still counted as visited (their dot products are computed).
  * Synchronises the last stream used. */
 tnn_status tnn_last_jacobi_stats(tnn_ctx* ctx, int64_t out[6]);
+
+/* Per-slice statistics of the same launch as tnn_last_jacobi_stats: for each
+ * slice k < min(n, slices), sweeps[k] (sweeps run), kept[k] (singular values
+ * above tau) and rotations[k] (rotations applied).  Host arrays of n
+ * entries, any of them NULL to skip it; entries k >= slices are left alone.
+ * TNN_EINVAL for a null ctx or n < 0; all zero-work (nothing written) when
+ * no Jacobi launch has run on ctx.  Synchronises the last stream used. */
+tnn_status tnn_last_slice_stats(tnn_ctx* ctx, int64_t n, int32_t* sweeps, int32_t* kept, int64_t* rotations);
+
+/* The per-sweep log of the last Jacobi launch on ctx, recorded when
+ * TNN_OPT_JACOBI_SWEEP_LOG was 1 for it: for each slice k < min(n, slices)
+ * and sweep s < 8, six floats at out[(k * 8 + s) * 6 ...]: the sweep's big
+ * rotations (|gamma| > 2 tol sqrt(alpha beta)), its wide rotations (those
+ * that block the small-rotation stop), its big rotations between two
+ * columns below tau, the largest |gamma| / sqrt(alpha beta) of its big
+ * rotations, the largest |t| of its big rotations and the largest |t| of
+ * all its rotations; all zero for sweeps not run (and for slices spread over
+ * a cluster, which keep no log).  out is a host array of n * 48 floats.
+ * TNN_EINVAL if the last launch kept no log.  Synchronises the last stream
+ * used. */
+tnn_status tnn_last_sweep_log(tnn_ctx* ctx, int64_t n, float* out);
 
 /* tsvt_dct without a context and without any device allocation (no
  * counterpart in the paper).  For callers that cannot allocate device memory

@@ -28,6 +28,11 @@ struct tnn_ctx {
     int opt_jacobi_sweeps = 0;   // TNN_OPT_JACOBI_MAX_SWEEPS (0: the kernels' default)
     int opt_tc_polls = -1;       // TNN_OPT_TC_WAIT_POLLS (negative: the default limit)
     int opt_angle64 = 0;         // TNN_OPT_JACOBI_FP64_ANGLES
+    int opt_small_stop = 1;      // TNN_OPT_JACOBI_SMALL_STOP
+    int opt_sweep_log = 0;       // TNN_OPT_JACOBI_SWEEP_LOG
+    float* d_sweep_log = nullptr;  // the log's device buffer (grown on demand)
+    int64_t sweep_log_cap = 0;   // slices it holds
+    float* last_sweep_log = nullptr;  // the log of the last Jacobi launch, if it kept one
     int opt_warm = 1;            // TNN_OPT_ADMM_WARM_START (tnn_complete)
     SliceStats* last_stats = nullptr;
     int64_t last_n3 = 0;
@@ -311,6 +316,7 @@ void tnn_destroy(tnn_ctx* ctx)
     for (auto& kv : ctx->ops) cudaFree(kv.second);
     for (auto& kv : ctx->tc_ops) cudaFree(kv.second);
     if (ctx->d_err) cudaFree(ctx->d_err);
+    if (ctx->d_sweep_log) cudaFree(ctx->d_sweep_log);
     for (auto& r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : ctx->pool) cudaEventDestroy(e);
     if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
@@ -336,6 +342,14 @@ tnn_status tnn_set_option(tnn_ctx* ctx, int option, int64_t value)
     case TNN_OPT_ADMM_WARM_START:
         if (value != 0 && value != 1) return fail(ctx, TNN_EINVAL, "warm-start flag must be 0 or 1");
         ctx->opt_warm = (int)value;
+        return TNN_OK;
+    case TNN_OPT_JACOBI_SMALL_STOP:
+        if (value != 0 && value != 1) return fail(ctx, TNN_EINVAL, "small-rotation stop flag must be 0 or 1");
+        ctx->opt_small_stop = (int)value;
+        return TNN_OK;
+    case TNN_OPT_JACOBI_SWEEP_LOG:
+        if (value != 0 && value != 1) return fail(ctx, TNN_EINVAL, "sweep-log flag must be 0 or 1");
+        ctx->opt_sweep_log = (int)value;
         return TNN_OK;
     default: return fail(ctx, TNN_EINVAL, "unknown option %d", option);
     }
@@ -482,6 +496,24 @@ tnn_status tdct3(tnn_ctx* ctx, const void* X, tnn_shape sh, int inverse, int sca
     return sg.finish();
 }
 
+// TNN_OPT_JACOBI_SWEEP_LOG: the plan's log buffer (sweep_log_floats per
+// slice, grown here, outside any stream capture; the launches that use it
+// clear it first); none when the option is off.
+static tnn_status attach_sweep_log(tnn_ctx* ctx, JacobiPlan& jp)
+{
+    jp.sweep_log = nullptr;
+    if (!ctx->opt_sweep_log) return TNN_OK;
+    if (jp.n3 > ctx->sweep_log_cap) {
+        if (ctx->d_sweep_log) CK(cudaFree(ctx->d_sweep_log));
+        ctx->d_sweep_log = nullptr;
+        ctx->sweep_log_cap = 0;
+        CK(cudaMalloc(&ctx->d_sweep_log, sizeof(float) * sweep_log_floats * (size_t)jp.n3));
+        ctx->sweep_log_cap = jp.n3;
+    }
+    jp.sweep_log = ctx->d_sweep_log;
+    return TNN_OK;
+}
+
 tnn_status tsvt_dct(tnn_ctx* ctx, const void* Z, tnn_shape sh, double tau, tnn_precision prec, void* Y,
                     double* tnn_out, void* stream)
 {
@@ -496,6 +528,8 @@ tnn_status tsvt_dct(tnn_ctx* ctx, const void* Z, tnn_shape sh, double tau, tnn_p
     if (!jacobi_plan(sh.n1, sh.n2, sh.n3, elem, &jp)) return fail(ctx, TNN_EINVAL, "slice %lldx%lld too large",
                                                                 (long long)sh.n1, (long long)sh.n2);
     jp.angle64 = ctx->opt_angle64;
+    jp.small_stop = ctx->opt_small_stop;
+    if ((st = attach_sweep_log(ctx, jp))) return st;
     const size_t bytes = (size_t)sh.n1 * sh.n2 * sh.n3 * elem;
     Arg az = make_arg(Z, bytes), ay = make_arg(Y, bytes);
     Carve cv;
@@ -518,6 +552,7 @@ tnn_status tsvt_dct(tnn_ctx* ctx, const void* Z, tnn_shape sh, double tau, tnn_p
     {
         TRACE(K_JACOBI_SVT);
         const int sw = ctx->opt_jacobi_sweeps;
+        if (jp.sweep_log) CK(cudaMemsetAsync(jp.sweep_log, 0, sizeof(float) * sweep_log_floats * sh.n3, s));
         if (elem == 8) CK(launch_jacobi_svt<double>(jp, (double*)W, tau, nullptr, sw, at(ctx, ojw), stats, s));
         else CK(launch_jacobi_svt<float>(jp, (float*)W, tau, nullptr, sw, at(ctx, ojw), stats, s));
     }
@@ -525,6 +560,7 @@ tnn_status tsvt_dct(tnn_ctx* ctx, const void* Z, tnn_shape sh, double tau, tnn_p
         TRACE(K_TUBE);
         CK(tube_any(ctx, elem, W, ay.dev, opi, P, sh.n3, s));
     }
+    ctx->last_sweep_log = jp.sweep_log;
     ctx->last_stats = stats;
     ctx->last_n3 = sh.n3;
     ctx->last_stream = s;
@@ -581,6 +617,7 @@ tnn_status tsvd_dct_forward(tnn_ctx* ctx, const void* X, tnn_shape sh, tnn_preci
     CK(tube_any(ctx, elem, Uh, au.dev, opi, sh.n1 * r, sh.n3, s));
     CK(tube_any(ctx, elem, Vh, av.dev, opi, sh.n2 * r, sh.n3, s));
     CK(tube_any(ctx, elem, Sh, as.dev, opi, r, sh.n3, s));
+    ctx->last_sweep_log = nullptr;
     ctx->last_stats = stats;
     ctx->last_n3 = sh.n3;
     ctx->last_stream = s;
@@ -724,6 +761,8 @@ tnn_status admm_enqueue_iters(tnn_ctx* ctx, const AdmmJob& j, int iters, cudaStr
               CK(launch_tube_fwd_admm_op<double>((const double*)j.X, (const double*)j.M, (double*)j.W,
                                                  (const double*)opf.op, P, n3, j.ctl, s)); }
             { TRACE(K_JACOBI_SVT);
+              if (j.jp.sweep_log)
+                  CK(cudaMemsetAsync(j.jp.sweep_log, 0, sizeof(float) * sweep_log_floats * n3, s));
               CK(launch_jacobi_svt<double>(j.jp, (double*)j.W, 0.0, j.ctl, sweeps, j.jwork, j.stats, s)); }
             { TRACE(K_TUBE_INV_ADMM);
               CK(launch_tube_inv_admm_op<double>((const double*)j.W, (double*)j.X, (double*)j.M, (const double*)j.B,
@@ -746,6 +785,8 @@ tnn_status admm_enqueue_iters(tnn_ctx* ctx, const AdmmJob& j, int iters, cudaStr
                 CK(launch_warm_gemm<float>(j.jp, (const float*)j.W, Q, wflag, (float*)j.wscr, j.ctl, s));
             }
             { TRACE(K_JACOBI_SVT);
+              if (j.jp.sweep_log)
+                  CK(cudaMemsetAsync(j.jp.sweep_log, 0, sizeof(float) * sweep_log_floats * n3, s));
               const WarmPtrs wp{j.wscr, wflag, j.wscr, j.wrec};
               CK(launch_jacobi_svt<float>(j.jp, (float*)j.W, 0.0, j.ctl, sweeps, j.jwork, j.stats, s,
                                           warm ? &wp : nullptr)); }
@@ -791,6 +832,7 @@ tnn_status admm_run(tnn_ctx* ctx, AdmmJob& j, double beta0, int max_iter, cudaSt
     }
     if ((st = check_tc_error(ctx))) return st;
     *out = *ctx->h_ctl;
+    ctx->last_sweep_log = j.jp.sweep_log;
     ctx->last_stats = j.stats;
     ctx->last_n3 = j.sh.n3;
     ctx->last_stream = s;
@@ -836,6 +878,8 @@ tnn_status tnn_complete(tnn_ctx* ctx, const void* B, const uint8_t* mask, tnn_sh
     JacobiPlan jp;
     if (!jacobi_plan(sh.n1, sh.n2, sh.n3, elem, &jp)) return fail(ctx, TNN_EINVAL, "slice too large");
     jp.angle64 = ctx->opt_angle64;
+    jp.small_stop = ctx->opt_small_stop;
+    if ((st = attach_sweep_log(ctx, jp))) return st;
     const size_t N = (size_t)sh.n1 * sh.n2 * sh.n3, bytes = N * elem;
     Arg ab = make_arg(B, bytes), am = make_arg(mask, N), ax = make_arg(X_out, bytes);
     const int nparts = tube_partials_count(sh.n1 * sh.n2, sh.n3);
@@ -894,6 +938,8 @@ tnn_status tnn_admm_iterate(tnn_ctx* ctx, const void* B, const uint8_t* mask, tn
     JacobiPlan jp;
     if (!jacobi_plan(sh.n1, sh.n2, sh.n3, elem, &jp)) return fail(ctx, TNN_EINVAL, "slice too large");
     jp.angle64 = ctx->opt_angle64;
+    jp.small_stop = ctx->opt_small_stop;
+    if ((st = attach_sweep_log(ctx, jp))) return st;
     const size_t N = (size_t)sh.n1 * sh.n2 * sh.n3, bytes = N * elem;
     Arg ab = make_arg(B, bytes), am = make_arg(mask, N), ax = make_arg(X, bytes), amm = make_arg(M, bytes);
     const int nparts = tube_partials_count(sh.n1 * sh.n2, sh.n3);
@@ -1027,6 +1073,7 @@ static tnn_status tsvt_plain_run(tnn_ctx* ctx, const void* Z, tnn_shape sh, doub
                          : launch_tube_op<float>((const float*)W, (float*)Y, (const float*)opi, P, n3, s));
         }
     }
+    ctx->last_sweep_log = nullptr;
     ctx->last_stats = stats;
     ctx->last_n3 = nsl;
     ctx->last_stream = s;
@@ -1078,6 +1125,37 @@ tnn_status tnn_last_jacobi_stats(tnn_ctx* ctx, int64_t out[6])
         if (x.sweeps > out[3]) out[3] = x.sweeps;
         out[4] += x.converged ? 0 : 1;
         out[5] += x.kept;
+    }
+    return TNN_OK;
+}
+
+tnn_status tnn_last_sweep_log(tnn_ctx* ctx, int64_t n, float* out)
+{
+    if (!ctx || n < 0 || (n > 0 && !out)) return TNN_EINVAL;
+    if (!ctx->last_stats || !ctx->last_sweep_log) return fail(ctx, TNN_EINVAL, "no sweep log was recorded");
+    tnn_status st = set_device(ctx);
+    if (st) return st;
+    const int64_t cnt = n < ctx->last_n3 ? n : ctx->last_n3;
+    CK(cudaStreamSynchronize(ctx->last_stream));
+    if (cnt > 0)
+        CK(cudaMemcpy(out, ctx->last_sweep_log, sizeof(float) * sweep_log_floats * cnt, cudaMemcpyDeviceToHost));
+    return TNN_OK;
+}
+
+tnn_status tnn_last_slice_stats(tnn_ctx* ctx, int64_t n, int32_t* sweeps, int32_t* kept, int64_t* rotations)
+{
+    if (!ctx || n < 0) return TNN_EINVAL;
+    if (!ctx->last_stats || n == 0) return TNN_OK;
+    tnn_status st = set_device(ctx);
+    if (st) return st;
+    std::vector<SliceStats> h((size_t)ctx->last_n3);
+    CK(cudaStreamSynchronize(ctx->last_stream));
+    CK(cudaMemcpy(h.data(), ctx->last_stats, sizeof(SliceStats) * ctx->last_n3, cudaMemcpyDeviceToHost));
+    const int64_t cnt = n < ctx->last_n3 ? n : ctx->last_n3;
+    for (int64_t k = 0; k < cnt; ++k) {
+        if (sweeps) sweeps[k] = h[(size_t)k].sweeps;
+        if (kept) kept[k] = h[(size_t)k].kept;
+        if (rotations) rotations[k] = h[(size_t)k].rotations;
     }
     return TNN_OK;
 }

@@ -170,6 +170,8 @@ struct Counters {
     int rots;
     int big;
     int bigll;  // the part of big whose two columns both had squared norms below tau^2
+    int wide;   // rotations applied with |gamma| / sqrt(alpha beta) or |t| above theta (the small-rotation stop)
+    float cbig, tbig, tall;  // sweep log: largest |gamma| / sqrt(alpha beta) and |t| of the big rotations, |t| of all
 };
 
 // Registers of one group: 2K columns of A (and of V when WITHV), with the
@@ -282,7 +284,7 @@ __device__ __forceinline__ void recompute_norm(Regs<T, K, R, WITHV>& S, int c)
 // sweep's set of small columns); a pair of two flagged columns is left alone.
 template <typename T, int K, int R, int L, bool WITHV, bool CROSS, int r>
 __device__ __forceinline__ void do_round(Regs<T, K, R, WITHV>& S, const T tol, const int hl, Counters& cnt,
-                                         const unsigned lm, const bool a64, const T tau2)
+                                         const unsigned lm, const bool a64, const T tau2, const T theta)
 {
     constexpr int G = L / K;
     const int slot = hl / G;
@@ -308,15 +310,19 @@ __device__ __forceinline__ void do_round(Regs<T, K, R, WITHV>& S, const T tol, c
     }
     const T gam = (di * dj) * gs;
     T t1 = T(0), t2 = T(0), cc = T(1), tg = T(0);
-    bool bigp, rotp;
+    bool bigp, rotp, widep = false;
     if (a64) {
         const double off = lo ? 0.0 : off64((double)ai, (double)aj, (double)gam);
         bigp = off > 2.0 * (double)tol;
         rotp = off > (double)tol;
+        widep = off > (double)theta;
+        if (bigp) cnt.cbig = fmaxf(cnt.cbig, (float)off);
     } else {
         const T off = lo ? T(0) : fabs(gam) * rsqrt(ai) * rsqrt(aj);
         bigp = off > T(2) * tol;
         rotp = off > tol;  // false for a zero column (0 * inf = NaN) and for a carried norm gone negative
+        widep = off > theta;
+        if (bigp) cnt.cbig = fmaxf(cnt.cbig, (float)off);
     }
     if (rotp) {
         if (a64) {
@@ -326,12 +332,20 @@ __device__ __forceinline__ void do_round(Regs<T, K, R, WITHV>& S, const T tol, c
             t2 = (T)(t * ((double)di / (double)dj));
             cc = (T)c;
             tg = (T)(t * (double)gam);
+            widep = widep || fabs(t) > (double)theta;
+            cnt.tall = fmaxf(cnt.tall, (float)fabs(t));
+            if (bigp) cnt.tbig = fmaxf(cnt.tbig, (float)fabs(t));
         } else {
             T t, c;
             rot_params(ai, aj, gam, t, c);
             rot_factors(t, di, dj, t1, t2, cc);
             tg = t * gam;
+            widep = widep || fabs(t) > theta;
+            cnt.tall = fmaxf(cnt.tall, (float)fabs(t));
+            if (bigp) cnt.tbig = fmaxf(cnt.tbig, (float)fabs(t));
         }
+    } else {
+        widep = false;
     }
     T T1[K], T2[K], CC[K], TG[K];
 #pragma unroll
@@ -345,6 +359,7 @@ __device__ __forceinline__ void do_round(Regs<T, K, R, WITHV>& S, const T tol, c
         ++cnt.big;
         if (ai < tau2 && aj < tau2) ++cnt.bigll;
     }
+    if (widep && hl % G == 0) ++cnt.wide;
     if (hl == 0) cnt.pairs += K;
     unsigned need = 0;
 #pragma unroll
@@ -398,7 +413,8 @@ struct Slot {
 // (t1, t2) by shuffles.
 template <typename T, int K, int R, int L, bool WITHV, int r>
 __device__ __forceinline__ void cross_round(Regs<T, K, R, WITHV>& S, Slot<T>& st, const T tol, const int hl,
-                                            Counters& cnt, const unsigned lm, const bool a64, const T tau2)
+                                            Counters& cnt, const unsigned lm, const bool a64, const T tau2,
+                                            const T theta)
 {
     constexpr int G = L / K;
     const int slot = hl / G;
@@ -413,15 +429,19 @@ __device__ __forceinline__ void cross_round(Regs<T, K, R, WITHV>& S, Slot<T>& st
     T t1 = T(0), t2 = T(0);
     bool needI = false, needJ = false;
     const unsigned lo = (lm >> slot) & (lm >> (K + (slot + r) % K)) & 1u;
-    bool bigp, rotp;
+    bool bigp, rotp, widep;
     if (a64) {
         const double off = lo ? 0.0 : off64((double)st.aI, (double)st.aJ, (double)gam);
         bigp = off > 2.0 * (double)tol;
         rotp = off > (double)tol;
+        widep = off > (double)theta;
+        if (bigp) cnt.cbig = fmaxf(cnt.cbig, (float)off);
     } else {
         const T off = lo ? T(0) : fabs(gam) * rsqrt(st.aI) * rsqrt(st.aJ);
         bigp = off > T(2) * tol;
         rotp = off > tol;  // false for a zero column (0 * inf = NaN) and for a carried norm gone negative
+        widep = off > theta;
+        if (bigp) cnt.cbig = fmaxf(cnt.cbig, (float)off);
     }
     if (bigp && hl % G == 0) {
         ++cnt.big;
@@ -436,12 +456,19 @@ __device__ __forceinline__ void cross_round(Regs<T, K, R, WITHV>& S, Slot<T>& st
             t2 = (T)(td * ((double)st.dI / (double)st.dJ));
             c = (T)cd;
             tg = (T)(td * (double)gam);
+            widep = widep || fabs(td) > (double)theta;
+            cnt.tall = fmaxf(cnt.tall, (float)fabs(td));
+            if (bigp) cnt.tbig = fmaxf(cnt.tbig, (float)fabs(td));
         } else {
             T t;
             rot_params(st.aI, st.aJ, gam, t, c);
             rot_factors(t, st.dI, st.dJ, t1, t2, c);
             tg = t * gam;
+            widep = widep || fabs(t) > theta;
+            cnt.tall = fmaxf(cnt.tall, (float)fabs(t));
+            if (bigp) cnt.tbig = fmaxf(cnt.tbig, (float)fabs(t));
         }
+        if (widep && hl % G == 0) ++cnt.wide;
         const T oI = st.aI, oJ = st.aJ;
         st.aI = oI - tg;
         st.aJ = oJ + tg;
@@ -514,17 +541,17 @@ __device__ __forceinline__ void cross_round(Regs<T, K, R, WITHV>& S, Slot<T>& st
 template <typename T, int K, int R, int L, bool WITHV, int... Rs>
 __device__ __forceinline__ void cross_rounds(Regs<T, K, R, WITHV>& S, Slot<T>& st, const T tol, const int hl,
                                              Counters& cnt, std::integer_sequence<int, Rs...>, const unsigned lm = 0u,
-                                             const bool a64 = false, const T tau2 = T(0))
+                                             const bool a64 = false, const T tau2 = T(0), const T theta = T(0))
 {
-    (cross_round<T, K, R, L, WITHV, Rs>(S, st, tol, hl, cnt, lm, a64, tau2), ...);
+    (cross_round<T, K, R, L, WITHV, Rs>(S, st, tol, hl, cnt, lm, a64, tau2, theta), ...);
 }
 
 template <typename T, int K, int R, int L, bool WITHV, bool CROSS, int... Rs>
 __device__ __forceinline__ void do_rounds(Regs<T, K, R, WITHV>& S, const T tol, const int hl, Counters& cnt,
                                           std::integer_sequence<int, Rs...>, const unsigned lm = 0u,
-                                          const bool a64 = false, const T tau2 = T(0))
+                                          const bool a64 = false, const T tau2 = T(0), const T theta = T(0))
 {
-    (do_round<T, K, R, L, WITHV, CROSS, Rs>(S, tol, hl, cnt, lm, a64, tau2), ...);
+    (do_round<T, K, R, L, WITHV, CROSS, Rs>(S, tol, hl, cnt, lm, a64, tau2, theta), ...);
 }
 
 // Load the 2K columns of blocks bI, bJ into the group's registers and the
@@ -720,6 +747,8 @@ struct KArgs {
     const int* wflag;
     T* vrec;
     int* wrec;
+    int small_stop;     // 1: stop after a sweep of small rotations only (see theta in the kernel)
+    float* sweep_log;   // optional: per slice and sweep s < kSweepLogSweeps, kSweepLogVals values (see the sweep loop)
 };
 
 // Shared-memory carve-up (bytes) for a launch: dsc, sig, cf, carried norms
@@ -786,7 +815,8 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
     int* kidx = reinterpret_cast<int*>(anorm + npad);
     int* rank = kidx + npad;
     T* gbuf = reinterpret_cast<T*>(rank + npad);
-    __shared__ int s_rot, s_rotll, s_keep, s_nonfinite, s_nlo, s_cnt;
+    __shared__ int s_rot, s_rotll, s_wide, s_keep, s_nonfinite, s_nlo, s_cnt;
+    __shared__ int s_lg[3];
     __shared__ double s_nuc, s_fro, s_lo, s_s1, s_yn;
     __shared__ unsigned long long s_maxb;  // bits of a nonnegative double (ordered as integers)
     __shared__ unsigned long long s_pairs, s_rots;
@@ -857,8 +887,21 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
     // columns' alphas still sum below tau^2 (a rotation with a column that
     // has shrunk below them can grow them); otherwise full sweeps follow.
     const T tol = sqrt((T)m) * Num<T>::unit();
+    // The small-rotation stop.  A pair rotated in a sweep is left orthogonal
+    // to rounding; a later rotation of one of its columns with a third
+    // column k by the tangent t changes the pair's normalised dot product by
+    // at most about max(|t|, |gamma_ik| / sqrt(alpha_i alpha_k)) times column
+    // k's normalised dot product with the other column (the column-norm
+    // ratio that enters is offset by the small angle: t ~ gamma / (alpha_k -
+    // alpha_i)), and each column meets fewer than n partners in a sweep.  So
+    // a sweep whose rotations all had both quantities at most theta leaves
+    // every pair within tol + 4 n theta^2 of orthogonal, and with theta =
+    // sqrt(tol / (4 n)) within 2 tol: the level the stopping rule (no
+    // rotation above 2 tol in a sweep) accepts, without the extra sweep that
+    // rule spends confirming it.  theta = 0 turns the stop off.
+    const T theta = a.small_stop ? sqrt(tol / (T(4) * (T)n)) : T(0);
     constexpr bool a64 = A64 && sizeof(T) == 4;
-    Counters cnt{0, 0, 0};
+    Counters cnt{0, 0, 0, 0, 0, 0.f, 0.f, 0.f};
     int sweeps = 0, converged = skip ? 1 : 0;
     const int max_sweeps = a.max_sweeps > 0 ? a.max_sweeps : 30;
     const int npairs = nb / 2;
@@ -971,7 +1014,8 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
         }
     }
     while (!skip && sweeps < max_sweeps) {
-        if (tid == 0) { s_rot = 0; s_rotll = 0; s_lo = 0.0; s_nlo = 0; }
+        if (tid == 0) { s_rot = 0; s_rotll = 0; s_wide = 0; s_lo = 0.0; s_nlo = 0; s_lg[0] = s_lg[1] = s_lg[2] = 0; }
+        cnt.cbig = cnt.tbig = cnt.tall = 0.f;
         __syncthreads();
         if (!full_only || gmode) {
             // columns flagged: below tau^2 / 4 (small-column sweeps) or, with
@@ -997,7 +1041,7 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
         // flagged sweeps only where they pay: most columns flagged (a few
         // tiny columns save nothing and can cost a closing full sweep)
         const bool partial = gmode || (!full_only && s_lo <= 0.9 * tau_s * tau_s && 2 * s_nlo >= n);
-        const int big0 = cnt.big, bigll0 = cnt.bigll;
+        const int big0 = cnt.big, bigll0 = cnt.bigll, wide0 = cnt.wide;
         // one sweep; compiled twice, so that a sweep without flagged columns
         // runs code without the flag tests
         auto sweep = [&](auto flagged) {
@@ -1024,11 +1068,12 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
                     if (step == 0) {
                         gather_state<T, K, R, L, WITHV>(Sr, st);
                         do_rounds<T, K, R, L, WITHV, false>(Sr, tol, hl, cnt,
-                                                            std::make_integer_sequence<int, K - 1>{}, lm, a64, tau2);
+                                                            std::make_integer_sequence<int, K - 1>{}, lm, a64, tau2,
+                                                            theta);
                         scatter_state<T, K, R, L, WITHV>(Sr, st, hl);
                     }
                     cross_rounds<T, K, R, L, WITHV>(Sr, st, tol, hl, cnt, std::make_integer_sequence<int, K>{}, lm,
-                                                    a64, tau2);
+                                                    a64, tau2, theta);
                     store_cols<T, K, R, L, WITHV>(Sr, st, Aw, Aw, Vw, dsc, dsc, ldA, bI, bJ, hl, active, anorm);
                     if (!active) cnt = cnt0;  // an inactive group's work is discarded, and so are its counts
                 }
@@ -1039,10 +1084,28 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
         else sweep(std::false_type{});
         if (cnt.big != big0) atomicAdd(&s_rot, cnt.big - big0);
         if (cnt.bigll != bigll0) atomicAdd(&s_rotll, cnt.bigll - bigll0);
+        if (cnt.wide != wide0) atomicAdd(&s_wide, cnt.wide - wide0);
+        if (a.sweep_log) {  // the sweep's largest rotations, as float bits (nonnegative: ordered as integers)
+            atomicMax(&s_lg[0], __float_as_int(cnt.cbig));
+            atomicMax(&s_lg[1], __float_as_int(cnt.tbig));
+            atomicMax(&s_lg[2], __float_as_int(cnt.tall));
+        }
         __syncthreads();
         const int nrot = s_rot, nrotll = s_rotll;
+        if (a.sweep_log && tid == 0 && sweeps < kSweepLogSweeps && !item) {
+            // big rotations, wide ones (the small-rotation stop), big low-low
+            // ones, largest |gamma| / sqrt(alpha beta) of the big ones,
+            // largest |t| of the big ones and of all
+            float* lg = a.sweep_log + ((size_t)slice * kSweepLogSweeps + sweeps) * kSweepLogVals;
+            lg[0] = (float)nrot; lg[1] = (float)s_wide; lg[2] = (float)nrotll;
+            lg[3] = __int_as_float(s_lg[0]); lg[4] = __int_as_float(s_lg[1]); lg[5] = __int_as_float(s_lg[2]);
+        }
         ++sweeps;
-        bool done = nrot == 0;
+        // converged: no big rotation in the sweep, or only small ones (every
+        // rotation applied had |gamma| / sqrt(alpha beta) <= theta and
+        // |t| <= theta, so what they left between any two columns is at most
+        // about 4 n theta^2 <= tol; see theta above)
+        bool done = nrot == 0 || s_wide == 0;
         if (done && partial && !gmode) {
             // the flagged columns' alphas after the sweep
             if (tid == 0) s_lo = 0.0;

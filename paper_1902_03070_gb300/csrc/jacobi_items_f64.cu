@@ -13,7 +13,7 @@ cudaError_t launch_jacobi_svt_items<double>(const JacobiPlan& plan, const SliceI
     jac::KArgs<double> a{};
     a.items = items;
     a.nb = p.nb; a.ldA = p.ldA; a.n3 = count;
-    a.max_sweeps = max_sweeps;
+    a.max_sweeps = max_sweeps; a.small_stop = p.small_stop;
     a.work = reinterpret_cast<double*>(work);
     if (p.cluster > 1) return launch_jacobi_svt_cluster<double>(p, a, true, s);
     switch (p.L * 1000 + p.RA * 10 + p.K) {

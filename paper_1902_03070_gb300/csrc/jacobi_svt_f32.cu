@@ -12,7 +12,7 @@ cudaError_t launch_jacobi_svt<float>(const JacobiPlan& p, float* data, double ta
     jac::KArgs<float> a{};
     a.data = data; a.n1 = p.n1; a.n2 = p.n2; a.n3 = p.n3;
     a.m = p.m; a.n = p.n; a.tr = p.tr; a.nb = p.nb; a.ldA = p.ldA;
-    a.tau = tau; a.ctl = ctl; a.max_sweeps = max_sweeps;
+    a.tau = tau; a.ctl = ctl; a.max_sweeps = max_sweeps; a.small_stop = p.small_stop; a.sweep_log = p.sweep_log;
     a.work = reinterpret_cast<float*>(work); a.stats = stats;
     if (warm) {
         a.w0 = static_cast<const float*>(warm->w0);

@@ -12,7 +12,7 @@ cudaError_t launch_jacobi_svt<double>(const JacobiPlan& p, double* data, double 
     jac::KArgs<double> a{};
     a.data = data; a.n1 = p.n1; a.n2 = p.n2; a.n3 = p.n3;
     a.m = p.m; a.n = p.n; a.tr = p.tr; a.nb = p.nb; a.ldA = p.ldA;
-    a.tau = tau; a.ctl = ctl; a.max_sweeps = max_sweeps;
+    a.tau = tau; a.ctl = ctl; a.max_sweeps = max_sweeps; a.small_stop = p.small_stop; a.sweep_log = p.sweep_log;
     a.work = reinterpret_cast<double*>(work); a.stats = stats;
     if (p.cluster > 1) return launch_jacobi_svt_cluster<double>(p, a, false, s);
     switch (p.L * 1000 + p.RA * 10 + p.K) {

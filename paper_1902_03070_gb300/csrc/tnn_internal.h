@@ -30,6 +30,12 @@ struct AdmmCtl {
 };
 
 // Per-slice Jacobi statistics, written by the SVT/SVD kernels.
+// Per-sweep log of the single-CTA Jacobi SVT (TNN_OPT_JACOBI_SWEEP_LOG): for
+// each slice and sweep s < kSweepLogSweeps, kSweepLogVals floats.
+constexpr int kSweepLogSweeps = 8;
+constexpr int kSweepLogVals = 6;
+constexpr int sweep_log_floats = kSweepLogSweeps * kSweepLogVals;
+
 struct SliceStats {
     double nuc;        // sum_i (sigma_i - tau)_+ of the slice
     int64_t pairs;     // column pairs visited
@@ -127,6 +133,8 @@ struct JacobiPlan {
     int elem;          // sizeof(T)
     int cluster;       // > 1: each slice spread over a cluster of this many CTAs (SVT only)
     int angle64 = 0;   // FP32 SVT of slices in shared memory: rotation angles and convergence tests in FP64
+    int small_stop = 1; // Jacobi: stop after a sweep whose rotations were all small (KArgs::small_stop)
+    float* sweep_log = nullptr;  // single-CTA SVT: per-sweep rotation log (KArgs::sweep_log), or none
 };
 
 // Plan a Jacobi launch for n1 x n2 slices of element size elem (4 or 8).

@@ -26,56 +26,97 @@
 namespace tnn {
 namespace {
 
-constexpr int WT = 256;   // threads per CTA of the QR
-constexpr int WTG = 384;  // threads per CTA of the GEMM (12 warps)
-constexpr int WCB = 6;    // output columns per warp pass of the GEMM
+constexpr int WQ = 512;   // threads per CTA of the QR (16 warps)
+constexpr int WGM = 640;  // most threads per CTA of the GEMM (20 warps)
+constexpr int WCB = 8;    // output columns per warp tile of the GEMM
 constexpr int WMR = 8;    // most rows per lane of the GEMM (m <= 256)
-constexpr int WQR = 7;    // rows per lane of a Q column (n <= 224)
+constexpr int WQN = 224; // most columns of the QR (28 rows per lane)
 
+// Leading dimensions of the GEMM's shared-memory operands: A is held with
+// lda = 32 MR + 1 rows (odd, so that the transposing stores of a slice with
+// tr = 1 hit distinct banks; rows m..32 MR - 1 are zero), and Q transposed,
+// Qt[j * ldq + c] = Q[c * n + j], with ldq = n rounded up to the tile width
+// plus 4 (a multiple of 4 floats, so each warp reads its 8 entries of a row
+// as two 16-byte loads; columns n.. are zero).
+__host__ __device__ inline int gemm_lda(int mr) { return 32 * mr + 1; }
+__host__ __device__ inline int gemm_ldq(int n) { return (n + WCB - 1) / WCB * WCB + 4; }
+
+// Cooperative copy of `cols` columns of `rows` elements (source column j at
+// src + j * lds) into shared memory: dst[j * ldd + i] (tr: dst[i * ldd + j]).
+// A warp takes eight columns at a time, lanes over the rows, so each thread
+// keeps eight loads in flight.
+template <typename T>
+__device__ __forceinline__ void load_cols(T* dst, int ldd, const T* __restrict__ src, int64_t lds, int rows,
+                                          int cols, bool tr, int warp, int W, int lane)
+{
+    constexpr int U = 8;
+    for (int j0 = warp * U; j0 < cols; j0 += W * U)
+        for (int i = lane; i < rows; i += 32) {
+            T v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) v[u] = (j0 + u < cols) ? src[(size_t)(j0 + u) * lds + i] : T(0);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (j0 + u >= cols) break;
+                if (tr) dst[(size_t)i * ldd + j0 + u] = v[u];
+                else dst[(size_t)(j0 + u) * ldd + i] = v[u];
+            }
+        }
+}
+
+// W0 = A0 Q for one slice per CTA, both operands in shared memory; each warp
+// computes 32 MR x 8 output tiles (lane rows r = 32 q + lane, eight columns),
+// so one k step costs MR + 2 shared loads for 8 MR FMAs.
 template <typename T, int MR>
-__global__ void __launch_bounds__(WTG) warm_gemm_kernel(const T* __restrict__ data, int64_t n1, int64_t n2, int m,
+__global__ void __launch_bounds__(WGM) warm_gemm_kernel(const T* __restrict__ data, int64_t n1, int64_t n2, int m,
                                                       int n, int tr, int ldA, int npad, size_t stride,
                                                       const T* __restrict__ Q, const int* __restrict__ flag,
                                                       T* __restrict__ w0, const AdmmCtl* __restrict__ ctl)
 {
+    static_assert(sizeof(T) == 4, "FP32 only");
     if (ctl && ctl->done) return;
     const int k = blockIdx.x;
     if (!flag[k]) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* As = reinterpret_cast<T*>(smem_raw);  // oriented slice, column j at As + j * m
-    T* Qs = As + (size_t)m * n;              // Q_k, column c at Qs + c * n
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = WTG / 32;
-    const T* src = data + (size_t)k * n1 * n2;
-    const int64_t S = n1 * n2;
-    for (int64_t e = tid; e < S; e += WTG) {
-        const int i = (int)(e % n1), j = (int)(e / n1);
-        const int r = tr ? j : i, c = tr ? i : j;
-        As[(size_t)c * m + r] = src[e];
-    }
-    const T* Qk = Q + (size_t)k * n * n;
-    for (int e = tid; e < n * n; e += WTG) Qs[e] = Qk[e];
+    constexpr int lda = 32 * MR + 1;
+    const int ldq = gemm_ldq(n);
+    T* As = reinterpret_cast<T*>(smem_raw);             // column c at As + c * lda
+    T* Qt = As + ((size_t)lda * n + 3) / 4 * 4;         // row j (all c) at Qt + j * ldq
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = blockDim.x >> 5;
+    // the oriented slice (source columns j, n1 rows each; tr: A's rows) and
+    // Q transposed (4-way bank conflicts on those stores), zero-padded
+    load_cols(As, lda, data + (size_t)k * n1 * n2, n1, (int)n1, (int)n2, tr != 0, warp, W, lane);
+    load_cols(Qt, ldq, Q + (size_t)k * n * n, n, n, n, true, warp, W, lane);
+    for (int c = warp; c < n; c += W)
+        for (int r = m + lane; r < 32 * MR; r += 32) As[(size_t)c * lda + r] = T(0);
+    for (int j = warp; j < n; j += W)
+        for (int c = n + lane; c < ldq; c += 32) Qt[(size_t)j * ldq + c] = T(0);
     __syncthreads();
     T* out = w0 + (size_t)k * stride;
-    for (int c0 = warp * WCB; c0 < npad; c0 += W * WCB) {
-        T acc[MR][WCB];
+    const int ntile = (n + WCB - 1) / WCB;
+    for (int t = warp; t < ntile; t += W) {
+        const int c0 = t * WCB;
+        float acc[MR][WCB];
 #pragma unroll
         for (int q = 0; q < MR; ++q)
 #pragma unroll
-            for (int b = 0; b < WCB; ++b) acc[q][b] = T(0);
-#pragma unroll 4
+            for (int b = 0; b < WCB; ++b) acc[q][b] = 0.0f;
+        const T* ap = As + lane;
+        const T* qp = Qt + c0;
+#pragma unroll 2
         for (int j = 0; j < n; ++j) {
-            T av[MR], qv[WCB];
+            float av[MR];
 #pragma unroll
-            for (int q = 0; q < MR; ++q) {
-                const int r = q * 32 + lane;
-                av[q] = r < m ? As[(size_t)j * m + r] : T(0);
-            }
-#pragma unroll
-            for (int b = 0; b < WCB; ++b) qv[b] = (c0 + b < n) ? Qs[(size_t)(c0 + b) * n + j] : T(0);
+            for (int q = 0; q < MR; ++q) av[q] = ap[q * 32];
+            const float4 q0 = *reinterpret_cast<const float4*>(qp);
+            const float4 q1 = *reinterpret_cast<const float4*>(qp + 4);
+            const float qv[WCB] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
 #pragma unroll
             for (int q = 0; q < MR; ++q)
 #pragma unroll
-                for (int b = 0; b < WCB; ++b) acc[q][b] = fma(av[q], qv[b], acc[q][b]);
+                for (int b = 0; b < WCB; ++b) acc[q][b] = fmaf(av[q], qv[b], acc[q][b]);
+            ap += lda;
+            qp += ldq;
         }
 #pragma unroll
         for (int b = 0; b < WCB; ++b) {
@@ -90,6 +131,9 @@ __global__ void __launch_bounds__(WTG) warm_gemm_kernel(const T* __restrict__ da
             for (int r = MR * 32 + lane; r < ldA; r += 32) col[r] = T(0);
         }
     }
+    // padding columns past the last tile
+    for (int c = ntile * WCB + warp; c < npad; c += W)
+        for (int r = lane; r < ldA; r += 32) out[(size_t)c * ldA + r] = T(0);
 }
 
 // Reflector of column c (rows c..n-1, norm^2 s2 given): alpha = -sign(x_c)
@@ -106,8 +150,118 @@ __device__ __forceinline__ void make_reflector(T* x, int c, T s2, T* bet)
     bet[c] = vn2 > T(0) ? T(2) / vn2 : T(0);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(WT) warm_qr_kernel(T* __restrict__ vrec, int n, size_t stride, int* __restrict__ wrec,
+// The QR keeps the n x n matrix in shared memory, column c at Vs + c * ldv
+// (rows n.. zero).  A column is worked on by 8 lanes (lane l8 = lane % 8
+// holds rows r = 8 i + l8, i < NB), so a warp takes four consecutive columns
+// at once and a dot product is a 3-level reduction within 8 lanes; ldv is
+// 8 or 24 modulo 32, so the four columns fall in distinct banks.  Reflector
+// c touches rows c.. only: the work with c in a 16-row segment runs over the
+// row blocks from that segment on (the template argument I0 = 2 (c / 16);
+// the segment's own two blocks are masked to rows >= c).
+
+// Factorisation step c: the columns j > c go in chunks of four (chunk q =
+// columns c + 1 + 4 q .. c + 4 + 4 q, to warp q mod W) and get reflector c;
+// warp 0, whose first chunk holds column c + 1, then forms reflector c + 1.
+template <typename T, int NB, int I0>
+__device__ __forceinline__ void qr_step(T* Vs, T* bet, int ldv, int n, int c, int warp, int W, int lane)
+{
+    const int l8 = lane & 7, sg = lane >> 3;
+    const T b = bet[c];
+    const T* x = Vs + (size_t)c * ldv + l8;
+    T xv[NB];
+#pragma unroll
+    for (int i = I0; i < NB; ++i) xv[i] = (i >= I0 + 2 || 8 * i + l8 >= c) ? x[8 * i] : T(0);
+    const int nq = (n - 1 - c + 3) >> 2;
+    for (int q = warp; q < nq; q += W) {
+        const int j = c + 1 + 4 * q + sg;
+        const bool valid = j < n;
+        T* y = Vs + (size_t)(valid ? j : c) * ldv + l8;  // a lane past the last column reads column c, stores nothing
+        T yv[NB];
+        T d0 = T(0), d1 = T(0);
+#pragma unroll
+        for (int i = I0; i < NB; ++i) {
+            yv[i] = y[8 * i];
+            if ((i - I0) & 1) d1 = fma(xv[i], yv[i], d1);
+            else d0 = fma(xv[i], yv[i], d0);
+        }
+        T d = d0 + d1;
+        d += __shfl_xor_sync(0xffffffffu, d, 4);
+        d += __shfl_xor_sync(0xffffffffu, d, 2);
+        d += __shfl_xor_sync(0xffffffffu, d, 1);
+        const T f = b * d;
+        T s2 = T(0);
+#pragma unroll
+        for (int i = I0; i < NB; ++i) {
+            const T v = fma(-f, xv[i], yv[i]);  // rows < c: xv = 0, the value is kept
+            if (valid) y[8 * i] = v;
+            if (8 * i + l8 > c) s2 = fma(v, v, s2);
+        }
+        if (q == 0) {  // lanes 0-7 hold column c + 1: the next reflector
+            s2 += __shfl_xor_sync(0xffffffffu, s2, 4);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, 2);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, 1);
+            __syncwarp();
+            if (lane == 0) make_reflector(Vs + (size_t)(c + 1) * ldv, c + 1, s2, bet);
+        }
+    }
+}
+
+template <typename T, int NB, int I0 = 0>
+__device__ __forceinline__ void qr_step_at(int I, T* Vs, T* bet, int ldv, int n, int c, int warp, int W, int lane)
+{
+    if constexpr (I0 < NB) {
+        if (I == I0) qr_step<T, NB, I0>(Vs, bet, ldv, n, c, warp, W, lane);
+        else qr_step_at<T, NB, I0 + 2>(I, Vs, bet, ldv, n, c, warp, W, lane);
+    }
+}
+
+// Q formation: reflectors chi down to clo (one 16-row segment, I0 its first
+// block) applied to the column this lane's group of 8 holds.
+template <typename T, int NB, int I0>
+__device__ __forceinline__ void q_apply(T (&qv)[NB], const T* Vs, const T* bet, int ldv, int chi, int clo, int l8)
+{
+    for (int c = chi; c >= clo; --c) {
+        const T b = bet[c];
+        if (b == T(0)) continue;
+        const T* x = Vs + (size_t)c * ldv + l8;
+        T xv[NB];
+        T d0 = T(0), d1 = T(0);
+#pragma unroll
+        for (int i = I0; i < NB; ++i) {
+            xv[i] = (i >= I0 + 2 || 8 * i + l8 >= c) ? x[8 * i] : T(0);
+            if ((i - I0) & 1) d1 = fma(xv[i], qv[i], d1);
+            else d0 = fma(xv[i], qv[i], d0);
+        }
+        T d = d0 + d1;
+        d += __shfl_xor_sync(0xffffffffu, d, 4);
+        d += __shfl_xor_sync(0xffffffffu, d, 2);
+        d += __shfl_xor_sync(0xffffffffu, d, 1);
+        const T f = b * d;
+#pragma unroll
+        for (int i = I0; i < NB; ++i) qv[i] = fma(-f, xv[i], qv[i]);
+    }
+}
+
+template <typename T, int NB, int I0 = 0>
+__device__ __forceinline__ void q_apply_at(int I, T (&qv)[NB], const T* Vs, const T* bet, int ldv, int chi, int clo,
+                                           int l8)
+{
+    if constexpr (I0 < NB) {
+        if (I == I0) q_apply<T, NB, I0>(qv, Vs, bet, ldv, chi, clo, l8);
+        else q_apply_at<T, NB, I0 + 2>(I, qv, Vs, bet, ldv, chi, clo, l8);
+    }
+}
+
+// Shared-memory leading dimension of the QR: at least 8 NB rows, 8 or 24
+// modulo 32 (see above).
+__host__ __device__ inline int qr_ldv(int nb)
+{
+    const int r = 8 * nb;
+    return (r % 32 == 0 || r % 32 == 16) ? r + 8 : r;
+}
+
+template <typename T, int NB>
+__global__ void __launch_bounds__(WQ) warm_qr_kernel(T* __restrict__ vrec, int n, size_t stride, int* __restrict__ wrec,
                                                     T* __restrict__ Q, int* __restrict__ flag,
                                                     const AdmmCtl* __restrict__ ctl)
 {
@@ -115,16 +269,18 @@ __global__ void __launch_bounds__(WT) warm_qr_kernel(T* __restrict__ vrec, int n
     const int k = blockIdx.x;
     if (!wrec[k]) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* Vs = reinterpret_cast<T*>(smem_raw);  // n x n, column c at Vs + c * n; Householder vectors below the diagonal
-    T* bet = Vs + (size_t)n * n;             // beta of each reflector
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = WT / 32;
-    const T* V = vrec + (size_t)k * stride;
-    for (int e = tid; e < n * n; e += WT) Vs[e] = V[e];
+    const int ldv = qr_ldv(NB);
+    T* Vs = reinterpret_cast<T*>(smem_raw);  // Householder vectors below the diagonal, R on and above it
+    T* bet = Vs + (size_t)ldv * n;           // beta of each reflector
+    __shared__ int s_next;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = blockDim.x >> 5;
+    const int l8 = lane & 7, sg = lane >> 3;
+    load_cols(Vs, ldv, vrec + (size_t)k * stride, n, n, n, false, warp, W, lane);
+    for (int c = warp; c < n; c += W)
+        for (int r = n + lane; r < ldv; r += 32) Vs[(size_t)c * ldv + r] = T(0);
+    if (tid == 0) s_next = 0;
     __syncthreads();
-    // Householder QR, one barrier per column: in step c every warp applies
-    // reflector c to its columns j > c (column j belongs to warp j mod W,
-    // four columns at a time so that four reductions overlap), and the warp
-    // holding column c + 1 then forms reflector c + 1 from it
+    // Householder QR, one barrier per column
     if (warp == 0) {
         T s2 = T(0);
         for (int r = lane; r < n; r += 32) s2 = fma(Vs[r], Vs[r], s2);
@@ -133,105 +289,38 @@ __global__ void __launch_bounds__(WT) warm_qr_kernel(T* __restrict__ vrec, int n
         if (lane == 0) make_reflector(Vs, 0, s2, bet);
     }
     __syncthreads();
-    for (int c = 0; c < n; ++c) {
-        const T b = bet[c];
-        const T* x = Vs + (size_t)c * n;
-        T xv[WQR];
-#pragma unroll
-        for (int i = 0; i < WQR; ++i) {
-            const int r = i * 32 + lane;
-            xv[i] = (r >= c && r < n) ? x[r] : T(0);
-        }
-        // this warp's columns j > c: j = j0 + W q, j0 the first of them
-        const int j0 = c + 1 + ((warp - (c + 1)) % W + W) % W;
-        for (int jb = j0; jb < n; jb += 4 * W) {
-            T* y[4];
-            T yv[4][WQR];
-            T d[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int j = jb + u * W;
-                y[u] = Vs + (size_t)(j < n ? j : c) * n;
-                d[u] = T(0);
-#pragma unroll
-                for (int i = 0; i < WQR; ++i) {
-                    const int r = i * 32 + lane;
-                    yv[u][i] = (j < n && r < n) ? y[u][r] : T(0);
-                    d[u] = fma(xv[i], yv[u][i], d[u]);
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-                for (int u = 0; u < 4; ++u) d[u] += __shfl_xor_sync(0xffffffffu, d[u], o);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int j = jb + u * W;
-                if (j >= n) continue;
-                const T f = b * d[u];
-                T s2 = T(0);
-#pragma unroll
-                for (int i = 0; i < WQR; ++i) {
-                    const int r = i * 32 + lane;
-                    const T v = fma(-f, xv[i], yv[u][i]);
-                    if (r >= c && r < n) y[u][r] = v;
-                    if (j == c + 1 && r >= c + 1 && r < n) s2 = fma(v, v, s2);
-                }
-                if (j == c + 1) {  // the next reflector, from the column just updated
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-                    __syncwarp();
-                    if (lane == 0) make_reflector(y[u], c + 1, s2, bet);
-                }
-            }
-        }
+    for (int c = 0; c < n - 1; ++c) {
+        qr_step_at<T, NB>(2 * (c >> 4), Vs, bet, ldv, n, c, warp, W, lane);
         __syncthreads();
     }
     // Q = H_0 H_1 ... H_{n-1}; its column j is H_0 ... H_j e_j (the later
-    // reflectors leave e_j alone).  Each warp takes four consecutive columns
-    // at a time (in registers, row r = 32 i + lane) and applies reflectors
-    // from the group's last column down to 0 (a reflector past a column's
-    // own leaves it unchanged).
+    // reflectors leave e_j alone).  A warp takes four consecutive columns (a
+    // group of 8 lanes each, in registers) and applies the reflectors from
+    // the last column's down to 0; the groups go out largest first (their
+    // work grows with their columns) from a shared counter.
     T* Qk = Q + (size_t)k * n * n;
-    for (int g0 = warp * 4; g0 < n; g0 += 4 * W) {
-        T qv[4][WQR];
+    const int ng = (n + 3) / 4;
+    for (;;) {
+        int idx = 0;
+        if (lane == 0) idx = atomicAdd(&s_next, 1);
+        idx = __shfl_sync(0xffffffffu, idx, 0);
+        if (idx >= ng) break;
+        const int g0 = 4 * (ng - 1 - idx);
+        const int j = g0 + sg;
+        T qv[NB];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int i = 0; i < WQR; ++i) qv[u][i] = (i * 32 + lane == g0 + u) ? T(1) : T(0);
+        for (int i = 0; i < NB; ++i) qv[i] = (8 * i + l8 == j) ? T(1) : T(0);
         const int cmax = g0 + 3 < n - 1 ? g0 + 3 : n - 1;
-        for (int c = cmax; c >= 0; --c) {
-            const T b = bet[c];
-            if (b == T(0)) continue;
-            const T* x = Vs + (size_t)c * n;
-            T xv[WQR];
-            T d[4] = {T(0), T(0), T(0), T(0)};
-#pragma unroll
-            for (int i = 0; i < WQR; ++i) {
-                const int r = i * 32 + lane;
-                xv[i] = (r >= c && r < n) ? x[r] : T(0);
-#pragma unroll
-                for (int u = 0; u < 4; ++u) d[u] = fma(xv[i], qv[u][i], d[u]);
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-                for (int u = 0; u < 4; ++u) d[u] += __shfl_xor_sync(0xffffffffu, d[u], o);
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const T f = b * d[u];
-#pragma unroll
-                for (int i = 0; i < WQR; ++i) qv[u][i] = fma(-f, xv[i], qv[u][i]);
-            }
+        for (int seg = cmax >> 4; seg >= 0; --seg) {
+            const int chi = cmax < 16 * seg + 15 ? cmax : 16 * seg + 15;
+            q_apply_at<T, NB>(2 * seg, qv, Vs, bet, ldv, chi, 16 * seg, l8);
         }
+        if (j < n) {
+            T* qc = Qk + (size_t)j * n;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            if (g0 + u >= n) break;
-            T* qc = Qk + (size_t)(g0 + u) * n;
-#pragma unroll
-            for (int i = 0; i < WQR; ++i) {
-                const int r = i * 32 + lane;
-                if (r < n) qc[r] = qv[u][i];
+            for (int i = 0; i < NB; ++i) {
+                const int r = 8 * i + l8;
+                if (r < n) qc[r] = qv[i];
             }
         }
     }
@@ -244,14 +333,22 @@ __global__ void __launch_bounds__(WT) warm_qr_kernel(T* __restrict__ vrec, int n
 
 }  // namespace
 
-size_t warm_gemm_smem(int m, int n, int elem) { return ((size_t)m * n + (size_t)n * n) * elem; }
-size_t warm_qr_smem(int n, int elem) { return ((size_t)n * n + n) * elem; }
+// rows per lane of the GEMM's tiles (even, 2..8) and of the QR's columns (even, 2..28)
+int gemm_mr(int m) { return ((m + 31) / 32 + 1) / 2 * 2; }
+int qr_nb(int n) { return ((n + 7) / 8 + 1) / 2 * 2; }
+
+size_t warm_gemm_smem(int m, int n, int elem)
+{
+    return (((size_t)gemm_lda(gemm_mr(m)) * n + 3) / 4 * 4 + (size_t)n * gemm_ldq(n)) * elem;
+}
+size_t warm_qr_smem(int n, int elem) { return ((size_t)qr_ldv(qr_nb(n)) * n + n) * elem; }
+
+constexpr size_t kMaxDynSmem = 227 * 1024;
 
 bool warm_supported(const JacobiPlan& p)
 {
-    return p.cluster <= 1 && p.elem == 4 && p.m <= WMR * 32 && p.n <= WQR * 32 &&
-           warm_gemm_smem(p.m, p.n, p.elem) <= 200 * 1024 &&
-           warm_qr_smem(p.n, p.elem) <= 200 * 1024;
+    return p.cluster <= 1 && p.elem == 4 && p.m >= 1 && p.n >= 1 && p.m <= WMR * 32 && p.n <= WQN &&
+           warm_gemm_smem(p.m, p.n, p.elem) <= kMaxDynSmem && warm_qr_smem(p.n, p.elem) <= kMaxDynSmem;
 }
 
 size_t warm_state_bytes(int64_t n3, int n, int elem)
@@ -263,24 +360,54 @@ template <typename T>
 cudaError_t launch_warm_gemm(const JacobiPlan& p, const T* data, const T* Q, const int* flag, T* w0,
                              const AdmmCtl* ctl, cudaStream_t s)
 {
+    if (!warm_supported(p)) return cudaErrorInvalidValue;
     const size_t sm = warm_gemm_smem(p.m, p.n, sizeof(T));
-    auto kern = p.m <= 192 ? warm_gemm_kernel<T, 6> : warm_gemm_kernel<T, WMR>;
+    decltype(&warm_gemm_kernel<T, 2>) kern;
+    switch (gemm_mr(p.m)) {
+    case 2: kern = warm_gemm_kernel<T, 2>; break;
+    case 4: kern = warm_gemm_kernel<T, 4>; break;
+    case 6: kern = warm_gemm_kernel<T, 6>; break;
+    default: kern = warm_gemm_kernel<T, 8>; break;
+    }
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
+    const int ntile = (p.n + WCB - 1) / WCB;
+    const int warps = ntile < WGM / 32 ? ntile : WGM / 32;
     const size_t stride = (size_t)p.ldA * p.nb * p.K;
-    kern<<<(unsigned)p.n3, WTG, sm, s>>>(data, p.n1, p.n2, p.m, p.n, p.tr, p.ldA, p.nb * p.K, stride, Q, flag, w0, ctl);
+    kern<<<(unsigned)p.n3, 32 * warps, sm, s>>>(data, p.n1, p.n2, p.m, p.n, p.tr, p.ldA, p.nb * p.K, stride, Q, flag,
+                                               w0, ctl);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_warm_qr(const JacobiPlan& p, T* vrec, int* wrec, T* Q, int* flag, const AdmmCtl* ctl, cudaStream_t s)
 {
+    if (!warm_supported(p)) return cudaErrorInvalidValue;
     const size_t sm = warm_qr_smem(p.n, sizeof(T));
-    auto kern = warm_qr_kernel<T>;
+    decltype(&warm_qr_kernel<T, 2>) kern;
+    switch (qr_nb(p.n)) {
+    case 2: kern = warm_qr_kernel<T, 2>; break;
+    case 4: kern = warm_qr_kernel<T, 4>; break;
+    case 6: kern = warm_qr_kernel<T, 6>; break;
+    case 8: kern = warm_qr_kernel<T, 8>; break;
+    case 10: kern = warm_qr_kernel<T, 10>; break;
+    case 12: kern = warm_qr_kernel<T, 12>; break;
+    case 14: kern = warm_qr_kernel<T, 14>; break;
+    case 16: kern = warm_qr_kernel<T, 16>; break;
+    case 18: kern = warm_qr_kernel<T, 18>; break;
+    case 20: kern = warm_qr_kernel<T, 20>; break;
+    case 22: kern = warm_qr_kernel<T, 22>; break;
+    case 24: kern = warm_qr_kernel<T, 24>; break;
+    case 26: kern = warm_qr_kernel<T, 26>; break;
+    default: kern = warm_qr_kernel<T, 28>; break;
+    }
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
+    // a warp per two chunks of four columns, 4 to 16 warps
+    int warps = (p.n + 7) / 8;
+    warps = warps < 4 ? 4 : (warps > WQ / 32 ? WQ / 32 : warps);
     const size_t stride = (size_t)p.ldA * p.nb * p.K;
-    kern<<<(unsigned)p.n3, WT, sm, s>>>(vrec, p.n, stride, wrec, Q, flag, ctl);
+    kern<<<(unsigned)p.n3, 32 * warps, sm, s>>>(vrec, p.n, stride, wrec, Q, flag, ctl);
     return cudaGetLastError();
 }
 

@@ -26,6 +26,7 @@ _lib = _ct.CDLL(LIB_PATH)
 
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ENONFINITE, ENODEV = range(7)
 OPT_JACOBI_MAX_SWEEPS, OPT_TC_WAIT_POLLS, OPT_JACOBI_FP64_ANGLES, OPT_ADMM_WARM_START = 1, 2, 3, 4
+OPT_JACOBI_SMALL_STOP, OPT_JACOBI_SWEEP_LOG = 5, 6
 PRECISIONS = {"fp64": 0, "fp32": 1, "tf32x3": 2, "bf16split": 3}
 OP_TDCT3, OP_TSVT, OP_TSVD, OP_TPROD, OP_COMPLETE = range(5)
 
@@ -84,6 +85,11 @@ _lib.tnn_admm_warm_size.argtypes = [Shape, _ct.c_int, _ct.POINTER(_ct.c_size_t)]
 _lib.tnn_admm_warm_size.restype = _st
 _lib.tnn_last_jacobi_stats.argtypes = [_vp, _ct.POINTER(_ct.c_int64)]
 _lib.tnn_last_jacobi_stats.restype = _st
+_lib.tnn_last_slice_stats.argtypes = [_vp, _ct.c_int64, _ct.POINTER(_ct.c_int32), _ct.POINTER(_ct.c_int32),
+                                      _ct.POINTER(_ct.c_int64)]
+_lib.tnn_last_slice_stats.restype = _st
+_lib.tnn_last_sweep_log.argtypes = [_vp, _ct.c_int64, _ct.POINTER(_ct.c_float)]
+_lib.tnn_last_sweep_log.restype = _st
 _lib.tnn_fma_peak.argtypes = [_ct.c_int32, _ct.c_int32, _ct.POINTER(_ct.c_double)]
 _lib.tnn_fma_peak.restype = _st
 _lib.tnn_jacobi_plan_info.argtypes = [Shape, _ct.c_int, _ct.POINTER(_ct.c_int64)]
@@ -172,7 +178,7 @@ _lib.tsvt_dct_plain.restype = _st
 EXPORTS = ["tnn_create", "tnn_destroy", "tnn_status_string", "tnn_last_error", "tnn_reserve", "tnn_set_option",
            "tnn_workspace_size",
            "tdct3", "tsvt_dct", "tsvd_dct_forward", "tsvd_dct_inverse", "tprod_dct", "tnn_complete",
-           "tnn_admm_iterate", "tnn_admm_warm_size", "tnn_last_jacobi_stats", "tnn_profile", "tnn_profile_read", "tsvt_dct_static",
+           "tnn_admm_iterate", "tnn_admm_warm_size", "tnn_last_jacobi_stats", "tnn_last_slice_stats", "tnn_last_sweep_log", "tnn_profile", "tnn_profile_read", "tsvt_dct_static",
            "tnn_tsvt_batch_create", "tnn_tsvt_batch_run", "tnn_tsvt_batch_info", "tnn_tsvt_batch_group",
            "tnn_tsvt_batch_profile", "tnn_tsvt_batch_stats", "tnn_tsvt_batch_destroy",
            "tnn_server_create", "tnn_server_submit", "tnn_server_step", "tnn_server_job_state", "tnn_server_take",
@@ -331,7 +337,8 @@ class Context:
 
     def set_option(self, option, value):
         """tnn_set_option: OPT_JACOBI_MAX_SWEEPS, OPT_TC_WAIT_POLLS,
-        OPT_JACOBI_FP64_ANGLES or OPT_ADMM_WARM_START."""
+        OPT_JACOBI_FP64_ANGLES, OPT_ADMM_WARM_START, OPT_JACOBI_SMALL_STOP or
+        OPT_JACOBI_SWEEP_LOG."""
         self._chk(_lib.tnn_set_option(self._h, int(option), int(value)), "tnn_set_option")
 
     def workspace_size(self, op, shape, prec="fp32"):
@@ -510,6 +517,27 @@ class Context:
         self._chk(_lib.tnn_last_jacobi_stats(self._h, out), "tnn_last_jacobi_stats")
         keys = ["slices", "pairs", "rotations", "max_sweeps", "unconverged", "kept"]
         return dict(zip(keys, list(out)))
+
+    def last_slice_stats(self):
+        """Per-slice sweeps, kept singular values and rotations of the last
+        Jacobi launch: {"sweeps": [...], "kept": [...], "rotations": [...]}."""
+        n = self.last_jacobi_stats()["slices"]
+        sw = (_ct.c_int32 * max(n, 1))()
+        kp = (_ct.c_int32 * max(n, 1))()
+        rt = (_ct.c_int64 * max(n, 1))()
+        self._chk(_lib.tnn_last_slice_stats(self._h, n, sw, kp, rt), "tnn_last_slice_stats")
+        return {"sweeps": list(sw)[:n], "kept": list(kp)[:n], "rotations": list(rt)[:n]}
+
+    def last_sweep_log(self):
+        """Per-sweep log of the last Jacobi launch (OPT_JACOBI_SWEEP_LOG on):
+        a numpy array (slices, 8 sweeps, 6): big rotations, wide rotations,
+        big low-low rotations, largest |gamma|/sqrt(alpha beta) of the big
+        ones, largest |t| of the big ones, largest |t| of all."""
+        n = self.last_jacobi_stats()["slices"]
+        out = _np.zeros((max(n, 1), 8, 6), dtype=_np.float32)
+        self._chk(_lib.tnn_last_sweep_log(self._h, n, out.ctypes.data_as(_ct.POINTER(_ct.c_float))),
+                  "tnn_last_sweep_log")
+        return out[:n]
 
     def profile(self, enable=True):
         """Bracket every kernel launch of later calls with CUDA events."""

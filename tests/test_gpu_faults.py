@@ -123,5 +123,5 @@ def test_tensor_core_wait_timeout_reports_error(ctx, prec):
 def test_options_reject_out_of_range(ctx):
     from paper_1902_03070_gb300 import tnn
     for opt, val in ((tnn.OPT_JACOBI_MAX_SWEEPS, -1), (tnn.OPT_JACOBI_MAX_SWEEPS, 1001),
-                     (tnn.OPT_TC_WAIT_POLLS, 1 << 31), (99, 0)):
+                     (tnn.OPT_TC_WAIT_POLLS, 1 << 31), (tnn.OPT_JACOBI_SMALL_STOP, 2), (99, 0)):
         assert tnn._lib.tnn_set_option(ctx._h, opt, val) == tnn.EINVAL

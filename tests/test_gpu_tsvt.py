@@ -350,3 +350,88 @@ def test_tsvt_fp64_angles(ctx, prec, shape):
     for a64 in (0, 1):
         assert errs[a64][1] <= TOL[prec], errs
         assert errs[a64][0] <= TOL[prec], errs
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_slice_stats_match_totals(ctx, prec):
+    # the per-slice statistics add up to the launch totals, and each slice's
+    # kept count is the oracle's count of singular values above tau
+    rng = np.random.default_rng(5)
+    shape = (60, 44, 7)
+    Z = inputs.random_tensor(shape, rng)
+    if prec != "fp64":
+        Z = Z.astype(np.float32).astype(np.float64)
+    tau = tau_at_quantile(Z, 0.6)
+    _run(ctx, Z, tau, prec)
+    tot = ctx.last_jacobi_stats()
+    per = ctx.last_slice_stats()
+    assert len(per["sweeps"]) == shape[2]
+    assert max(per["sweeps"]) == tot["max_sweeps"]
+    assert sum(per["kept"]) == tot["kept"]
+    assert sum(per["rotations"]) == tot["rotations"]
+    Zbar = O.tube_transform(Z)
+    for k in range(shape[2]):
+        s = np.linalg.svd(Zbar[:, :, k], compute_uv=False)
+        # a singular value within rounding of tau may fall either way
+        sure = int((s > tau * (1 + 1e-5)).sum())
+        maybe = int((s > tau * (1 - 1e-5)).sum())
+        assert sure <= per["kept"][k] <= maybe
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("q", [0.3, 0.8])
+def test_small_rotation_stop(ctx, prec, q):
+    # the small-rotation stop (default on) against the plain stopping rule:
+    # never more sweeps, and both within the same bounds of the oracle
+    from paper_1902_03070_gb300 import tnn
+    rng = np.random.default_rng(31)
+    shape = (120, 90, 5)
+    Z = inputs.random_tensor(shape, rng)
+    if prec != "fp64":
+        Z = Z.astype(np.float32).astype(np.float64)
+    tau = tau_at_quantile(Z, q)
+    ref = O.tsvt(Z, tau, nthreads=THREADS)
+    out = {}
+    try:
+        for flag in (1, 0):
+            ctx.set_option(tnn.OPT_JACOBI_SMALL_STOP, flag)
+            Y = _run(ctx, Z, tau, prec)
+            st = ctx.last_jacobi_stats()
+            assert st["unconverged"] == 0
+            out[flag] = (Y, sum(ctx.last_slice_stats()["sweeps"]))
+    finally:
+        ctx.set_option(tnn.OPT_JACOBI_SMALL_STOP, 1)
+    assert out[1][1] <= out[0][1]
+    for flag in (1, 0):
+        err_y = rel_err(out[flag][0], ref, Z)
+        log_err("tsvt small-stop=%d %s q=%s sweeps=%d" % (flag, prec, q, out[flag][1]), err_y=err_y)
+        assert err_y <= TOL[prec]
+
+
+def test_sweep_log(ctx):
+    # the per-sweep log: one row per sweep run, and the last row of every
+    # slice meets a stopping rule (no big rotation, or no wide one)
+    from paper_1902_03070_gb300 import tnn
+    rng = np.random.default_rng(41)
+    shape = (96, 72, 6)
+    Z = inputs.random_tensor(shape, rng).astype(np.float32).astype(np.float64)
+    tau = tau_at_quantile(Z, 0.3)
+    try:
+        ctx.set_option(tnn.OPT_JACOBI_SWEEP_LOG, 1)
+        _run(ctx, Z, tau, "fp32")
+        log = ctx.last_sweep_log()
+    finally:
+        ctx.set_option(tnn.OPT_JACOBI_SWEEP_LOG, 0)
+    sweeps = ctx.last_slice_stats()["sweeps"]
+    assert log.shape == (shape[2], 8, 6)
+    for k in range(shape[2]):
+        s = sweeps[k]
+        assert 1 <= s <= 8
+        last = log[k, s - 1]
+        assert last[0] == 0 or last[1] == 0
+        assert np.all(log[k, s:] == 0)
+        assert log[k, 0, 0] > 0  # a random slice is not orthogonal to begin with
+        assert np.all(np.isfinite(log[k])) and np.all(log[k] >= 0)
+    _run(ctx, Z, tau, "fp32")
+    with pytest.raises(tnn.TnnError):
+        ctx.last_sweep_log()  # the launch after the option was cleared kept none

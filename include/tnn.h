@@ -500,8 +500,9 @@ void tnn_server_destroy(tnn_server* server);
  *   6 ADMM state init           7 Jacobi SVD
  *   8 facewise product          9 DFT / rectangular tube transform
  *  10 plain Jacobi SVT (comparison path)
- *  11 warm start of the Jacobi SVT (A Q before it, Q after it) */
-#define TNN_NKERNELS 12
+ *  11 warm start of the Jacobi SVT (A Q before it, Q after it)
+ *  12 tail of the warm-started SVT (recovered vectors and rebuild) */
+#define TNN_NKERNELS 13
 tnn_status tnn_profile(tnn_ctx* ctx, int enable);
 tnn_status tnn_profile_read(tnn_ctx* ctx, double ms[TNN_NKERNELS], int64_t launches[TNN_NKERNELS]);
 

@@ -146,7 +146,7 @@ struct Trace {
 
 // Kernel kinds reported by tnn_profile_read (array index, listed in tnn.h).
 enum { K_TUBE = 0, K_TUBE_FWD_ADMM, K_JACOBI_SVT, K_TUBE_INV_ADMM, K_FINALIZE, K_CTL_INIT, K_ADMM_INIT,
-       K_JACOBI_SVD, K_FACEWISE, K_DFT, K_JACOBI_PLAIN, K_WARM, K_NKINDS };
+       K_JACOBI_SVD, K_FACEWISE, K_DFT, K_JACOBI_PLAIN, K_WARM, K_SVT_TAIL, K_NKINDS };
 #define TRACE_CAT2(a, b) a##b
 #define TRACE_CAT(a, b) TRACE_CAT2(a, b)
 #define TRACE(kind) Trace TRACE_CAT(trace_, __LINE__)(ctx, kind, s)
@@ -784,15 +784,26 @@ tnn_status admm_enqueue_iters(tnn_ctx* ctx, const AdmmJob& j, int iters, cudaStr
                 TRACE(K_WARM);
                 CK(launch_warm_gemm<float>(j.jp, (const float*)j.W, Q, wflag, (float*)j.wscr, j.ctl, s));
             }
+            // with the offloaded tail the Jacobi kernel leaves its columns in
+            // the scratch, the tail kernel writes the recovered vectors over
+            // Q (consumed above) and the QR turns them into the next Q in place
+            const bool tail = warm && j.tinfo != nullptr;
             { TRACE(K_JACOBI_SVT);
               if (j.jp.sweep_log)
                   CK(cudaMemsetAsync(j.jp.sweep_log, 0, sizeof(float) * sweep_log_floats * n3, s));
-              const WarmPtrs wp{j.wscr, wflag, j.wscr, j.wrec};
+              WarmPtrs wp{j.wscr, wflag, j.wscr, j.wrec};
+              if (tail) { wp.tail_s = j.wscr; wp.tail_info = j.tinfo; }
               CK(launch_jacobi_svt<float>(j.jp, (float*)j.W, 0.0, j.ctl, sweeps, j.jwork, j.stats, s,
                                           warm ? &wp : nullptr)); }
+            if (tail) {
+                TRACE(K_SVT_TAIL);
+                CK(launch_warm_tail<float>(j.jp, (float*)j.W, (const float*)j.wscr, j.tinfo, Q, j.wrec, j.ctl, s));
+            }
             if (warm) {
                 TRACE(K_WARM);
-                CK(launch_warm_qr<float>(j.jp, (float*)j.wscr, j.wrec, Q, wflag, j.ctl, s));
+                const size_t wstride = (size_t)j.jp.ldA * j.jp.nb * j.jp.K;
+                CK(launch_warm_qr<float>(j.jp, tail ? Q : (const float*)j.wscr, tail ? (size_t)j.jp.n * j.jp.n : wstride,
+                                         j.wrec, Q, wflag, j.ctl, s));
             }
             { TRACE(K_TUBE_INV_ADMM);
               if (opi.tc)
@@ -893,6 +904,8 @@ tnn_status tnn_complete(tnn_ctx* ctx, const void* B, const uint8_t* mask, tnn_sh
     const size_t wscr = warm ? (size_t)sh.n3 * jp.ldA * jp.nb * jp.K * elem : 0;
     size_t oWs = warm ? cv.add(wstate) : 0, oWc = warm ? cv.add(wscr) : 0;
     size_t oWr = warm ? cv.add(sizeof(int) * sh.n3) : 0;
+    const bool tail = warm && tail_supported(jp);
+    size_t oWt = tail ? cv.add(sizeof(float) * sh.n3 * tail_info_stride(jp.nb * jp.K)) : 0;
     if ((st = ensure_ws(ctx, cv.total))) return st;
     Stager sg{ctx, s};
     if ((st = sg.in(ab, ohb))) return st;
@@ -913,6 +926,7 @@ tnn_status tnn_complete(tnn_ctx* ctx, const void* B, const uint8_t* mask, tnn_sh
         job.warm = at(ctx, oWs);
         job.wscr = at(ctx, oWc);
         job.wrec = (int*)at(ctx, oWr);
+        if (tail) job.tinfo = (float*)at(ctx, oWt);
     }
     st = admm_run(ctx, job, params->beta0, params->max_iter, s, &res);
     if (st) return st;
@@ -954,6 +968,8 @@ tnn_status tnn_admm_iterate(tnn_ctx* ctx, const void* B, const uint8_t* mask, tn
     if (warm && !is_device_ptr(warm_state)) return fail(ctx, TNN_EINVAL, "warm state must be device memory");
     const size_t wscr = warm ? (size_t)sh.n3 * jp.ldA * jp.nb * jp.K * elem : 0;
     size_t oWc = warm ? cv.add(wscr) : 0, oWr = warm ? cv.add(sizeof(int) * sh.n3) : 0;
+    const bool tail = warm && tail_supported(jp);
+    size_t oWt = tail ? cv.add(sizeof(float) * sh.n3 * tail_info_stride(jp.nb * jp.K)) : 0;
     if ((st = ensure_ws(ctx, cv.total))) return st;
     Stager sg{ctx, s};
     if ((st = sg.in(ab, ohb))) return st;
@@ -971,6 +987,7 @@ tnn_status tnn_admm_iterate(tnn_ctx* ctx, const void* B, const uint8_t* mask, tn
         job.warm = warm_state;
         job.wscr = at(ctx, oWc);
         job.wrec = (int*)at(ctx, oWr);
+        if (tail) job.tinfo = (float*)at(ctx, oWt);
     }
     st = admm_run(ctx, job, *beta, max_iter, s, &res);
     if (st) return st;

@@ -39,6 +39,7 @@
 
 #include <utility>
 
+#include "async_copy.cuh"
 #include "tnn_internal.h"
 
 namespace tnn {
@@ -749,6 +750,12 @@ struct KArgs {
     int* wrec;
     int small_stop;     // 1: stop after a sweep of small rotations only (see theta in the kernel)
     float* sweep_log;   // optional: per slice and sweep s < kSweepLogSweeps, kSweepLogVals values (see the sweep loop)
+    // offloaded tail (warm-started single-tensor SVT): instead of the
+    // recovery and the rebuild, the kernel writes its converged columns to
+    // tail_s + k * stride (its working-copy layout) and, at tail_info + k *
+    // tail_info_stride(npad), what warm_tail_kernel needs (see there)
+    T* tail_s;
+    float* tail_info;
 };
 
 // Shared-memory carve-up (bytes) for a launch: dsc, sig, cf, carried norms
@@ -831,10 +838,17 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
         // vectors (orthogonal), already oriented, padded and laid out as here;
         // the same singular values, columns nearly orthogonal
         const T* w0 = a.w0 + (size_t)slice * wstride;
-        for (size_t e = tid; e < wsz; e += nthr) {
-            const T v = w0[e];
-            Aw[e] = v;
-            fro = fma(v, v, fro);
+        if constexpr (SMEM && sizeof(T) == 4) {  // all chunks in flight at once, then the norm from shared memory
+            copy_to_shared(reinterpret_cast<float*>(Aw), reinterpret_cast<const float*>(w0), wsz, tid, nthr);
+            cp_async_wait_all();
+            __syncthreads();
+            for (size_t e = tid; e < wsz; e += nthr) fro = fma(Aw[e], Aw[e], fro);
+        } else {
+            for (size_t e = tid; e < wsz; e += nthr) {
+                const T v = w0[e];
+                Aw[e] = v;
+                fro = fma(v, v, fro);
+            }
         }
     } else {
         for (size_t e = tid; e < wsz; e += nthr) Aw[e] = T(0);
@@ -1173,11 +1187,34 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
     }
     __syncthreads();
 
+    // ---- offloaded tail: the converged columns, each column's rank by
+    // descending sigma (ties by index) and its recovery scale 1 / (d_c
+    // |s_c|^2) go to global memory; the kept columns and their coefficients
+    // follow below
+    const bool offload = !WITHV && !ITEMS && a.tail_info != nullptr;
+    float* tinfo = offload ? a.tail_info + (size_t)slice * tail_info_stride(npad) : nullptr;
+    if (offload && !skip) {
+        int* irank = reinterpret_cast<int*>(tinfo + 2 * npad);
+        for (int c = tid; c < n; c += nthr) {
+            int rk = 0;
+            const T sc = sig[c];
+            for (int o = 0; o < n; ++o) {
+                const T so = sig[o];
+                rk += (so > sc || (so == sc && o < c)) ? 1 : 0;
+            }
+            irank[c] = rk;
+            const T den = dsc[c] * cf[c];
+            tinfo[npad + c] = den > T(0) ? (float)(T(1) / den) : 0.0f;
+        }
+        T* so = a.tail_s + (size_t)slice * wstride;
+        for (size_t e = tid; e < (size_t)ldA * n; e += nthr) so[e] = Aw[e];
+    }
+
     // ---- warm start for the next iteration: v_c = A0^T s_c / (d_c |s_c|^2)
     // = A0^T u_c / sigma_c for every column, columns by descending sigma
     // (the reliable ones first for the orthogonalisation that follows).  A
     // slice that ran no sweep has no new vectors.
-    if (!WITHV && !ITEMS && a.vrec && !skip) {
+    if (!WITHV && !ITEMS && a.vrec && !skip && !offload) {
         for (int c = tid; c < n; c += nthr) {
             int rk = 0;
             const T sc = sig[c];
@@ -1256,6 +1293,17 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
         }
         __syncthreads();
         const int keep = s_keep;
+        if (offload) {  // the kept columns and their coefficients, for the tail kernel
+            int* ikidx = reinterpret_cast<int*>(tinfo + 3 * npad);
+            for (int q = tid; q < keep; q += nthr) {
+                ikidx[q] = kidx[q];
+                tinfo[q] = (float)cf[q];
+            }
+            if (tid == 0) {
+                reinterpret_cast<int*>(tinfo)[4 * npad] = keep;
+                reinterpret_cast<int*>(tinfo)[4 * npad + 1] = skip ? 0 : 1;
+            }
+        }
         // ---- rebuild Y = sum_q cf_q s_q (s_q^T a0_j), JB output columns per
         // warp (each shared-memory load of a kept column feeds JB FMAs); the
         // slice is overwritten in place (each warp reads only the columns it
@@ -1265,7 +1313,7 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
         constexpr int NV = 4 * JB;     // partial sums per batch: 4 kept columns x JB
         constexpr int GV = 32 / NV;    // lanes holding each reduced value
         T* gb = gbuf + (size_t)warp * 4 * npad;
-        for (int j0 = warp * JB; j0 < n; j0 += JB * W) {
+        for (int j0 = warp * JB; j0 < (offload ? 0 : n); j0 += JB * W) {
             T x[JB][RR];
 #pragma unroll
             for (int u = 0; u < JB; ++u)

@@ -19,6 +19,8 @@ cudaError_t launch_jacobi_svt<float>(const JacobiPlan& p, float* data, double ta
         a.wflag = warm->wflag;
         a.vrec = static_cast<float*>(warm->vrec);
         a.wrec = warm->wrec;
+        a.tail_s = static_cast<float*>(warm->tail_s);
+        a.tail_info = warm->tail_info;
     }
     if (p.cluster > 1) return launch_jacobi_svt_cluster<float>(p, a, false, s);
     if (p.angle64 && p.in_smem) return launch_jacobi_svt_f32_a64(p, a, s);

@@ -97,7 +97,7 @@ bool pageable(const void* p)
 
 // Device layout of one job (offsets into its allocation).
 struct Layout {
-    size_t B, mask, X, M, W, partials, stats, ctl, jwork, warm, wscr, wrec, total;
+    size_t B, mask, X, M, W, partials, stats, ctl, jwork, warm, wscr, wrec, tinfo, total;
 };
 
 // A job warm-starts its Jacobi from the previous iteration's right singular
@@ -131,6 +131,8 @@ Layout layout_of(const tnn_shape& sh, int elem, const JacobiPlan& jp, bool warm)
     L.warm = warm ? add(warm_state_bytes(sh.n3, jp.n, elem)) : 0;
     L.wscr = warm ? add((size_t)sh.n3 * jp.ldA * jp.nb * jp.K * elem) : 0;
     L.wrec = warm ? add(sizeof(int) * sh.n3) : 0;
+    const bool tail = warm && tail_supported(jp);  // the offloaded SVT tail's per-slice record
+    L.tinfo = tail ? add(sizeof(float) * sh.n3 * tail_info_stride(jp.nb * jp.K)) : 0;
     L.total = o;
     return L;
 }
@@ -258,6 +260,7 @@ bool admit(tnn_server* sv, SJob& j)
         j.aj.warm = c + L.warm;
         j.aj.wscr = c + L.wscr;
         j.aj.wrec = reinterpret_cast<int*>(c + L.wrec);
+        if (tail_supported(jp)) j.aj.tinfo = reinterpret_cast<float*>(c + L.tinfo);
     }
     bool ok = cudaMemcpyAsync(c + L.B, j.B_user, bytes, cudaMemcpyDefault, s) == cudaSuccess &&
               cudaMemcpyAsync(c + L.mask, j.mask_user, N, cudaMemcpyDefault, s) == cudaSuccess;

@@ -36,6 +36,12 @@ constexpr int kSweepLogSweeps = 8;
 constexpr int kSweepLogVals = 6;
 constexpr int sweep_log_floats = kSweepLogSweeps * kSweepLogVals;
 
+// Per-slice record the Jacobi SVT leaves for the offloaded tail
+// (warm_tail_kernel), in 32-bit words: coef[q] (q < keep), 1 / (d_c |s_c|^2)
+// by column, rank_c by column (int), kidx[q] (int), keep (int), has_vec (int:
+// the slice ran sweeps, so its recovered vectors are valid).
+__host__ __device__ inline size_t tail_info_stride(int npad) { return 4 * (size_t)npad + 4; }
+
 struct SliceStats {
     double nuc;        // sum_i (sigma_i - tau)_+ of the slice
     int64_t pairs;     // column pairs visited
@@ -154,6 +160,8 @@ struct WarmPtrs {
     const int* wflag;
     void* vrec;
     int* wrec;
+    void* tail_s = nullptr;       // offloaded tail: the converged columns go here (may be w0) ...
+    float* tail_info = nullptr;   // ... and the per-slice record (tail_info_stride words each)
 };
 
 template <typename T>
@@ -170,8 +178,16 @@ template <typename T>
 cudaError_t launch_warm_gemm(const JacobiPlan& p, const T* data, const T* Q, const int* flag, T* w0,
                              const AdmmCtl* ctl, cudaStream_t s);
 template <typename T>
-cudaError_t launch_warm_qr(const JacobiPlan& p, T* vrec, int* wrec, T* Q, int* flag, const AdmmCtl* ctl,
-                           cudaStream_t s);
+cudaError_t launch_warm_qr(const JacobiPlan& p, const T* vrec, size_t vstride, int* wrec, T* Q, int* flag,
+                           const AdmmCtl* ctl, cudaStream_t s);
+// The offloaded tail of the warm-started SVT (recovered vectors into V, n x n
+// per slice; the rebuild over the slices in `data`), from the Jacobi
+// kernel's columns S and record `info`; tail_supported says whether the
+// shape fits (else the Jacobi kernel keeps its own tail).
+bool tail_supported(const JacobiPlan& p);
+template <typename T>
+cudaError_t launch_warm_tail(const JacobiPlan& p, T* data, const T* S, const float* info, T* V, int* wrec,
+                             const AdmmCtl* ctl, cudaStream_t s);
 
 // SVT of a list of slices (device array of `count` SliceItems) that all use
 // the variant of `plan` (K, RA, L, ldA, in_smem); plan.nb and plan.n3 must be
@@ -317,6 +333,8 @@ struct AdmmJob {
     void* warm = nullptr;
     void* wscr = nullptr;
     int* wrec = nullptr;
+    // offloaded SVT tail (tail_supported(jp)): n3 x tail_info_stride(npad) words
+    float* tinfo = nullptr;
 };
 
 // The job's transform operators, from the context's caches (built on first use).

@@ -21,6 +21,7 @@
 // (0: no Q yet, start from A0); a zero-filled state is a cold start.
 #include <cuda_runtime.h>
 
+#include "async_copy.cuh"
 #include "tnn_internal.h"
 
 namespace tnn {
@@ -261,7 +262,7 @@ __host__ __device__ inline int qr_ldv(int nb)
 }
 
 template <typename T, int NB>
-__global__ void __launch_bounds__(WQ) warm_qr_kernel(T* __restrict__ vrec, int n, size_t stride, int* __restrict__ wrec,
+__global__ void __launch_bounds__(WQ) warm_qr_kernel(const T* __restrict__ vrec, int n, size_t stride, int* __restrict__ wrec,
                                                     T* __restrict__ Q, int* __restrict__ flag,
                                                     const AdmmCtl* __restrict__ ctl)
 {
@@ -331,6 +332,166 @@ __global__ void __launch_bounds__(WQ) warm_qr_kernel(T* __restrict__ vrec, int n
     }
 }
 
+// The tail of the warm-started SVT of one slice after its sweeps, on all
+// SMs: CTA (t, k) takes the JT output columns j0 = JT t .. of slice k, with
+// S the converged columns (s_c, m rows), A0 the oriented slice (overwritten
+// by Y) and the Jacobi kernel's record (coef, recovery scale, rank, kept
+// columns; tail_info_stride):
+//   R = S^T A0[:, tile]                         (n x JT, in shared memory)
+//   V[j, rank_c] = R[c, j] / (d_c |s_c|^2)      (the recovered right vectors)
+//   Y[:, tile] = sum_q S[:, kidx_q] coef_q R[kidx_q, tile]
+// with coef_q = (1 - tau / sigma_q) / |s_q|^2: the V-free rebuild of the
+// shrunk slice, Y = sum_{sigma > tau} (1 - tau / sigma) u u^T A0.  Each warp
+// computes 32 MR x 8 output tiles (lanes over rows), as in the A Q product.
+constexpr int TJ = 48;            // output columns per CTA
+constexpr int TW = TJ / WCB;      // warps per CTA
+constexpr int TLD = TJ + 4;       // leading dimension of the row-major tiles (16-byte rows)
+
+// shared memory: S as the Jacobi kernel laid it out (ldA rows per column), the
+// A0 tile and the R tile (32 MR rows of TLD), the kept columns' coef and index
+__host__ __device__ inline size_t tail_smem_floats(int n, int ldA, int npad, int mrc, int mrr)
+{
+    return ((size_t)n * ldA + 3) / 4 * 4 + (size_t)32 * mrr * TLD + (size_t)32 * mrc * TLD + 2 * (size_t)npad;
+}
+
+template <int MRC, int MRR>
+__global__ void __launch_bounds__(32 * TW) warm_tail_kernel(float* __restrict__ data, int64_t n1, int64_t n2, int m,
+                                                            int n, int tr, int ldA, int npad, size_t stride,
+                                                            const float* __restrict__ S, const float* __restrict__ info,
+                                                            float* __restrict__ V, int* __restrict__ wrec,
+                                                            const AdmmCtl* __restrict__ ctl)
+{
+    if (ctl && ctl->done) return;
+    const int t = blockIdx.x, k = blockIdx.y;
+    const int j0 = t * TJ;
+    if (j0 >= n) return;
+    const int jn = n - j0 < TJ ? n - j0 : TJ;
+    const float* inf = info + (size_t)k * tail_info_stride(npad);
+    const int* iinf = reinterpret_cast<const int*>(inf);
+    const int keep = iinf[4 * npad], hasv = iinf[4 * npad + 1];
+    float* src = data + (size_t)k * n1 * n2;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    auto at = [&](int r, int j) -> float& {  // element (r, j) of the oriented slice
+        return tr ? src[(size_t)j + (size_t)n1 * r] : src[(size_t)r + (size_t)n1 * j];
+    };
+    if (!hasv && keep == 0) {  // a slice without sweeps keeps nothing: Y = 0
+        for (int e = tid; e < m * jn; e += 32 * TW) {
+            const int r = tr ? e / jn : e % m, j = tr ? e % jn : e / m;
+            at(r, j0 + j) = 0.0f;
+        }
+        return;
+    }
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lds = ldA;  // rows m .. ldA - 1 of the Jacobi kernel's columns are zero, and ldA >= 32 MRR
+    float* Ss = reinterpret_cast<float*>(smem_raw);                // column c at Ss + c * lds
+    float* At = Ss + ((size_t)n * lds + 3) / 4 * 4;                // A0 tile, row r at At + r * TLD (rows m.., columns jn.. zero)
+    float* Rt = At + (size_t)32 * MRR * TLD;                       // R tile, row c at Rt + c * TLD
+    float* cq = Rt + (size_t)32 * MRC * TLD;                       // coef of the kept columns
+    int* kq = reinterpret_cast<int*>(cq + npad);                   // the kept columns
+    // S in one contiguous asynchronous copy (16-byte chunks)
+    copy_to_shared(Ss, S + (size_t)k * stride, (size_t)n * lds, tid, 32 * TW);
+    if (tr && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) && n1 % 4 == 0) {
+        // A0 rows are source columns: TJ contiguous j per r, 16-byte chunks
+        for (int e = tid; e < 32 * MRR * (TJ / 4); e += 32 * TW) {
+            const int r = e / (TJ / 4), q = 4 * (e % (TJ / 4));
+            float* d = At + (size_t)r * TLD + q;
+            if (r < m && q + 3 < jn) cp_async16(d, src + (size_t)(j0 + q) + (size_t)n1 * r);
+            else
+                for (int u = 0; u < 4; ++u) d[u] = (r < m && q + u < jn) ? src[(size_t)(j0 + q + u) + (size_t)n1 * r] : 0.0f;
+        }
+    } else if (tr) {
+        for (int e = tid; e < 32 * MRR * TJ; e += 32 * TW) {
+            const int r = e / TJ, j = e % TJ;
+            At[(size_t)r * TLD + j] = (r < m && j < jn) ? src[(size_t)(j0 + j) + (size_t)n1 * r] : 0.0f;
+        }
+    } else {  // A0 columns are source columns: eight loads in flight per thread
+        load_cols(At, TLD, src + (size_t)n1 * j0, n1, m, jn, true, warp, TW, lane);
+        for (int j = jn + warp; j < TJ; j += TW)
+            for (int r = lane; r < m; r += 32) At[(size_t)r * TLD + j] = 0.0f;
+        for (int e = tid; e < (32 * MRR - m) * TJ; e += 32 * TW) At[(size_t)(m + e / TJ) * TLD + e % TJ] = 0.0f;
+    }
+    for (int q = tid; q < keep; q += 32 * TW) {
+        cq[q] = inf[q];
+        kq[q] = iinf[3 * npad + q];
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    const int jj = warp * WCB;  // this warp's 8 columns of the tile
+    {   // R = S^T A0: rows c = 32 q + lane
+        float acc[MRC][WCB];
+#pragma unroll
+        for (int q = 0; q < MRC; ++q)
+#pragma unroll
+            for (int b = 0; b < WCB; ++b) acc[q][b] = 0.0f;
+        const float* sp[MRC];
+#pragma unroll
+        for (int q = 0; q < MRC; ++q) {
+            const int c = 32 * q + lane;
+            sp[q] = Ss + (size_t)(c < n ? c : 0) * lds;
+        }
+#pragma unroll 2
+        for (int r = 0; r < m; ++r) {
+            float av[MRC];
+#pragma unroll
+            for (int q = 0; q < MRC; ++q) av[q] = (32 * q + lane < n) ? sp[q][r] : 0.0f;
+            const float4 b0 = *reinterpret_cast<const float4*>(At + (size_t)r * TLD + jj);
+            const float4 b1 = *reinterpret_cast<const float4*>(At + (size_t)r * TLD + jj + 4);
+            const float bv[WCB] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int q = 0; q < MRC; ++q)
+#pragma unroll
+                for (int b = 0; b < WCB; ++b) acc[q][b] = fmaf(av[q], bv[b], acc[q][b]);
+        }
+        const int* irank = iinf + 2 * npad;
+        float* Vk = V + (size_t)k * n * n;
+#pragma unroll
+        for (int q = 0; q < MRC; ++q) {
+            const int c = 32 * q + lane;
+            if (c >= n) continue;
+            const float rs = inf[npad + c];
+            const int rk = irank[c];
+#pragma unroll
+            for (int b = 0; b < WCB; ++b) {
+                Rt[(size_t)c * TLD + jj + b] = acc[q][b];
+                if (hasv && jj + b < jn) Vk[(size_t)rk * n + j0 + jj + b] = acc[q][b] * rs;
+            }
+        }
+    }
+    __syncthreads();
+    {   // Y = sum_q coef_q s_{kidx_q} R[kidx_q, :]: rows r = 32 p + lane
+        float acc[MRR][WCB];
+#pragma unroll
+        for (int p = 0; p < MRR; ++p)
+#pragma unroll
+            for (int b = 0; b < WCB; ++b) acc[p][b] = 0.0f;
+#pragma unroll 2
+        for (int q = 0; q < keep; ++q) {
+            const int c = kq[q];
+            const float w = cq[q];
+            const float* col = Ss + (size_t)c * lds + lane;
+            float av[MRR];
+#pragma unroll
+            for (int p = 0; p < MRR; ++p) av[p] = col[32 * p] * w;
+            const float4 g0 = *reinterpret_cast<const float4*>(Rt + (size_t)c * TLD + jj);
+            const float4 g1 = *reinterpret_cast<const float4*>(Rt + (size_t)c * TLD + jj + 4);
+            const float gv[WCB] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+#pragma unroll
+            for (int p = 0; p < MRR; ++p)
+#pragma unroll
+                for (int b = 0; b < WCB; ++b) acc[p][b] = fmaf(av[p], gv[b], acc[p][b]);
+        }
+#pragma unroll
+        for (int p = 0; p < MRR; ++p) {
+            const int r = 32 * p + lane;
+            if (r >= m) continue;
+#pragma unroll
+            for (int b = 0; b < WCB; ++b)
+                if (jj + b < jn) at(r, j0 + jj + b) = acc[p][b];
+        }
+    }
+    if (hasv && t == 0 && tid == 0) wrec[k] = 1;
+}
+
 }  // namespace
 
 // rows per lane of the GEMM's tiles (even, 2..8) and of the QR's columns (even, 2..28)
@@ -380,7 +541,8 @@ cudaError_t launch_warm_gemm(const JacobiPlan& p, const T* data, const T* Q, con
 }
 
 template <typename T>
-cudaError_t launch_warm_qr(const JacobiPlan& p, T* vrec, int* wrec, T* Q, int* flag, const AdmmCtl* ctl, cudaStream_t s)
+cudaError_t launch_warm_qr(const JacobiPlan& p, const T* vrec, size_t vstride, int* wrec, T* Q, int* flag,
+                           const AdmmCtl* ctl, cudaStream_t s)
 {
     if (!warm_supported(p)) return cudaErrorInvalidValue;
     const size_t sm = warm_qr_smem(p.n, sizeof(T));
@@ -406,14 +568,53 @@ cudaError_t launch_warm_qr(const JacobiPlan& p, T* vrec, int* wrec, T* Q, int* f
     // a warp per two chunks of four columns, 4 to 16 warps
     int warps = (p.n + 7) / 8;
     warps = warps < 4 ? 4 : (warps > WQ / 32 ? WQ / 32 : warps);
+    kern<<<(unsigned)p.n3, 32 * warps, sm, s>>>(vrec, p.n, vstride, wrec, Q, flag, ctl);
+    return cudaGetLastError();
+}
+
+bool tail_supported(const JacobiPlan& p)
+{
+    if (!warm_supported(p)) return false;
+    const int mrr = gemm_mr(p.m), mrc = (p.n + 31) / 32;
+    return mrc <= mrr && mrc >= mrr - 1 && 32 * mrr <= p.ldA &&
+           tail_smem_floats(p.n, p.ldA, p.nb * p.K, mrc, mrr) * sizeof(float) <= kMaxDynSmem;
+}
+
+template <typename T>
+cudaError_t launch_warm_tail(const JacobiPlan& p, T* data, const T* S, const float* info, T* V, int* wrec,
+                             const AdmmCtl* ctl, cudaStream_t s)
+{
+    static_assert(sizeof(T) == 4, "FP32 only");
+    if (!tail_supported(p)) return cudaErrorInvalidValue;
+    const int mrr = gemm_mr(p.m), mrc = (p.n + 31) / 32;
+    decltype(&warm_tail_kernel<1, 2>) kern = nullptr;
+    switch (mrr * 10 + mrc) {
+    case 21: kern = warm_tail_kernel<1, 2>; break;
+    case 22: kern = warm_tail_kernel<2, 2>; break;
+    case 43: kern = warm_tail_kernel<3, 4>; break;
+    case 44: kern = warm_tail_kernel<4, 4>; break;
+    case 65: kern = warm_tail_kernel<5, 6>; break;
+    case 66: kern = warm_tail_kernel<6, 6>; break;
+    case 87: kern = warm_tail_kernel<7, 8>; break;
+    case 88: kern = warm_tail_kernel<8, 8>; break;
+    default: return cudaErrorInvalidValue;  // a shape whose n is far below m keeps the in-kernel tail
+    }
+    const size_t sm = tail_smem_floats(p.n, p.ldA, p.nb * p.K, mrc, mrr) * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
     const size_t stride = (size_t)p.ldA * p.nb * p.K;
-    kern<<<(unsigned)p.n3, 32 * warps, sm, s>>>(vrec, p.n, stride, wrec, Q, flag, ctl);
+    const dim3 grid((unsigned)((p.n + TJ - 1) / TJ), (unsigned)p.n3);
+    kern<<<grid, 32 * TW, sm, s>>>(reinterpret_cast<float*>(data), p.n1, p.n2, p.m, p.n, p.tr, p.ldA, p.nb * p.K,
+                                   stride, reinterpret_cast<const float*>(S), info, reinterpret_cast<float*>(V), wrec,
+                                   ctl);
     return cudaGetLastError();
 }
 
 template cudaError_t launch_warm_gemm<float>(const JacobiPlan&, const float*, const float*, const int*, float*,
                                              const AdmmCtl*, cudaStream_t);
-template cudaError_t launch_warm_qr<float>(const JacobiPlan&, float*, int*, float*, int*, const AdmmCtl*,
-                                           cudaStream_t);
+template cudaError_t launch_warm_qr<float>(const JacobiPlan&, const float*, size_t, int*, float*, int*,
+                                           const AdmmCtl*, cudaStream_t);
+template cudaError_t launch_warm_tail<float>(const JacobiPlan&, float*, const float*, const float*, float*, int*,
+                                             const AdmmCtl*, cudaStream_t);
 
 }  // namespace tnn

@@ -167,9 +167,9 @@ _lib.tnn_admm_batch_destroy.argtypes = [_vp]
 _lib.tnn_admm_batch_destroy.restype = None
 BATCH_GRAPH = 1
 BATCH_AUTOTUNE = 2
-NKERNELS = 12
+NKERNELS = 13
 KERNEL_KINDS = ["tube", "tube_fwd_admm", "jacobi_svt", "tube_inv_admm", "admm_finalize", "ctl_init", "admm_init",
-                "jacobi_svd", "facewise", "dft", "jacobi_plain", "warm"]
+                "jacobi_svd", "facewise", "dft", "jacobi_plain", "warm", "svt_tail"]
 _lib.tsvt_dft.argtypes = [_vp, _vp, Shape, _ct.c_double, _ct.c_int, _vp, _ct.POINTER(_ct.c_double), _vp]
 _lib.tsvt_dft.restype = _st
 _lib.tsvt_dct_plain.argtypes = [_vp, _vp, Shape, _ct.c_double, _ct.c_int, _vp, _ct.POINTER(_ct.c_double), _vp]

@@ -73,7 +73,8 @@ def test_server_footprint(tnn):
     # least; the Jacobi scratch only when the slices are not in shared memory;
     # for a warm-started job also its warm-start state (tnn_admm_warm_size)
     # and the scratch of its start columns (one L R x nb K working copy per
-    # slice, the slice oriented with its rows the longer side)
+    # slice, the slice oriented with its rows the longer side) and of the
+    # offloaded SVT tail's record
     import ctypes
     for shape, prec in (((144, 176, 100), "tf32x3"), ((48, 48, 16), "fp64"), ((512, 512, 31), "bf16split"),
                         ((300, 20, 7), "fp32")):
@@ -86,6 +87,8 @@ def test_server_footprint(tnn):
         warm = wb.value
         if warm:
             warm += shape[2] * plan["L"] * plan["R"] * plan["nb"] * plan["K"] * elem + 4 * shape[2]
+            # the offloaded SVT tail's per-slice record: 4 (nb K) + 4 words
+            warm += shape[2] * 4 * (4 * plan["nb"] * plan["K"] + 4)
         # warm-started: the video-shaped FP32 job; not FP64, not slices on clusters or over 256 rows
         assert (warm > 0) == (shape == (144, 176, 100))
         assert fp >= 4 * N * elem + N + plan["work_bytes"] + warm

@@ -911,10 +911,16 @@ def probe_admm_trace(torch, inputs, tnn):
             if it in LOGGED_ITERS:
                 lg = ctx.last_sweep_log()
                 keep = sorted({0, 1, 2, 50, slow})
-                logged[it] = {k: [[round(float(v), 9) for v in row] for row in lg[k] if row.any()] for k in keep}
+                logged[it] = {k: {"sweeps": [[round(float(v), 9) for v in row] for row in lg[k, :8] if row.any()],
+                                  "phase_cycles": [float(v) for v in lg[k, 8, :4]]} for k in keep}
+                ph = lg[:, 8, :4].astype(np.float64)
+                logged[it]["phase_cycles_mean"] = [float(v) for v in ph.mean(0)]
+                logged[it]["phase_cycles_max"] = [float(v) for v in ph.max(0)]
         print(json.dumps({"probe": "admm_trace", "workload": "144x176x100 video-shaped, 20% observed, tf32x3",
                           "total_ms": sum(r["ms"] for r in rows), "rows": rows,
-                          "sweep_log_fields": ["big", "wide", "big_lowlow", "max_c_big", "max_t_big", "max_t_all"],
+                          "sweep_log_fields": ["big", "wide", "big_lowlow", "max_c_big", "max_t_big", "max_t_all",
+                                               "sweep_cycles", "stop_test_cycles"],
+                          "phase_cycle_fields": ["load", "sweeps", "tail", "total"],
                           "sweep_logs": logged}))
 
 

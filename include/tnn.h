@@ -276,14 +276,17 @@ tnn_status tnn_last_jacobi_stats(tnn_ctx* ctx, int64_t out[6]);
 tnn_status tnn_last_slice_stats(tnn_ctx* ctx, int64_t n, int32_t* sweeps, int32_t* kept, int64_t* rotations);
 
 /* The per-sweep log of the last Jacobi launch on ctx, recorded when
- * TNN_OPT_JACOBI_SWEEP_LOG was 1 for it: for each slice k < min(n, slices)
- * and sweep s < 8, six floats at out[(k * 8 + s) * 6 ...]: the sweep's big
- * rotations (|gamma| > 2 tol sqrt(alpha beta)), its wide rotations (those
- * that block the small-rotation stop), its big rotations between two
- * columns below tau, the largest |gamma| / sqrt(alpha beta) of its big
- * rotations, the largest |t| of its big rotations and the largest |t| of
- * all its rotations; all zero for sweeps not run (and for slices spread over
- * a cluster, which keep no log).  out is a host array of n * 48 floats.
+ * TNN_OPT_JACOBI_SWEEP_LOG was 1 for it: for each slice k < min(n, slices),
+ * nine rows of eight floats at out[(k * 9 + row) * 8 ...].  Row s < 8 is
+ * sweep s: its big rotations (|gamma| > 2 tol sqrt(alpha beta)), its wide
+ * rotations (those that block the small-rotation stop), its big rotations
+ * between two columns below tau, the largest |gamma| / sqrt(alpha beta) of
+ * its big rotations, the largest |t| of its big rotations and of all its
+ * rotations, the sweep's SM clock cycles and those of the stopping tests
+ * after it (certificates included); all zero for sweeps not run.  Row 8 is
+ * the slice's cycles in the load (start columns and norms), the sweeps, the
+ * tail (singular values, recovery or record, rebuild) and in all.  Slices
+ * spread over a cluster keep no log.  out is a host array of n * 72 floats.
  * TNN_EINVAL if the last launch kept no log.  Synchronises the last stream
  * used. */
 tnn_status tnn_last_sweep_log(tnn_ctx* ctx, int64_t n, float* out);

@@ -783,6 +783,7 @@ template <typename T, int K, int R, int L, bool SMEM, bool WITHV, bool ITEMS = f
 __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KArgs<T> a)
 {
     if (a.ctl && a.ctl->done) return;
+    const long long t_start = clock64();  // phase times for the sweep log
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int W = blockDim.x >> 5;
@@ -1027,7 +1028,9 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
             if (lane == 0) anorm[c] = s2;  // the scales are all 1 here
         }
     }
+    const long long t_load = clock64();
     while (!skip && sweeps < max_sweeps) {
+        const long long t_sweep = clock64();
         if (tid == 0) { s_rot = 0; s_rotll = 0; s_wide = 0; s_lo = 0.0; s_nlo = 0; s_lg[0] = s_lg[1] = s_lg[2] = 0; }
         cnt.cbig = cnt.tbig = cnt.tall = 0.f;
         __syncthreads();
@@ -1106,13 +1109,19 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
         }
         __syncthreads();
         const int nrot = s_rot, nrotll = s_rotll;
-        if (a.sweep_log && tid == 0 && sweeps < kSweepLogSweeps && !item) {
+        long long t_dec = 0;
+        float* lg = (a.sweep_log && tid == 0 && sweeps < kSweepLogSweeps && !item)
+                        ? a.sweep_log + ((size_t)slice * (kSweepLogSweeps + 1) + sweeps) * kSweepLogVals
+                        : nullptr;
+        if (lg) {
             // big rotations, wide ones (the small-rotation stop), big low-low
             // ones, largest |gamma| / sqrt(alpha beta) of the big ones,
-            // largest |t| of the big ones and of all
-            float* lg = a.sweep_log + ((size_t)slice * kSweepLogSweeps + sweeps) * kSweepLogVals;
+            // largest |t| of the big ones and of all, then the sweep's cycles
+            // (thread 0's clock) and those of the stopping tests after it
+            t_dec = clock64();
             lg[0] = (float)nrot; lg[1] = (float)s_wide; lg[2] = (float)nrotll;
             lg[3] = __int_as_float(s_lg[0]); lg[4] = __int_as_float(s_lg[1]); lg[5] = __int_as_float(s_lg[2]);
+            lg[6] = (float)(t_dec - t_sweep);
         }
         ++sweeps;
         // converged: no big rotation in the sweep, or only small ones (every
@@ -1167,8 +1176,10 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
             if (amax < 0.999 * tau_s * tau_s) done = low_cert(true);  // every column is in the low set
         }
         __syncthreads();
+        if (lg) lg[7] = (float)(clock64() - t_dec);
         if (done) { converged = 1; break; }
     }
+    const long long t_sweeps = clock64();
     if (cnt.pairs) atomicAdd(&s_pairs, (unsigned long long)cnt.pairs);
     if (cnt.rots) atomicAdd(&s_rots, (unsigned long long)cnt.rots);
 
@@ -1414,6 +1425,14 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
         }
     }
     __syncthreads();
+    if (a.sweep_log && tid == 0 && !item) {  // phase cycles: load, sweeps, tail, total
+        float* ph = a.sweep_log + ((size_t)slice * (kSweepLogSweeps + 1) + kSweepLogSweeps) * kSweepLogVals;
+        const long long t_end = clock64();
+        ph[0] = (float)(t_load - t_start);
+        ph[1] = (float)(t_sweeps - t_load);
+        ph[2] = (float)(t_end - t_sweeps);
+        ph[3] = (float)(t_end - t_start);
+    }
     if (tid == 0) {
         SliceStats st;
         st.nuc = s_nuc;

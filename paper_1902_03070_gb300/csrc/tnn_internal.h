@@ -31,10 +31,11 @@ struct AdmmCtl {
 
 // Per-slice Jacobi statistics, written by the SVT/SVD kernels.
 // Per-sweep log of the single-CTA Jacobi SVT (TNN_OPT_JACOBI_SWEEP_LOG): for
-// each slice and sweep s < kSweepLogSweeps, kSweepLogVals floats.
+// each slice, kSweepLogSweeps rows (one per sweep) and a row of phase times,
+// kSweepLogVals floats each.
 constexpr int kSweepLogSweeps = 8;
-constexpr int kSweepLogVals = 6;
-constexpr int sweep_log_floats = kSweepLogSweeps * kSweepLogVals;
+constexpr int kSweepLogVals = 8;
+constexpr int sweep_log_floats = (kSweepLogSweeps + 1) * kSweepLogVals;
 
 // Per-slice record the Jacobi SVT leaves for the offloaded tail
 // (warm_tail_kernel), in 32-bit words: coef[q] (q < keep), 1 / (d_c |s_c|^2)

@@ -530,11 +530,13 @@ class Context:
 
     def last_sweep_log(self):
         """Per-sweep log of the last Jacobi launch (OPT_JACOBI_SWEEP_LOG on):
-        a numpy array (slices, 8 sweeps, 6): big rotations, wide rotations,
-        big low-low rotations, largest |gamma|/sqrt(alpha beta) of the big
-        ones, largest |t| of the big ones, largest |t| of all."""
+        a numpy array (slices, 9, 8).  Rows 0-7 are sweeps: big rotations,
+        wide rotations, big low-low rotations, largest |gamma|/sqrt(alpha
+        beta) of the big ones, largest |t| of the big ones and of all, the
+        sweep's clock cycles, the stopping tests' cycles.  Row 8: cycles of
+        the load, the sweeps, the tail and the whole slice."""
         n = self.last_jacobi_stats()["slices"]
-        out = _np.zeros((max(n, 1), 8, 6), dtype=_np.float32)
+        out = _np.zeros((max(n, 1), 9, 8), dtype=_np.float32)
         self._chk(_lib.tnn_last_sweep_log(self._h, n, out.ctypes.data_as(_ct.POINTER(_ct.c_float))),
                   "tnn_last_sweep_log")
         return out[:n]

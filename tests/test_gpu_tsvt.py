@@ -423,15 +423,20 @@ def test_sweep_log(ctx):
     finally:
         ctx.set_option(tnn.OPT_JACOBI_SWEEP_LOG, 0)
     sweeps = ctx.last_slice_stats()["sweeps"]
-    assert log.shape == (shape[2], 8, 6)
+    assert log.shape == (shape[2], 9, 8)
     for k in range(shape[2]):
         s = sweeps[k]
         assert 1 <= s <= 8
         last = log[k, s - 1]
         assert last[0] == 0 or last[1] == 0
-        assert np.all(log[k, s:] == 0)
+        assert np.all(log[k, s:8] == 0)
         assert log[k, 0, 0] > 0  # a random slice is not orthogonal to begin with
         assert np.all(np.isfinite(log[k])) and np.all(log[k] >= 0)
+        assert np.all(log[k, :s, 6] > 0)  # every sweep took time
+        ph = log[k, 8]
+        # (the parts are rounded to float one by one)
+        assert ph[3] >= 0.999 * (ph[0] + ph[1] + ph[2]) > 0
+        assert ph[1] >= 0.999 * (log[k, :s, 6].sum() + log[k, :s, 7].sum())
     _run(ctx, Z, tau, "fp32")
     with pytest.raises(tnn.TnnError):
         ctx.last_sweep_log()  # the launch after the option was cleared kept none

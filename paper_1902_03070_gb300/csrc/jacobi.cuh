@@ -967,52 +967,77 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
         // zero: the zero-SVT certificate below (every column in the set, bound below tau^2)
         const double lim = zero ? (1.0 - 1e-4) * tau_s * tau_s
                                 : (tau_s + 1e-7 * sqrt(s_yn)) * (tau_s + 1e-7 * sqrt(s_yn));
-        constexpr int RG = (R * L + 31) / 32;  // rows per lane (lane-strided; rows past L R are padding)
+        // The Gram G = S_lo^T S_lo (true scales: G_ij = d_i d_j s_i.s_j) in 4 x 4
+        // blocks, a thread per block of its upper triangle, each entry a
+        // column-pair dot product over the m rows; the row sums of |G_ij|
+        // are added up as 64-bit fixed point (unit tau^2 2^-40, each term
+        // rounded up), so that they are an upper bound and do not depend on
+        // the order of the additions.
         const double uu = (double)Num<T>::unit();
         double wmax = 0.0;
-        for (int i0 = 2 * warp; i0 < nl; i0 += 2 * W) {
-            const int c0 = rank[i0], c1 = rank[i0 + 1 < nl ? i0 + 1 : i0];
-            T x0[RG], x1[RG];
-#pragma unroll
-            for (int q = 0; q < RG; ++q) {
-                const int r = q * 32 + lane;
-                x0[q] = r < ldA ? Aw[(size_t)c0 * ldA + r] : T(0);
-                x1[q] = r < ldA ? Aw[(size_t)c1 * ldA + r] : T(0);
-            }
-            T r0 = T(0), r1 = T(0);
-            for (int j0 = 0; j0 < nl; j0 += 32) {
-                T p0[32], p1[32];
-#pragma unroll
-                for (int jj = 0; jj < 32; ++jj) {
-                    p0[jj] = T(0);
-                    p1[jj] = T(0);
-                    if (j0 + jj < nl) {
-                        const T* col = Aw + (size_t)rank[j0 + jj] * ldA;
-#pragma unroll
-                        for (int q = 0; q < RG; ++q) {
-                            const int r = q * 32 + lane;
-                            const T v = r < ldA ? col[r] : T(0);
-                            p0[jj] = fma(x0[q], v, p0[jj]);
-                            p1[jj] = fma(x1[q], v, p1[jj]);
-                        }
-                    }
-                }
-                const T g0 = reduce_scatter<T, 32, 32>(p0, lane);  // lane: G(i, list[j0 + lane]) / scales
-                const T g1 = reduce_scatter<T, 32, 32>(p1, lane);
-                if (j0 + lane < nl) {
-                    const T dj = dsc[rank[j0 + lane]];
-                    r0 += fabs(g0 * dj);
-                    r1 += fabs(g1 * dj);
-                }
-            }
-            r0 = group_sum<32>(r0);
-            r1 = group_sum<32>(r1);
-            const double b0 = (double)(r0 * dsc[c0]) * (1.0 + 2.0 * nl * uu) +
-                              2.0 * m * uu * sqrt(fmax((double)anorm[c0], 0.0)) * S1;
-            const double b1 = (double)(r1 * dsc[c1]) * (1.0 + 2.0 * nl * uu) +
-                              2.0 * m * uu * sqrt(fmax((double)anorm[c1], 0.0)) * S1;
-            wmax = fmax(wmax, fmax(b0, b1));
+        unsigned long long* rsum = reinterpret_cast<unsigned long long*>(gbuf);  // nl words (gbuf is free during the sweeps)
+        const double unit = tau_s * tau_s * 0x1p-40;
+        if (!(unit > 0.0)) {
+            __syncthreads();
+            return false;
         }
+        for (int i = tid; i < nl; i += nthr) rsum[i] = 0ull;
+        __syncthreads();
+        const int B = (nl + 3) / 4, nblk = B * (B + 1) / 2;
+        for (int blk = tid; blk < nblk; blk += nthr) {
+            int bi = 0, rem = blk;  // blk -> (bi, bj), bi <= bj, row by row of the upper triangle
+            while (rem >= B - bi) { rem -= B - bi; ++bi; }
+            const int bj = bi + rem;
+            const T* ci[4];
+            const T* cj[4];
+            bool vi[4], vj[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                vi[u] = 4 * bi + u < nl;
+                vj[u] = 4 * bj + u < nl;
+                ci[u] = Aw + (size_t)rank[vi[u] ? 4 * bi + u : 0] * ldA;
+                cj[u] = Aw + (size_t)rank[vj[u] ? 4 * bj + u : 0] * ldA;
+            }
+            T acc[4][4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = T(0);
+            for (int r = 0; r < m; ++r) {
+                T x[4], y[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    x[u] = ci[u][r];
+                    y[u] = cj[u][r];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u][v] = fma(x[u], y[v], acc[u][v]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (!vi[u]) continue;
+                const double di = (double)dsc[rank[4 * bi + u]];
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    if (!vj[v]) continue;
+                    const double g = fabs((double)acc[u][v]) * di * (double)dsc[rank[4 * bj + v]];
+                    const unsigned long long q = (unsigned long long)ceil(g / unit);
+                    atomicAdd(&rsum[4 * bi + u], q);
+                    if (bi != bj) atomicAdd(&rsum[4 * bj + v], q);
+                }
+            }
+        }
+        __syncthreads();
+        for (int i = tid; i < nl; i += nthr) {
+            const int c = rank[i];
+            const double b = (double)rsum[i] * unit * (1.0 + 2.0 * nl * uu) +
+                             2.0 * m * uu * sqrt(fmax((double)anorm[c], 0.0)) * S1;
+            wmax = fmax(wmax, b);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) wmax = fmax(wmax, __shfl_xor_sync(FULL, wmax, o));
         if (lane == 0) atomicMax(&s_maxb, (unsigned long long)__double_as_longlong(wmax));
         __syncthreads();
         const bool ok = __longlong_as_double((long long)s_maxb) <= lim;

@@ -342,16 +342,19 @@ __global__ void __launch_bounds__(WQ) warm_qr_kernel(const T* __restrict__ vrec,
 //   Y[:, tile] = sum_q S[:, kidx_q] coef_q R[kidx_q, tile]
 // with coef_q = (1 - tau / sigma_q) / |s_q|^2: the V-free rebuild of the
 // shrunk slice, Y = sum_{sigma > tau} (1 - tau / sigma) u u^T A0.  Each warp
-// computes 32 MR x 8 output tiles (lanes over rows), as in the A Q product.
+// computes 8 output columns (lanes over rows) for one half of the rows, as
+// in the A Q product, so that 12 warps share a tile.
 constexpr int TJ = 48;            // output columns per CTA
-constexpr int TW = TJ / WCB;      // warps per CTA
+constexpr int TWC = TJ / WCB;     // column tiles per CTA
+constexpr int TW = 2 * TWC;       // warps per CTA: each column tile's rows in two halves
 constexpr int TLD = TJ + 4;       // leading dimension of the row-major tiles (16-byte rows)
 
 // shared memory: S as the Jacobi kernel laid it out (ldA rows per column), the
-// A0 tile and the R tile (32 MR rows of TLD), the kept columns' coef and index
+// A0 tile (later the Y tile) and the R tile (32 MR rows of TLD), then per
+// column the recovery scale and rank and per kept column its coef and index
 __host__ __device__ inline size_t tail_smem_floats(int n, int ldA, int npad, int mrc, int mrr)
 {
-    return ((size_t)n * ldA + 3) / 4 * 4 + (size_t)32 * mrr * TLD + (size_t)32 * mrc * TLD + 2 * (size_t)npad;
+    return ((size_t)n * ldA + 3) / 4 * 4 + (size_t)32 * mrr * TLD + (size_t)32 * mrc * TLD + 4 * (size_t)npad;
 }
 
 template <int MRC, int MRR>
@@ -388,6 +391,8 @@ __global__ void __launch_bounds__(32 * TW) warm_tail_kernel(float* __restrict__ 
     float* Rt = At + (size_t)32 * MRR * TLD;                       // R tile, row c at Rt + c * TLD
     float* cq = Rt + (size_t)32 * MRC * TLD;                       // coef of the kept columns
     int* kq = reinterpret_cast<int*>(cq + npad);                   // the kept columns
+    float* rsm = cq + 2 * npad;                                    // recovery scale by column
+    int* rkm = reinterpret_cast<int*>(cq + 3 * npad);              // rank by column
     // S in one contiguous asynchronous copy (16-byte chunks)
     copy_to_shared(Ss, S + (size_t)k * stride, (size_t)n * lds, tid, 32 * TW);
     if (tr && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) && n1 % 4 == 0) {
@@ -414,80 +419,111 @@ __global__ void __launch_bounds__(32 * TW) warm_tail_kernel(float* __restrict__ 
         cq[q] = inf[q];
         kq[q] = iinf[3 * npad + q];
     }
+    if (hasv)
+        for (int c = tid; c < n; c += 32 * TW) {
+            rsm[c] = inf[npad + c];
+            rkm[c] = iinf[2 * npad + c];
+        }
     cp_async_wait_all();
     __syncthreads();
-    const int jj = warp * WCB;  // this warp's 8 columns of the tile
-    {   // R = S^T A0: rows c = 32 q + lane
-        float acc[MRC][WCB];
+    const int jj = (warp % TWC) * WCB;  // this warp's 8 columns of the tile
+    const int h = warp / TWC;           // and its half of the rows
+    {   // R = S^T A0: rows c = 32 q + lane, q in this half's blocks
+        constexpr int QH = (MRC + 1) / 2;
+        float acc[QH][WCB];
 #pragma unroll
-        for (int q = 0; q < MRC; ++q)
+        for (int q = 0; q < QH; ++q)
 #pragma unroll
             for (int b = 0; b < WCB; ++b) acc[q][b] = 0.0f;
-        const float* sp[MRC];
+        const float* sp[QH];
+        bool cv[QH];
 #pragma unroll
-        for (int q = 0; q < MRC; ++q) {
-            const int c = 32 * q + lane;
-            sp[q] = Ss + (size_t)(c < n ? c : 0) * lds;
+        for (int q = 0; q < QH; ++q) {
+            const int c = 32 * (h * QH + q) + lane;
+            cv[q] = h * QH + q < MRC && c < n;
+            sp[q] = Ss + (size_t)(cv[q] ? c : 0) * lds;
         }
 #pragma unroll 2
         for (int r = 0; r < m; ++r) {
-            float av[MRC];
+            float av[QH];
 #pragma unroll
-            for (int q = 0; q < MRC; ++q) av[q] = (32 * q + lane < n) ? sp[q][r] : 0.0f;
+            for (int q = 0; q < QH; ++q) av[q] = cv[q] ? sp[q][r] : 0.0f;
             const float4 b0 = *reinterpret_cast<const float4*>(At + (size_t)r * TLD + jj);
             const float4 b1 = *reinterpret_cast<const float4*>(At + (size_t)r * TLD + jj + 4);
             const float bv[WCB] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
-            for (int q = 0; q < MRC; ++q)
+            for (int q = 0; q < QH; ++q)
 #pragma unroll
                 for (int b = 0; b < WCB; ++b) acc[q][b] = fmaf(av[q], bv[b], acc[q][b]);
         }
-        const int* irank = iinf + 2 * npad;
         float* Vk = V + (size_t)k * n * n;
 #pragma unroll
-        for (int q = 0; q < MRC; ++q) {
-            const int c = 32 * q + lane;
-            if (c >= n) continue;
-            const float rs = inf[npad + c];
-            const int rk = irank[c];
+        for (int q = 0; q < QH; ++q) {
+            if (!cv[q]) continue;
+            const int c = 32 * (h * QH + q) + lane;
 #pragma unroll
-            for (int b = 0; b < WCB; ++b) {
-                Rt[(size_t)c * TLD + jj + b] = acc[q][b];
-                if (hasv && jj + b < jn) Vk[(size_t)rk * n + j0 + jj + b] = acc[q][b] * rs;
+            for (int b = 0; b < WCB; ++b) Rt[(size_t)c * TLD + jj + b] = acc[q][b];
+            if (hasv) {
+                const float rs = rsm[c];
+                float* vrow = Vk + (size_t)rkm[c] * n + j0 + jj;
+#pragma unroll
+                for (int b = 0; b < WCB; ++b)
+                    if (jj + b < jn) vrow[b] = acc[q][b] * rs;
             }
         }
     }
     __syncthreads();
-    {   // Y = sum_q coef_q s_{kidx_q} R[kidx_q, :]: rows r = 32 p + lane
-        float acc[MRR][WCB];
+    {   // Y = sum_q coef_q s_{kidx_q} R[kidx_q, :]: rows r = 32 p + lane, p in this half's blocks
+        constexpr int PH = MRR / 2;
+        float acc[PH][WCB];
 #pragma unroll
-        for (int p = 0; p < MRR; ++p)
+        for (int p = 0; p < PH; ++p)
 #pragma unroll
             for (int b = 0; b < WCB; ++b) acc[p][b] = 0.0f;
 #pragma unroll 2
         for (int q = 0; q < keep; ++q) {
             const int c = kq[q];
             const float w = cq[q];
-            const float* col = Ss + (size_t)c * lds + lane;
-            float av[MRR];
+            const float* col = Ss + (size_t)c * lds + 32 * h * PH + lane;
+            float av[PH];
 #pragma unroll
-            for (int p = 0; p < MRR; ++p) av[p] = col[32 * p] * w;
+            for (int p = 0; p < PH; ++p) av[p] = col[32 * p] * w;
             const float4 g0 = *reinterpret_cast<const float4*>(Rt + (size_t)c * TLD + jj);
             const float4 g1 = *reinterpret_cast<const float4*>(Rt + (size_t)c * TLD + jj + 4);
             const float gv[WCB] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
 #pragma unroll
-            for (int p = 0; p < MRR; ++p)
+            for (int p = 0; p < PH; ++p)
 #pragma unroll
                 for (int b = 0; b < WCB; ++b) acc[p][b] = fmaf(av[p], gv[b], acc[p][b]);
         }
+        // the Y tile into the A0 tile's place (phase 1 is done with it)
 #pragma unroll
-        for (int p = 0; p < MRR; ++p) {
-            const int r = 32 * p + lane;
-            if (r >= m) continue;
-#pragma unroll
-            for (int b = 0; b < WCB; ++b)
-                if (jj + b < jn) at(r, j0 + jj + b) = acc[p][b];
+        for (int p = 0; p < PH; ++p) {
+            const int r = 32 * (h * PH + p) + lane;
+            float* yrow = At + (size_t)r * TLD + jj;
+            *reinterpret_cast<float4*>(yrow) = make_float4(acc[p][0], acc[p][1], acc[p][2], acc[p][3]);
+            *reinterpret_cast<float4*>(yrow + 4) = make_float4(acc[p][4], acc[p][5], acc[p][6], acc[p][7]);
         }
+    }
+    __syncthreads();
+    // coalesced stores of the Y tile
+    if (tr && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) && n1 % 4 == 0) {
+        for (int e = tid; e < m * (TJ / 4); e += 32 * TW) {
+            const int r = e / (TJ / 4), q = 4 * (e % (TJ / 4));
+            const float* y = At + (size_t)r * TLD + q;
+            float* d = src + (size_t)(j0 + q) + (size_t)n1 * r;
+            if (q + 3 < jn) *reinterpret_cast<float4*>(d) = *reinterpret_cast<const float4*>(y);
+            else
+                for (int u = 0; u < 4 && q + u < jn; ++u) d[u] = y[u];
+        }
+    } else if (tr) {
+        for (int e = tid; e < m * TJ; e += 32 * TW) {
+            const int r = e / TJ, j = e % TJ;
+            if (j < jn) src[(size_t)(j0 + j) + (size_t)n1 * r] = At[(size_t)r * TLD + j];
+        }
+    } else {
+        for (int j = warp; j < jn; j += TW)
+            for (int r = lane; r < m; r += 32) src[(size_t)r + (size_t)n1 * (j0 + j)] = At[(size_t)r * TLD + j];
     }
     if (hasv && t == 0 && tid == 0) wrec[k] = 1;
 }

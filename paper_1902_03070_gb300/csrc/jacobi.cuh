@@ -969,21 +969,21 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
                                 : (tau_s + 1e-7 * sqrt(s_yn)) * (tau_s + 1e-7 * sqrt(s_yn));
         // The Gram G = S_lo^T S_lo (true scales: G_ij = d_i d_j s_i.s_j) in 4 x 4
         // blocks, a thread per block of its upper triangle, each entry a
-        // column-pair dot product over the m rows; the row sums of |G_ij|
-        // are added up as 64-bit fixed point (unit tau^2 2^-40, each term
-        // rounded up), so that they are an upper bound and do not depend on
-        // the order of the additions.
+        // column-pair dot product over the m rows.  Each block writes its
+        // row sums of |G_ij| (and, off the diagonal, those of its transpose)
+        // into its own slot of part[row][block], and each row's slots are
+        // added in block order, so the bound does not depend on thread
+        // timing; the summation's rounding is covered by the (1 + 2 nl u)
+        // factor below.  All in the kernel's precision (FP64 here would run
+        // at a small fraction of the FP32 rate).
         const double uu = (double)Num<T>::unit();
         double wmax = 0.0;
-        unsigned long long* rsum = reinterpret_cast<unsigned long long*>(gbuf);  // nl words (gbuf is free during the sweeps)
-        const double unit = tau_s * tau_s * 0x1p-40;
-        if (!(unit > 0.0)) {
+        const int B = (nl + 3) / 4, nblk = B * (B + 1) / 2;
+        T* part = gbuf;  // nl x B (gbuf is free during the sweeps)
+        if ((size_t)nl * B > (size_t)W * 4 * npad) {  // no room: no certificate
             __syncthreads();
             return false;
         }
-        for (int i = tid; i < nl; i += nthr) rsum[i] = 0ull;
-        __syncthreads();
-        const int B = (nl + 3) / 4, nblk = B * (B + 1) / 2;
         for (int blk = tid; blk < nblk; blk += nthr) {
             int bi = 0, rem = blk;  // blk -> (bi, bj), bi <= bj, row by row of the upper triangle
             while (rem >= B - bi) { rem -= B - bi; ++bi; }
@@ -991,12 +991,16 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
             const T* ci[4];
             const T* cj[4];
             bool vi[4], vj[4];
+            T di[4], dj[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 vi[u] = 4 * bi + u < nl;
                 vj[u] = 4 * bj + u < nl;
-                ci[u] = Aw + (size_t)rank[vi[u] ? 4 * bi + u : 0] * ldA;
-                cj[u] = Aw + (size_t)rank[vj[u] ? 4 * bj + u : 0] * ldA;
+                const int a = rank[vi[u] ? 4 * bi + u : 0], b = rank[vj[u] ? 4 * bj + u : 0];
+                ci[u] = Aw + (size_t)a * ldA;
+                cj[u] = Aw + (size_t)b * ldA;
+                di[u] = vi[u] ? dsc[a] : T(0);
+                dj[u] = vj[u] ? dsc[b] : T(0);
             }
             T acc[4][4];
 #pragma unroll
@@ -1015,24 +1019,27 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
 #pragma unroll
                     for (int v = 0; v < 4; ++v) acc[u][v] = fma(x[u], y[v], acc[u][v]);
             }
+            T rs[4] = {T(0), T(0), T(0), T(0)}, cs[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (!vi[u]) continue;
-                const double di = (double)dsc[rank[4 * bi + u]];
+            for (int u = 0; u < 4; ++u)
 #pragma unroll
                 for (int v = 0; v < 4; ++v) {
-                    if (!vj[v]) continue;
-                    const double g = fabs((double)acc[u][v]) * di * (double)dsc[rank[4 * bj + v]];
-                    const unsigned long long q = (unsigned long long)ceil(g / unit);
-                    atomicAdd(&rsum[4 * bi + u], q);
-                    if (bi != bj) atomicAdd(&rsum[4 * bj + v], q);
+                    const T g = fabs(acc[u][v]) * di[u] * dj[v];  // zero outside the list
+                    rs[u] += g;
+                    cs[v] += g;
                 }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (vi[u]) part[(size_t)(4 * bi + u) * B + bj] = rs[u];
+                if (bi != bj && vj[u]) part[(size_t)(4 * bj + u) * B + bi] = cs[u];
             }
         }
         __syncthreads();
         for (int i = tid; i < nl; i += nthr) {
             const int c = rank[i];
-            const double b = (double)rsum[i] * unit * (1.0 + 2.0 * nl * uu) +
+            T rsum = T(0);
+            for (int q = 0; q < B; ++q) rsum += part[(size_t)i * B + q];
+            const double b = (double)rsum * (1.0 + 2.0 * nl * uu) +
                              2.0 * m * uu * sqrt(fmax((double)anorm[c], 0.0)) * S1;
             wmax = fmax(wmax, b);
         }

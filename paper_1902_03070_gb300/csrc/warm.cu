@@ -27,7 +27,9 @@
 namespace tnn {
 namespace {
 
-constexpr int WQ = 512;   // threads per CTA of the QR (16 warps)
+constexpr int WQ = 512;   // threads per CTA of the QR for 28 rows per lane (16 warps) ...
+// ... and 32 warps up to 18 rows per lane (a chunk per warp for n <= 128 +)
+template <int NB> constexpr int qr_threads() { return NB <= 18 ? 1024 : WQ; }
 constexpr int WGM = 640;  // most threads per CTA of the GEMM (20 warps)
 constexpr int WCB = 8;    // output columns per warp tile of the GEMM
 constexpr int WMR = 8;    // most rows per lane of the GEMM (m <= 256)
@@ -161,8 +163,9 @@ __device__ __forceinline__ void make_reflector(T* x, int c, T s2, T* bet)
 // the segment's own two blocks are masked to rows >= c).
 
 // Factorisation step c: the columns j > c go in chunks of four (chunk q =
-// columns c + 1 + 4 q .. c + 4 + 4 q, to warp q mod W) and get reflector c;
-// warp 0, whose first chunk holds column c + 1, then forms reflector c + 1.
+// columns c + 1 + 4 q .. c + 4 + 4 q) and get reflector c.  Warp 0 takes
+// chunk 0 alone, which holds column c + 1, and then forms reflector c + 1;
+// the other chunks go to warps 1 .. W - 1 in turn.
 template <typename T, int NB, int I0>
 __device__ __forceinline__ void qr_step(T* Vs, T* bet, int ldv, int n, int c, int warp, int W, int lane)
 {
@@ -173,7 +176,7 @@ __device__ __forceinline__ void qr_step(T* Vs, T* bet, int ldv, int n, int c, in
 #pragma unroll
     for (int i = I0; i < NB; ++i) xv[i] = (i >= I0 + 2 || 8 * i + l8 >= c) ? x[8 * i] : T(0);
     const int nq = (n - 1 - c + 3) >> 2;
-    for (int q = warp; q < nq; q += W) {
+    for (int q = warp; q < (warp == 0 ? 1 : nq); q += W - 1) {
         const int j = c + 1 + 4 * q + sg;
         const bool valid = j < n;
         T* y = Vs + (size_t)(valid ? j : c) * ldv + l8;  // a lane past the last column reads column c, stores nothing
@@ -262,7 +265,7 @@ __host__ __device__ inline int qr_ldv(int nb)
 }
 
 template <typename T, int NB>
-__global__ void __launch_bounds__(WQ) warm_qr_kernel(const T* __restrict__ vrec, int n, size_t stride, int* __restrict__ wrec,
+__global__ void __launch_bounds__(qr_threads<NB>()) warm_qr_kernel(const T* __restrict__ vrec, int n, size_t stride, int* __restrict__ wrec,
                                                     T* __restrict__ Q, int* __restrict__ flag,
                                                     const AdmmCtl* __restrict__ ctl)
 {
@@ -601,9 +604,10 @@ cudaError_t launch_warm_qr(const JacobiPlan& p, const T* vrec, size_t vstride, i
     }
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    // a warp per two chunks of four columns, 4 to 16 warps
-    int warps = (p.n + 7) / 8;
-    warps = warps < 4 ? 4 : (warps > WQ / 32 ? WQ / 32 : warps);
+    // a warp per chunk of four columns, 4 to 32 warps (16 beyond 18 rows per lane)
+    const int wmax = qr_nb(p.n) <= 18 ? 32 : WQ / 32;
+    int warps = (p.n + 3) / 4;
+    warps = warps < 4 ? 4 : (warps > wmax ? wmax : warps);
     kern<<<(unsigned)p.n3, 32 * warps, sm, s>>>(vrec, p.n, vstride, wrec, Q, flag, ctl);
     return cudaGetLastError();
 }

@@ -27,8 +27,9 @@
 namespace tnn {
 namespace {
 
-constexpr int WQ = 512;   // threads per CTA of the QR (16 warps)
-template <int NB> constexpr int qr_threads() { return WQ; }
+constexpr int WQ = 512;   // threads per CTA of the QR for 28 rows per lane (16 warps) ...
+// ... and 32 warps up to 18 rows per lane (a chunk per warp for n <= 128 +)
+template <int NB> constexpr int qr_threads() { return NB <= 18 ? 1024 : WQ; }
 constexpr int WGM = 640;  // most threads per CTA of the GEMM (20 warps)
 constexpr int WCB = 8;    // output columns per warp tile of the GEMM
 constexpr int WMR = 8;    // most rows per lane of the GEMM (m <= 256)
@@ -161,152 +162,60 @@ __device__ __forceinline__ void make_reflector(T* x, int c, T s2, T* bet)
 // row blocks from that segment on (the template argument I0 = 2 (c / 16);
 // the segment's own two blocks are masked to rows >= c).
 
-// Panel QR.  Panel s is the columns c0 = 4 s .. 4 s + 3, exactly one warp's
-// four 8-lane groups, and its four reflectors all start in one 16-row
-// segment (I0 = 2 (s / 4)).
-
-// The four reflectors of panel s applied to the chunk of columns 4 q ..
-// 4 q + 3 (this warp's groups), in compact form: with d_k = v_k . a (four
-// independent dot products) and G_ki = v_k . v_i (i < k, the panel's Gram),
-// w_k = beta_k (d_k - sum_{i<k} w_i G_ki) and a -= sum_k w_k v_k, which is
-// H_{c0+3} H_{c0+2} H_{c0+1} H_{c0} a.
+// Factorisation step c: the columns j > c go in chunks of four (chunk q =
+// columns c + 1 + 4 q .. c + 4 + 4 q) and get reflector c.  Warp 0 takes
+// chunk 0 alone, which holds column c + 1, and then forms reflector c + 1;
+// the other chunks go to warps 1 .. W - 1 in turn.
 template <typename T, int NB, int I0>
-__device__ __forceinline__ void qr_panel_update(T* Vs, const T* bet, const T* G, int ldv, int n, int s, int q,
-                                                int lane)
+__device__ __forceinline__ void qr_step(T* Vs, T* bet, int ldv, int n, int c, int warp, int W, int lane)
 {
     const int l8 = lane & 7, sg = lane >> 3;
-    const int c0 = 4 * s;
-    const int j = 4 * q + sg;
-    const bool valid = j < n;
-    T* y = Vs + (size_t)(valid ? j : c0) * ldv + l8;  // a group past the last column reads column c0, stores nothing
-    T yv[NB];
+    const T b = bet[c];
+    const T* x = Vs + (size_t)c * ldv + l8;
+    T xv[NB];
 #pragma unroll
-    for (int i = I0; i < NB; ++i) yv[i] = y[8 * i];
-    T d[4];
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-        const int c = c0 + kk;
-        const T* x = Vs + (size_t)(c < n ? c : c0) * ldv + l8;
-        T a0 = T(0), a1 = T(0);
-#pragma unroll
-        for (int i = I0; i < NB; ++i) {
-            const T xv = (c < n && (i >= I0 + 2 || 8 * i + l8 >= c)) ? x[8 * i] : T(0);
-            if ((i - I0) & 1) a1 = fma(xv, yv[i], a1);
-            else a0 = fma(xv, yv[i], a0);
-        }
-        d[kk] = a0 + a1;
-    }
-#pragma unroll
-    for (int o = 4; o > 0; o >>= 1)
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) d[kk] += __shfl_xor_sync(0xffffffffu, d[kk], o);
-    T w[4];
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-        T t = d[kk];
-#pragma unroll
-        for (int i = 0; i < kk; ++i) t = fma(-w[i], G[kk * 4 + i], t);
-        w[kk] = c0 + kk < n ? bet[c0 + kk] * t : T(0);
-    }
-#pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
-        const int c = c0 + kk;
-        if (c >= n) break;
-        const T* x = Vs + (size_t)c * ldv + l8;
+    for (int i = I0; i < NB; ++i) xv[i] = (i >= I0 + 2 || 8 * i + l8 >= c) ? x[8 * i] : T(0);
+    const int nq = (n - 1 - c + 3) >> 2;
+    for (int q = warp; q < (warp == 0 ? 1 : nq); q += W - 1) {
+        const int j = c + 1 + 4 * q + sg;
+        const bool valid = j < n;
+        T* y = Vs + (size_t)(valid ? j : c) * ldv + l8;  // a lane past the last column reads column c, stores nothing
+        T yv[NB];
+        T d0 = T(0), d1 = T(0);
 #pragma unroll
         for (int i = I0; i < NB; ++i) {
-            const T xv = (i >= I0 + 2 || 8 * i + l8 >= c) ? x[8 * i] : T(0);
-            yv[i] = fma(-w[kk], xv, yv[i]);
+            yv[i] = y[8 * i];
+            if ((i - I0) & 1) d1 = fma(xv[i], yv[i], d1);
+            else d0 = fma(xv[i], yv[i], d0);
         }
-    }
-    if (valid)
-#pragma unroll
-        for (int i = I0; i < NB; ++i) y[8 * i] = yv[i];
-}
-
-// Factorisation of panel s within one warp (its columns already carry all
-// earlier reflectors): for u = 0 .. 3, group u forms reflector c0 + u from
-// its column and the groups after it apply that reflector to theirs; then
-// the panel's Gram G_ki = v_k . v_i (i < k) for the compact update.
-template <typename T, int NB, int I0>
-__device__ __forceinline__ void qr_panel_factor(T* Vs, T* bet, T* G, int ldv, int n, int s, int lane)
-{
-    const int l8 = lane & 7, sg = lane >> 3;
-    const int c0 = 4 * s;
-    const bool valid = c0 + sg < n;
-    T* y = Vs + (size_t)(valid ? c0 + sg : c0) * ldv + l8;
-    __syncwarp();
-    T yv[NB];
-#pragma unroll
-    for (int i = I0; i < NB; ++i) yv[i] = y[8 * i];
-    for (int u = 0; u < 4; ++u) {
-        const int c = c0 + u;
-        if (c >= n) break;
+        T d = d0 + d1;
+        d += __shfl_xor_sync(0xffffffffu, d, 4);
+        d += __shfl_xor_sync(0xffffffffu, d, 2);
+        d += __shfl_xor_sync(0xffffffffu, d, 1);
+        const T f = b * d;
         T s2 = T(0);
 #pragma unroll
-        for (int i = I0; i < NB; ++i)
-            if (8 * i + l8 >= c) s2 = fma(yv[i], yv[i], s2);
-#pragma unroll
-        for (int o = 4; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-        if (sg == u && l8 == 0) make_reflector(Vs + (size_t)c * ldv, c, s2, bet);
-        __syncwarp();
-        const T b = bet[c];
-        const T* x = Vs + (size_t)c * ldv + l8;
-        T xv[NB];
-        T a0 = T(0), a1 = T(0);
-#pragma unroll
         for (int i = I0; i < NB; ++i) {
-            xv[i] = (i >= I0 + 2 || 8 * i + l8 >= c) ? x[8 * i] : T(0);
-            if ((i - I0) & 1) a1 = fma(xv[i], yv[i], a1);
-            else a0 = fma(xv[i], yv[i], a0);
+            const T v = fma(-f, xv[i], yv[i]);  // rows < c: xv = 0, the value is kept
+            if (valid) y[8 * i] = v;
+            if (8 * i + l8 > c) s2 = fma(v, v, s2);
         }
-        T dd = a0 + a1;
-#pragma unroll
-        for (int o = 4; o > 0; o >>= 1) dd += __shfl_xor_sync(0xffffffffu, dd, o);
-        if (sg > u && valid) {
-            const T f = b * dd;
-#pragma unroll
-            for (int i = I0; i < NB; ++i) {
-                yv[i] = fma(-f, xv[i], yv[i]);  // rows < c: xv = 0, the value is kept
-                y[8 * i] = yv[i];
-            }
+        if (q == 0) {  // lanes 0-7 hold column c + 1: the next reflector
+            s2 += __shfl_xor_sync(0xffffffffu, s2, 4);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, 2);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, 1);
+            __syncwarp();
+            if (lane == 0) make_reflector(Vs + (size_t)(c + 1) * ldv, c + 1, s2, bet);
         }
-        __syncwarp();
-    }
-    // the Gram of the panel's reflector vectors (v_k is zero above row c0 + k;
-    // its column holds R entries there), a dot product per (k, i), lanes over rows
-    for (int kk = 1; kk < 4; ++kk)
-        for (int i = 0; i < kk; ++i) {
-            const int ck = c0 + kk, ci = c0 + i;
-            T g = T(0);
-            if (ck < n) {
-                const T* vk = Vs + (size_t)ck * ldv;
-                const T* vi = Vs + (size_t)ci * ldv;
-                for (int r = ck + lane; r < n; r += 32) g = fma(vk[r], vi[r], g);
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
-            if (lane == 0) G[kk * 4 + i] = g;
-        }
-    __syncwarp();
-}
-
-template <typename T, int NB, int I0 = 0>
-__device__ __forceinline__ void qr_panel_update_at(int I, T* Vs, const T* bet, const T* G, int ldv, int n, int s, int q,
-                                                   int lane)
-{
-    if constexpr (I0 < NB) {
-        if (I == I0) qr_panel_update<T, NB, I0>(Vs, bet, G, ldv, n, s, q, lane);
-        else qr_panel_update_at<T, NB, I0 + 2>(I, Vs, bet, G, ldv, n, s, q, lane);
     }
 }
 
 template <typename T, int NB, int I0 = 0>
-__device__ __forceinline__ void qr_panel_factor_at(int I, T* Vs, T* bet, T* G, int ldv, int n, int s, int lane)
+__device__ __forceinline__ void qr_step_at(int I, T* Vs, T* bet, int ldv, int n, int c, int warp, int W, int lane)
 {
     if constexpr (I0 < NB) {
-        if (I == I0) qr_panel_factor<T, NB, I0>(Vs, bet, G, ldv, n, s, lane);
-        else qr_panel_factor_at<T, NB, I0 + 2>(I, Vs, bet, G, ldv, n, s, lane);
+        if (I == I0) qr_step<T, NB, I0>(Vs, bet, ldv, n, c, warp, W, lane);
+        else qr_step_at<T, NB, I0 + 2>(I, Vs, bet, ldv, n, c, warp, W, lane);
     }
 }
 
@@ -375,23 +284,17 @@ __global__ void __launch_bounds__(qr_threads<NB>()) warm_qr_kernel(const T* __re
         for (int r = n + lane; r < ldv; r += 32) Vs[(size_t)c * ldv + r] = T(0);
     if (tid == 0) s_next = 0;
     __syncthreads();
-    // Householder QR by panels of four columns, one block barrier per panel:
-    // in step s, warp 0 brings panel s + 1 up to date with panel s's
-    // reflectors and factors it (look-ahead), while the other warps apply
-    // panel s's reflectors to the later chunks
-    __shared__ T s_G[2][16];  // the Gram of panel s's reflectors, panel parity s % 2
-    const int nP = (n + 3) / 4;
-    if (warp == 0) qr_panel_factor_at<T, NB>(0, Vs, bet, s_G[0], ldv, n, 0, lane);
+    // Householder QR, one barrier per column
+    if (warp == 0) {
+        T s2 = T(0);
+        for (int r = lane; r < n; r += 32) s2 = fma(Vs[r], Vs[r], s2);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        if (lane == 0) make_reflector(Vs, 0, s2, bet);
+    }
     __syncthreads();
-    for (int s = 0; s < nP - 1; ++s) {
-        const int I = 2 * (s >> 2);  // the 16-row segment panel s starts in
-        const T* G = s_G[s & 1];
-        if (warp == 0) {
-            qr_panel_update_at<T, NB>(I, Vs, bet, G, ldv, n, s, s + 1, lane);
-            qr_panel_factor_at<T, NB>(2 * ((s + 1) >> 2), Vs, bet, s_G[(s + 1) & 1], ldv, n, s + 1, lane);
-        } else {
-            for (int q = s + 1 + warp; q < nP; q += W - 1) qr_panel_update_at<T, NB>(I, Vs, bet, G, ldv, n, s, q, lane);
-        }
+    for (int c = 0; c < n - 1; ++c) {
+        qr_step_at<T, NB>(2 * (c >> 4), Vs, bet, ldv, n, c, warp, W, lane);
         __syncthreads();
     }
     // Q = H_0 H_1 ... H_{n-1}; its column j is H_0 ... H_j e_j (the later
@@ -701,9 +604,10 @@ cudaError_t launch_warm_qr(const JacobiPlan& p, const T* vrec, size_t vstride, i
     }
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    // warp 0 for the panels, a warp per further chunk of four columns: 4 to 16 warps
+    // a warp per chunk of four columns, 4 to 32 warps (16 beyond 18 rows per lane)
+    const int wmax = qr_nb(p.n) <= 18 ? 32 : WQ / 32;
     int warps = (p.n + 3) / 4;
-    warps = warps < 4 ? 4 : (warps > WQ / 32 ? WQ / 32 : warps);
+    warps = warps < 4 ? 4 : (warps > wmax ? wmax : warps);
     kern<<<(unsigned)p.n3, 32 * warps, sm, s>>>(vrec, p.n, vstride, wrec, Q, flag, ctl);
     return cudaGetLastError();
 }

@@ -33,6 +33,9 @@ struct tnn_ctx {
     float* d_sweep_log = nullptr;  // the log's device buffer (grown on demand)
     int64_t sweep_log_cap = 0;   // slices it holds
     float* last_sweep_log = nullptr;  // the log of the last Jacobi launch, if it kept one
+    // the warm-start QR's side stream and its two events (none if their creation failed)
+    cudaStream_t qr_stream = nullptr;
+    cudaEvent_t ev_tail = nullptr, ev_qr = nullptr;
     int opt_warm = 1;            // TNN_OPT_ADMM_WARM_START (tnn_complete)
     SliceStats* last_stats = nullptr;
     int64_t last_n3 = 0;
@@ -303,6 +306,15 @@ tnn_status tnn_create(tnn_ctx** out, int device)
         delete ctx;
         return TNN_ENOMEM;
     }
+    if (cudaStreamCreateWithFlags(&ctx->qr_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_tail, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_qr, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();  // no side stream: the QR stays on the call's stream
+        if (ctx->ev_tail) cudaEventDestroy(ctx->ev_tail);
+        if (ctx->qr_stream) cudaStreamDestroy(ctx->qr_stream);
+        ctx->qr_stream = nullptr;
+        ctx->ev_tail = ctx->ev_qr = nullptr;
+    }
     *out = ctx;
     return TNN_OK;
 }
@@ -317,6 +329,9 @@ void tnn_destroy(tnn_ctx* ctx)
     for (auto& kv : ctx->tc_ops) cudaFree(kv.second);
     if (ctx->d_err) cudaFree(ctx->d_err);
     if (ctx->d_sweep_log) cudaFree(ctx->d_sweep_log);
+    if (ctx->ev_tail) cudaEventDestroy(ctx->ev_tail);
+    if (ctx->ev_qr) cudaEventDestroy(ctx->ev_qr);
+    if (ctx->qr_stream) cudaStreamDestroy(ctx->qr_stream);
     for (auto& r : ctx->recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : ctx->pool) cudaEventDestroy(e);
     if (ctx->h_ctl) cudaFreeHost(ctx->h_ctl);
@@ -782,6 +797,7 @@ tnn_status admm_enqueue_iters(tnn_ctx* ctx, const AdmmJob& j, int iters, cudaStr
             int* wflag = warm ? (int*)((char*)j.warm + ((size_t)n3 * j.jp.n * j.jp.n * 4 + 255) / 256 * 256) : nullptr;
             if (warm) {
                 TRACE(K_WARM);
+                if (j.qs) CK(cudaStreamWaitEvent(s, j.ev_qr, 0));  // the previous iteration's QR
                 CK(launch_warm_gemm<float>(j.jp, (const float*)j.W, Q, wflag, (float*)j.wscr, j.ctl, s));
             }
             // with the offloaded tail the Jacobi kernel leaves its columns in
@@ -799,7 +815,18 @@ tnn_status admm_enqueue_iters(tnn_ctx* ctx, const AdmmJob& j, int iters, cudaStr
                 TRACE(K_SVT_TAIL);
                 CK(launch_warm_tail<float>(j.jp, (float*)j.W, (const float*)j.wscr, j.tinfo, Q, j.wrec, j.ctl, s));
             }
-            if (warm) {
+            if (warm && tail && j.qs) {
+                // on the side stream, after the tail; it checks no stop flag (the
+                // tail marks the slices it wrote, and the finalize that may set
+                // the flag runs alongside)
+                CK(cudaEventRecord(j.ev_tail, s));
+                CK(cudaStreamWaitEvent(j.qs, j.ev_tail, 0));
+                {
+                    Trace tq(ctx, K_WARM, j.qs);
+                    CK(launch_warm_qr<float>(j.jp, Q, (size_t)j.jp.n * j.jp.n, j.wrec, Q, wflag, nullptr, j.qs));
+                }
+                CK(cudaEventRecord(j.ev_qr, j.qs));
+            } else if (warm) {
                 TRACE(K_WARM);
                 const size_t wstride = (size_t)j.jp.ldA * j.jp.nb * j.jp.K;
                 CK(launch_warm_qr<float>(j.jp, tail ? Q : (const float*)j.wscr, tail ? (size_t)j.jp.n * j.jp.n : wstride,
@@ -816,6 +843,7 @@ tnn_status admm_enqueue_iters(tnn_ctx* ctx, const AdmmJob& j, int iters, cudaStr
         }
         { TRACE(K_FINALIZE); CK(launch_admm_finalize(j.ctl, j.partials, nblk, j.stats, n3, s)); }
     }
+    if (j.qs) CK(cudaStreamWaitEvent(s, j.ev_qr, 0));  // the last QR before the call's stream goes on
     return TNN_OK;
 }
 
@@ -927,6 +955,11 @@ tnn_status tnn_complete(tnn_ctx* ctx, const void* B, const uint8_t* mask, tnn_sh
         job.wscr = at(ctx, oWc);
         job.wrec = (int*)at(ctx, oWr);
         if (tail) job.tinfo = (float*)at(ctx, oWt);
+        if (tail && ctx->qr_stream) {
+            job.qs = ctx->qr_stream;
+            job.ev_tail = ctx->ev_tail;
+            job.ev_qr = ctx->ev_qr;
+        }
     }
     st = admm_run(ctx, job, params->beta0, params->max_iter, s, &res);
     if (st) return st;
@@ -988,6 +1021,11 @@ tnn_status tnn_admm_iterate(tnn_ctx* ctx, const void* B, const uint8_t* mask, tn
         job.wscr = at(ctx, oWc);
         job.wrec = (int*)at(ctx, oWr);
         if (tail) job.tinfo = (float*)at(ctx, oWt);
+        if (tail && ctx->qr_stream) {
+            job.qs = ctx->qr_stream;
+            job.ev_tail = ctx->ev_tail;
+            job.ev_qr = ctx->ev_qr;
+        }
     }
     st = admm_run(ctx, job, *beta, max_iter, s, &res);
     if (st) return st;

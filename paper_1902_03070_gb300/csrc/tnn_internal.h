@@ -336,6 +336,11 @@ struct AdmmJob {
     int* wrec = nullptr;
     // offloaded SVT tail (tail_supported(jp)): n3 x tail_info_stride(npad) words
     float* tinfo = nullptr;
+    // with the tail: the QR on this side stream (it needs only the tail's
+    // output, so it overlaps the inverse and next forward transforms); the
+    // next A Q waits for ev_qr
+    cudaStream_t qs = nullptr;
+    cudaEvent_t ev_tail = nullptr, ev_qr = nullptr;
 };
 
 // The job's transform operators, from the context's caches (built on first use).

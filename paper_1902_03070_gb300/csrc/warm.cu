@@ -27,9 +27,8 @@
 namespace tnn {
 namespace {
 
-constexpr int WQ = 512;   // threads per CTA of the QR for 28 rows per lane (16 warps) ...
-// ... and 32 warps up to 18 rows per lane (a chunk per warp for n <= 128 +)
-template <int NB> constexpr int qr_threads() { return NB <= 18 ? 1024 : WQ; }
+constexpr int WQ = 512;   // threads per CTA of the QR (16 warps: room on its SMs for other kernels' CTAs)
+template <int NB> constexpr int qr_threads() { return WQ; }
 constexpr int WGM = 640;  // most threads per CTA of the GEMM (20 warps)
 constexpr int WCB = 8;    // output columns per warp tile of the GEMM
 constexpr int WMR = 8;    // most rows per lane of the GEMM (m <= 256)
@@ -604,10 +603,9 @@ cudaError_t launch_warm_qr(const JacobiPlan& p, const T* vrec, size_t vstride, i
     }
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    // a warp per chunk of four columns, 4 to 32 warps (16 beyond 18 rows per lane)
-    const int wmax = qr_nb(p.n) <= 18 ? 32 : WQ / 32;
+    // a warp per chunk of four columns, 4 to 16 warps
     int warps = (p.n + 3) / 4;
-    warps = warps < 4 ? 4 : (warps > wmax ? wmax : warps);
+    warps = warps < 4 ? 4 : (warps > WQ / 32 ? WQ / 32 : warps);
     kern<<<(unsigned)p.n3, 32 * warps, sm, s>>>(vrec, p.n, vstride, wrec, Q, flag, ctl);
     return cudaGetLastError();
 }

@@ -1318,21 +1318,35 @@ __global__ void __launch_bounds__(Bound<T, K, R, WITHV>::value) jacobi_kernel(KA
     const T tau = a.ctl ? (T)(1.0 / a.ctl->beta) : (ictl ? (T)(1.0 / ictl->beta) : (T)(item ? item->tau : a.tau));
 
     if (!WITHV) {
-        // ---- SVT: kept columns (sigma > tau) and their coefficients
-        if (tid == 0) {
+        // ---- SVT: kept columns (sigma > tau) and their coefficients, compacted
+        // in column order by warp 0, 32 columns at a time (each chunk's values
+        // are read before any of its writes, and a kept column's new position
+        // is never past its own, so no value is overwritten before it is read)
+        if (warp == 0) {
             int kk = 0;
             double nuc = 0.0;
-            for (int c = 0; c < npad; ++c) {
-                T sg = sig[c];
-                if (sg > tau && cf[c] > T(0)) {
-                    kidx[kk] = c;
-                    cf[kk] = (T(1) - tau / sg) / cf[c];
+            for (int c0 = 0; c0 < npad; c0 += 32) {
+                const int c = c0 + lane;
+                const T sg = c < npad ? sig[c] : T(0);
+                const T s2 = c < npad ? cf[c] : T(0);
+                const bool kp = c < npad && sg > tau && s2 > T(0);
+                const unsigned mask = __ballot_sync(FULL, kp);
+                const int pos = kk + __popc(mask & ((1u << lane) - 1u));
+                __syncwarp();
+                if (kp) {
+                    kidx[pos] = c;
+                    cf[pos] = (T(1) - tau / sg) / s2;
                     nuc += (double)(sg - tau);
-                    ++kk;
                 }
+                kk += __popc(mask);
+                __syncwarp();
             }
-            s_keep = kk;
-            s_nuc = nuc;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) nuc += __shfl_xor_sync(FULL, nuc, o);
+            if (lane == 0) {
+                s_keep = kk;
+                s_nuc = nuc;
+            }
         }
         __syncthreads();
         const int keep = s_keep;

@@ -149,7 +149,10 @@ __device__ __forceinline__ void make_reflector(T* x, int c, T s2, T* bet)
     const T alpha = x0 >= T(0) ? -nx : nx;
     x[c] = x0 - alpha;
     const T vn2 = T(2) * nx * (nx + fabs(x0));  // |x - alpha e_c|^2, no cancellation
-    bet[c] = vn2 > T(0) ? T(2) / vn2 : T(0);
+    T r;  // 1 / vn2, correctly rounded (the reciprocal is cheaper than a division on the reflector's chain)
+    if constexpr (sizeof(T) == 4) r = __frcp_rn(vn2);
+    else r = T(1) / vn2;
+    bet[c] = vn2 > T(0) ? T(2) * r : T(0);
 }
 
 // The QR keeps the n x n matrix in shared memory, column c at Vs + c * ldv

@@ -239,3 +239,41 @@ def test_admm_warm_size_zero_where_unused():
     assert tnn.Context.admm_warm_state((48, 48, 16), "fp64") is None        # FP64: cold
     assert tnn.Context.admm_warm_state((512, 512, 31), "bf16split") is None  # slices on clusters
     assert tnn.Context.admm_warm_state((48, 48, 16), "fp32") is not None
+
+
+@pytest.mark.parametrize("shape", [(100, 70, 6), (70, 101, 5), (52, 52, 4)])
+def test_warm_tail_ragged_shapes_match_oracle(ctx, shape):
+    """The warm start with its offloaded SVT tail on shapes whose smaller
+    side leaves a partial 48-column tile of the tail kernel, in both slice
+    orientations, one of them with a leading dimension that is not a multiple
+    of 4 (the tail's element-wise load and store paths): a whole FP32
+    completion has the oracle's final error and the cold run's iterates."""
+    from paper_1902_03070_gb300 import tnn
+    torch = torch_cuda()
+    T, B, mask = _small(seed=3, shape=shape, r=3, frac=0.5)
+    prm = dict(beta0=1e-2, rho=1.15, beta_max=1e8, tol=-1.0, max_iter=60)
+    Xo, _, _ = O.admm(B, mask, nthreads=THREADS, **prm)
+    dt = dtype_of("fp32")
+    Bd, md = tnn.to_fortran(B, dtype=dt), tnn.to_fortran(mask)
+    assert ctx.admm_warm_state(shape, "fp32") is not None
+    Xw = tnn.fortran_empty(B.shape, dt)
+    ctx.profile(True)
+    ctx.complete(Bd, md, Xw, ctx.params(**prm), prec="fp32")
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    assert "svt_tail" in prof and "warm" in prof  # the warm-started path with its tail ran
+    Xc = tnn.fortran_empty(B.shape, dt)
+    try:
+        ctx.set_option(tnn.OPT_ADMM_WARM_START, 0)
+        ctx.complete(Bd, md, Xc, ctx.params(**prm), prec="fp32")
+    finally:
+        ctx.set_option(tnn.OPT_ADMM_WARM_START, 1)
+    xw, xc = tnn.to_numpy(Xw).astype(np.float64), tnn.to_numpy(Xc).astype(np.float64)
+    nt = np.linalg.norm(T)
+    ew, ec, eo = np.linalg.norm(xw - T) / nt, np.linalg.norm(xc - T) / nt, np.linalg.norm(Xo - T) / nt
+    log_err("warm tail ragged %s" % (shape,), warm=ew, cold=ec, oracle=eo,
+            warm_vs_oracle=np.linalg.norm(xw - Xo) / np.linalg.norm(Xo))
+    assert abs(ew - eo) <= 1e-4 and abs(ec - eo) <= 1e-4, (ew, ec, eo)
+    assert np.linalg.norm(xw - Xo) <= 1e-3 * np.linalg.norm(Xo)
+    assert np.linalg.norm(xw - xc) <= 1e-3 * np.linalg.norm(Xo)

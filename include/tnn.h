@@ -222,7 +222,10 @@ tnn_status tprod_dct(tnn_ctx* ctx, const void* X, const void* Y, int64_t m1, int
  * rep (may be NULL) receives the run's report.  Synchronises the stream.
  * Returns TNN_ENOCONV if max_iter was reached before the tol test passed.
  * The FP32 precisions warm-start each iteration's per-slice Jacobi from the
- * previous iteration's right singular vectors (see tnn_admm_warm_size). */
+ * previous iteration's right singular vectors (see tnn_admm_warm_size); the
+ * orthogonalisation of those vectors runs on a stream the context owns,
+ * ordered after the iteration's work and before the next one's by events,
+ * and joined back to `stream` before the call returns. */
 tnn_status tnn_complete(tnn_ctx* ctx, const void* B, const uint8_t* mask, tnn_shape shape,
                         const tnn_admm_params* params, tnn_precision prec, void* X_out,
                         tnn_admm_report* rep, void* stream);
@@ -246,7 +249,10 @@ tnn_status tnn_complete(tnn_ctx* ctx, const void* B, const uint8_t* mask, tnn_sh
  * previous iteration makes the columns of A Q nearly orthogonal and cuts the
  * sweeps severalfold late in a completion.  Any orthogonal Q is correct, so
  * a zero-filled or stale buffer only costs sweeps.  Used by the FP32
- * precisions for slices one CTA holds; otherwise not touched. */
+ * precisions for slices one CTA holds; otherwise not touched.  Within a call
+ * the buffer briefly holds the unorthogonalised vectors (the context's side
+ * stream turns them into Q); the call joins that stream back to `stream`
+ * before it returns, so between calls the buffer always holds Q. */
 tnn_status tnn_admm_iterate(tnn_ctx* ctx, const void* B, const uint8_t* mask, tnn_shape shape,
                             const tnn_admm_params* params, tnn_precision prec, void* X, void* M,
                             double* beta, int32_t iters, void* warm, tnn_admm_report* rep, void* stream);
